@@ -1,0 +1,193 @@
+/*
+ * motjvie.h -- C ABI of libmotjvie: a single-GPU (sm_103a) marching-on-in-time
+ * current-density volume integral equation (MOT-JVIE) solver for transient
+ * dielectric scattering, whose present-time operator Z0 is applied matrix-free
+ * through zero-padded 3-D FFTs (paper Sec. IV, Eq. 10-12).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Status: every call returns a mot_status; 0 is success, negative values are
+ *   errors.  No call aborts or throws across the ABI.  mot_last_error() returns
+ *   a thread-local message describing the last failure of the calling thread.
+ * - Grid: n = {Nx, Ny, Nz} voxels of isotropic size h [m] (Sec. II: uniform
+ *   Cartesian voxel grid; Table I lists only isotropic meshes).  Voxel arrays are
+ *   [Nz][Ny][Nx] with x fastest.  Current vectors carry 3 Cartesian components
+ *   per voxel, [3][Nz][Ny][Nx], and a batch of nrhs excitations is
+ *   [nrhs][3][Nz][Ny][Nx].  Every voxel carries 3 unknowns, including voxels
+ *   with eps_r = 1, where the current is identically zero (Sec. II).
+ * - Time step: dt = alpha * dt_CFL with dt_CFL = h / (c0 sqrt 3) (Eq. 9), i.e.
+ *   c0 dt / h = alpha / sqrt 3.
+ * - Ownership: the caller owns every host array it passes; the library copies
+ *   what it keeps.  Device memory of a problem or run is owned by the library
+ *   (cudaMalloc on the context's device) and freed by the matching destroy.
+ *   Device pointers passed in (mot_apply_Z0) stay owned by the caller and must
+ *   hold at least the documented number of elements.  Borrowed device
+ *   pointers handed out (mot_run_current_device) stay valid until the next
+ *   mot_run_step or mot_run_destroy on that run.
+ * - Streams: all device work of a context is ordered on the context's stream
+ *   (the one given to mot_ctx_create, or a library-created one when NULL).
+ *   Calls that return host data synchronise that stream before returning.
+ * - Threads: handles are not thread-safe; use one context per host thread.
+ */
+#ifndef MOTJVIE_H
+#define MOTJVIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOT_OK = 0,
+    MOT_EINVAL = -1,       /* invalid argument (message says which)                    */
+    MOT_ENOMEM = -2,       /* device or host allocation failed                         */
+    MOT_ENOTCONV = -3,     /* TFQMR did not reach the tolerance within maxit          */
+    MOT_EUNSUPPORTED = -4, /* valid request outside what this build supports          */
+    MOT_ECUDA = -5,        /* a CUDA runtime call failed (message has the CUDA error)  */
+    MOT_ETIMEOUT = -6,     /* a bounded device wait gave up                            */
+    MOT_EBUSY = -7,
+    MOT_ECANCELLED = -8
+} mot_status;
+
+/* arithmetic of a marching run (a5/a6 of the solver):
+ * MOT_FP64  -- every product, FFT, history sum and Krylov vector in FP64;
+ * MOT_MIXED -- FFTs, spectral multiplies, the history sum and the inner TFQMR
+ *              vectors in FP32; FP64 for Krylov inner products, the residual,
+ *              the refinement correction and the marched solution J_n.         */
+typedef enum { MOT_FP64 = 0, MOT_MIXED = 1 } mot_precision;
+
+/* element type of device vectors handed to mot_apply_Z0 */
+typedef enum { MOT_F64 = 0, MOT_F32 = 1 } mot_dtype;
+
+/* Modulated-Gaussian plane wave of Eq. 7-8:
+ *   E^i(r,t) = E0 pol (1/(sigma sqrt(2 pi))) exp(-tau^2/(2 sigma^2)) cos(2 pi f0 tau),
+ *   tau = t - t0 - khat.(r - r_ref)/c0,
+ * with r_ref the grid corner that minimises khat.r, so the pulse enters the
+ * grid at t = t0.  SI units: E0 [V/m], sigma and t0 [s], f0 [Hz].  khat and pol
+ * must be unit vectors with khat.pol = 0 (|.|, dot checked to 1e-9).            */
+typedef struct {
+    double E0, sigma, t0, f0;
+    double khat[3];
+    double pol[3];
+} mot_planewave;
+
+/* Solver options; pass NULL for the defaults shown.                           */
+typedef struct {
+    double tol;       /* TFQMR relative residual target (paper: 1e-6, Sec. V-A).
+                         Default 1e-11 for MOT_FP64, 1e-6 (outer) for MOT_MIXED   */
+    int maxit;        /* TFQMR iteration cap per solve (default 500)             */
+    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-4)      */
+    int max_refine;   /* MOT_MIXED refinement sweeps cap (default 6)              */
+    double delta;     /* diagonal shift of the delta-regularised MOT,
+                         Z_n + delta I (Sec. II; the paper uses 0).  Only 0 is
+                         supported (MOT_EUNSUPPORTED otherwise)                   */
+    int timing;       /* 1: time the history z-pass and the Z0 spectral z-pass
+                         kernels of every step with CUDA events (fills
+                         ms_zhist / ms_zgreen of mot_step_stats; adds event
+                         overhead).  Default 0                                     */
+} mot_options;
+
+typedef struct {
+    int32_t n[3];    /* Nx, Ny, Nz                                              */
+    int32_t M0[3];   /* padded FFT grid of the present-time product (>= N + r0)  */
+    int32_t Mh[3];   /* padded FFT grid of the history sum (>= 2N - 1)           */
+    int32_t r0;      /* reach of the lag-0 table: largest |d_i| with g_0(d) != 0 */
+    int32_t ell;     /* history length ell = ceil(R_max/(c0 dt)) + 2 (Eq. 4)     */
+    double rho;      /* c0 dt / h = alpha / sqrt 3                               */
+    double dt;       /* time step [s]                                            */
+} mot_problem_info;
+
+typedef struct {
+    int32_t iters;     /* TFQMR iterations (sum over refinement sweeps)          */
+    int32_t sweeps;    /* refinement sweeps (1 for MOT_FP64)                     */
+    double relres;     /* final ||b - Z0 J_n|| / ||b|| (max over the batch)       */
+    float ms_history;  /* device time of the right-hand side (incident + history) */
+    float ms_solve;    /* device time of the solve                               */
+    float ms_push;     /* device time of the history-ring update                 */
+    int32_t mvps;      /* Z0 products applied in the step                        */
+    float ms_zhist;    /* history z-pass kernel time (timing option, else 0)     */
+    float ms_zgreen;   /* summed Z0 spectral z-pass kernel time (timing option)  */
+} mot_step_stats;
+
+typedef struct mot_ctx mot_ctx;
+typedef struct mot_problem mot_problem;
+typedef struct mot_run mot_run;
+
+/* Message of the calling thread's last failure ("" if none).                  */
+const char *mot_last_error(void);
+
+/* Context on CUDA device `device`, ordering all work on `cuda_stream` (a
+ * cudaStream_t, borrowed; NULL -> the library creates and owns a stream).
+ * Errors: MOT_EINVAL (bad device), MOT_ECUDA.                                  */
+mot_status mot_ctx_create(int device, void *cuda_stream, mot_ctx **out);
+void mot_ctx_destroy(mot_ctx *ctx);
+
+/* Problem: grid n, spacing h [m] > 0, relative permittivity eps_r (host,
+ * [Nz][Ny][Nx] doubles, each finite and >= 1; copied), time-step factor
+ * alpha > 0 (dt = alpha dt_CFL, Eq. 9).  Computes the lag-0 Galerkin table,
+ * its spectrum on the M0 grid and the device copies of eps_r.  The history
+ * tables are computed on the first mot_run_create.  Sec. II, Eq. 4, Eq. 10-11.
+ * Errors: MOT_EINVAL (sizes, h, alpha, eps_r), MOT_ENOMEM, MOT_ECUDA.           */
+mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const double *eps_r,
+                              double alpha, const mot_options *opt, mot_problem **out);
+mot_status mot_problem_info_get(const mot_problem *p, mot_problem_info *info);
+void mot_problem_destroy(mot_problem *p);
+
+/* y = Z0 x for nrhs current vectors (Eq. 12: Z0 x = D x - X (G x), with
+ * (G x) from Eq. 11 through zero-padded FFTs on the M0 grid).  x_dev, y_dev:
+ * device arrays of nrhs*3*Nz*Ny*Nx elements of `dtype` (MOT_F64 computes in
+ * FP64, MOT_F32 in FP32), x fastest; x and y must not overlap.  Asynchronous on
+ * the context stream.  Errors: MOT_EINVAL (null, nrhs < 1, dtype), MOT_ENOMEM
+ * (workspace), MOT_ECUDA.                                                     */
+mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
+
+/* The library's own Galerkin table of lag `lag` (0 <= lag <= ell):
+ * g_out[6][2Rz+1][2Ry+1][2Rx+1] doubles, components (xx, yy, zz, xy, xz, yz),
+ * offset d = (dx, dy, dz) at index (dz+Rz, dy+Ry, dx+Rx); R_out receives
+ * (Rx, Ry, Rz) = min(reach of lag, N_i - 1).  If g_out is NULL only R_out is
+ * written.  Synchronous.  Errors: MOT_EINVAL, MOT_ECUDA.                      */
+mot_status mot_kernel_table(mot_problem *p, int lag, double *g_out, int32_t R_out[3]);
+
+/* Replace the table of lag `lag` by a caller-supplied one (same layout as
+ * mot_kernel_table, extents R; entries beyond N_i - 1 are ignored) and
+ * recompute that lag's spectrum.  Used to feed an externally computed table
+ * into the FFT path.  Lags >= 1 must be set before mot_run_create.
+ * Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA.                                   */
+mot_status mot_set_kernel_table(mot_problem *p, int lag, const double *g, const int32_t R[3]);
+
+/* Host-only table generator (no GPU needed): the lag-`lag` Galerkin table for
+ * c0 dt / h = rho over |d_i| <= R_i, same layout as mot_kernel_table.
+ * Errors: MOT_EINVAL.                                                          */
+mot_status mot_table_host(double rho, int lag, const int32_t R[3], double *g_out);
+
+/* A marching run of nrhs excitations sharing the problem's Z0 (host array of
+ * nrhs plane waves, copied).  Allocates the device history ring (ell slots of
+ * spectra on the Mh grid) and computes the history tables on first use.
+ * Errors: MOT_EINVAL (nrhs < 1, bad plane wave), MOT_ENOMEM, MOT_ECUDA.        */
+mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, int precision,
+                          mot_run **out);
+
+/* Advance nsteps time steps (Eq. 3): b_n = E^i_n - sum_{k=1..ell} Z_k J_{n-k},
+ * then Z0 J_n = b_n by TFQMR (x0 = J_{n-1}).  J_out (host, nullable) receives
+ * [nsteps][nrhs][3][Nz][Ny][Nx] doubles in A/m^2; stats (nullable) receives
+ * nsteps entries.  Synchronous when J_out or stats is given.
+ * Errors: MOT_EINVAL, MOT_ENOTCONV (state still advanced), MOT_ECUDA.         */
+mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *stats);
+
+/* Device pointer to the latest J_n: nrhs*3*Nz*Ny*Nx doubles (borrowed).      */
+mot_status mot_run_current_device(mot_run *r, const void **J_dev);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (instrumentation for launch accounting; no counterpart in the paper).        */
+mot_status mot_kernel_launches(uint64_t *count);
+
+/* Index of the next step to be computed.                                       */
+mot_status mot_run_step_index(const mot_run *r, int64_t *n);
+void mot_run_destroy(mot_run *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOTJVIE_H */

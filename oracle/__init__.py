@@ -68,6 +68,7 @@ def lib():
         L.oracle_green_apply.argtypes = [i, i, i, i, i, i, P, P, P]
         L.oracle_Zk_apply.argtypes = [i, i, i, i, P, i, i, i, P, P, P]
         L.oracle_incident.argtypes = [i, i, i, d, P, P, d, P]
+        L.oracle_Zk_rows.argtypes = [i, i, i, i, P, i, i, i, P, P, i, P, P, P]
         L.oracle_init()
         _lib = L
     return _lib
@@ -195,6 +196,19 @@ def Zk_apply(k, N, eps, R, g, x) -> np.ndarray:
     return y
 
 
+def Zk_rows(k, N, eps, R, g, x, rows_p, rows_m) -> np.ndarray:
+    """Selected rows (p_i, m_i) of Z_k x, same definition as Zk_apply."""
+    Nx, Ny, Nz = N
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(3, Nz, Ny, Nx)
+    eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(Nz, Ny, Nx)
+    rp = np.ascontiguousarray(rows_p, dtype=np.int32)
+    rm = np.ascontiguousarray(rows_m, dtype=np.int64)
+    out = np.zeros(len(rp))
+    lib().oracle_Zk_rows(int(k), Nx, Ny, Nz, _ptr(eps), R[0], R[1], R[2], _ptr(np.ascontiguousarray(g)), _ptr(x),
+                         len(rp), _ptr(rp), _ptr(rm), _ptr(out))
+    return out
+
+
 def planewave_array(pw) -> np.ndarray:
     """(E0, sigma, t0, f0, khat[3], pol[3]) as 10 doubles."""
     if isinstance(pw, dict):
@@ -304,13 +318,3 @@ class Problem:
             for n in range(nsteps):
                 J[n] = self.solve_Z0(self.rhs(n, pw, J))
         return out
-
-
-def gaussian_pulse_for(nsteps: int, alpha: float, h: float, khat=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), E0=1.0):
-    """Synthetic pulse recipe: T_sim = nsteps*dt, sigma = T_sim/20, t0 = 5 sigma,
-    sigma_f = 1/(2 pi sigma), f0 = 2.5 sigma_f (Eq. 7-8 with Table II's shape)."""
-    dt = alpha * dt_cfl(h)
-    T = nsteps * dt
-    sigma = T / 20.0
-    sf = 1.0 / (2.0 * math.pi * sigma)
-    return {"E0": E0, "sigma": sigma, "t0": 5.0 * sigma, "f0": 2.5 * sf, "khat": tuple(khat), "pol": tuple(pol)}

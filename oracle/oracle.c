@@ -716,3 +716,34 @@ void oracle_incident(int Nx, int Ny, int Nz, double h, const double *eps, const 
         b[2 * n + m] = s * e[2];
     }
 }
+
+/*
+ * Selected rows of y = Z_k x (same definition as oracle_Zk_apply), for
+ * parity checks on grids where the full product is too slow:
+ * out[i] = (Z_k x)(p_i, m_i) with m_i = (mz*Ny + my)*Nx + mx.
+ */
+void oracle_Zk_rows(int k, int Nx, int Ny, int Nz, const double *eps, int Rx, int Ry, int Rz, const double *g,
+                    const double *x, int nrows, const int *rp, const long *rm, double *out) {
+    long n = (long)Nx * Ny * Nz;
+    int tx = 2 * Rx + 1, ty = 2 * Ry + 1, tz = 2 * Rz + 1;
+    long t3 = (long)tx * ty * tz;
+    double Tk = oracle_temporal(k);
+    int cmap[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < nrows; ++i) {
+        int p = rp[i];
+        long m = rm[i];
+        int mx = (int)(m % Nx), my = (int)((m / Nx) % Ny), mz = (int)(m / ((long)Nx * Ny));
+        double acc = 0.0;
+        for (int dz = -Rz; dz <= Rz; ++dz)
+            for (int dy = -Ry; dy <= Ry; ++dy)
+                for (int dx = -Rx; dx <= Rx; ++dx) {
+                    int sx = mx - dx, sy = my - dy, sz = mz - dz;
+                    if (sx < 0 || sx >= Nx || sy < 0 || sy >= Ny || sz < 0 || sz >= Nz) continue;
+                    long o = ((long)(dz + Rz) * ty + (dy + Ry)) * tx + (dx + Rx);
+                    long s = ((long)sz * Ny + sy) * Nx + sx;
+                    for (int q = 0; q < 3; ++q) acc += g[cmap[p][q] * t3 + o] * x[q * n + s];
+                }
+        out[i] = eps[m] * Tk * x[p * n + m] - (eps[m] - 1.0) * acc;
+    }
+}

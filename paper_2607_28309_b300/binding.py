@@ -1,0 +1,246 @@
+"""ctypes binding of libmotjvie (argument marshalling only).
+
+Every function keeps the C name and argument order of include/motjvie.h; device
+arrays are passed as raw pointers (``int``) or as torch CUDA tensors, host arrays
+as numpy arrays.  Errors raise MotError carrying the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmotjvie.so")
+
+MOT_OK = 0
+MOT_EINVAL = -1
+MOT_ENOMEM = -2
+MOT_ENOTCONV = -3
+MOT_EUNSUPPORTED = -4
+MOT_ECUDA = -5
+MOT_ETIMEOUT = -6
+MOT_FP64 = 0
+MOT_MIXED = 1
+MOT_F64 = 0
+MOT_F32 = 1
+
+__all__ = [
+    "LIB_PATH", "MotError", "lib", "mot_planewave", "mot_options", "mot_problem_info", "mot_step_stats",
+    "mot_last_error", "mot_ctx_create", "mot_ctx_destroy", "mot_problem_create", "mot_problem_info_get",
+    "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
+    "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
+    "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
+    "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
+]
+
+# every symbol include/motjvie.h declares
+EXPORTED = [
+    "mot_last_error", "mot_ctx_create", "mot_ctx_destroy", "mot_problem_create", "mot_problem_info_get",
+    "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
+    "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
+    "mot_kernel_launches",
+]
+
+
+class MotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmotjvie status {status}: {msg}")
+        self.status = status
+
+
+class mot_planewave(ctypes.Structure):
+    _fields_ = [("E0", ctypes.c_double), ("sigma", ctypes.c_double), ("t0", ctypes.c_double),
+                ("f0", ctypes.c_double), ("khat", ctypes.c_double * 3), ("pol", ctypes.c_double * 3)]
+
+
+class mot_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("delta", ctypes.c_double), ("timing", ctypes.c_int)]
+
+
+class mot_problem_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("M0", ctypes.c_int32 * 3), ("Mh", ctypes.c_int32 * 3),
+                ("r0", ctypes.c_int32), ("ell", ctypes.c_int32), ("rho", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class mot_step_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("ms_history", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_push", ctypes.c_float),
+                ("mvps", ctypes.c_int32), ("ms_zhist", ctypes.c_float), ("ms_zgreen", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmotjvie.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MotError(MOT_ECUDA, f"{LIB_PATH} not built (run paper_2607_28309_b300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        L.mot_last_error.restype = ctypes.c_char_p
+        L.mot_ctx_create.argtypes = [I, P, PP]
+        L.mot_ctx_destroy.argtypes = [P]
+        L.mot_ctx_destroy.restype = None
+        L.mot_problem_create.argtypes = [P, P, D, P, D, P, PP]
+        L.mot_problem_info_get.argtypes = [P, P]
+        L.mot_problem_destroy.argtypes = [P]
+        L.mot_problem_destroy.restype = None
+        L.mot_apply_Z0.argtypes = [P, P, P, I, I]
+        L.mot_kernel_table.argtypes = [P, I, P, P]
+        L.mot_set_kernel_table.argtypes = [P, I, P, P]
+        L.mot_table_host.argtypes = [D, I, P, P]
+        L.mot_run_create.argtypes = [P, I, P, I, PP]
+        L.mot_run_step.argtypes = [P, I, P, P]
+        L.mot_run_current_device.argtypes = [P, PP]
+        L.mot_run_step_index.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        L.mot_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.mot_run_destroy.argtypes = [P]
+        L.mot_run_destroy.restype = None
+        for name in EXPORTED:
+            if name not in ("mot_ctx_destroy", "mot_problem_destroy", "mot_run_destroy", "mot_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MOT_OK:
+        raise MotError(status, mot_last_error())
+
+
+def _ptr(a):
+    """device pointer of a torch tensor / int, or host pointer of a numpy array"""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def mot_last_error() -> str:
+    return lib().mot_last_error().decode()
+
+
+def mot_ctx_create(device: int = 0, cuda_stream: int | None = None):
+    out = ctypes.c_void_p()
+    _check(lib().mot_ctx_create(int(device), ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(out)))
+    return out
+
+
+def mot_ctx_destroy(ctx):
+    lib().mot_ctx_destroy(ctx)
+
+
+def mot_problem_create(ctx, n, h: float, eps_r, alpha: float, opt: mot_options | None = None):
+    n_arr = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    eps = np.ascontiguousarray(eps_r, dtype=np.float64)
+    if eps.size != int(n[0]) * int(n[1]) * int(n[2]):
+        raise MotError(MOT_EINVAL, "eps_r size does not match the grid")
+    out = ctypes.c_void_p()
+    _check(lib().mot_problem_create(ctx, n_arr, float(h), _ptr(eps), float(alpha),
+                                    ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
+    return out
+
+
+def mot_problem_info_get(prob) -> mot_problem_info:
+    info = mot_problem_info()
+    _check(lib().mot_problem_info_get(prob, ctypes.byref(info)))
+    return info
+
+
+def mot_problem_destroy(prob):
+    lib().mot_problem_destroy(prob)
+
+
+def mot_apply_Z0(prob, x_dev, y_dev, nrhs: int, dtype: int):
+    _check(lib().mot_apply_Z0(prob, _ptr(x_dev), _ptr(y_dev), int(nrhs), int(dtype)))
+
+
+def mot_kernel_table(prob, lag: int):
+    R = (ctypes.c_int32 * 3)()
+    _check(lib().mot_kernel_table(prob, int(lag), None, R))
+    Rx, Ry, Rz = R[0], R[1], R[2]
+    g = np.zeros((6, 2 * Rz + 1, 2 * Ry + 1, 2 * Rx + 1))
+    _check(lib().mot_kernel_table(prob, int(lag), _ptr(g), R))
+    return (Rx, Ry, Rz), g
+
+
+def mot_set_kernel_table(prob, lag: int, g, R):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    Ra = (ctypes.c_int32 * 3)(*[int(v) for v in R])
+    _check(lib().mot_set_kernel_table(prob, int(lag), _ptr(g), Ra))
+
+
+def mot_table_host(rho: float, lag: int, R):
+    Rx, Ry, Rz = (int(v) for v in R)
+    g = np.zeros((6, 2 * Rz + 1, 2 * Ry + 1, 2 * Rx + 1))
+    Ra = (ctypes.c_int32 * 3)(Rx, Ry, Rz)
+    _check(lib().mot_table_host(float(rho), int(lag), Ra, _ptr(g)))
+    return g
+
+
+def _planewaves(exc):
+    arr = (mot_planewave * len(exc))()
+    for i, w in enumerate(exc):
+        if isinstance(w, dict):
+            arr[i].E0, arr[i].sigma, arr[i].t0, arr[i].f0 = w["E0"], w["sigma"], w["t0"], w["f0"]
+            for j in range(3):
+                arr[i].khat[j] = w["khat"][j]
+                arr[i].pol[j] = w["pol"][j]
+        else:
+            arr[i] = w
+    return arr
+
+
+def mot_run_create(prob, exc, precision: int = MOT_FP64):
+    arr = _planewaves(exc)
+    out = ctypes.c_void_p()
+    _check(lib().mot_run_create(prob, len(exc), arr, int(precision), ctypes.byref(out)))
+    return out
+
+
+def mot_run_step(run, nsteps: int, J_out=None, stats=None, allow_notconv: bool = False):
+    st = lib().mot_run_step(run, int(nsteps), _ptr(J_out), ctypes.byref(stats[0]) if stats is not None else None)
+    if st == MOT_ENOTCONV and allow_notconv:
+        return st
+    _check(st)
+    return st
+
+
+def mot_run_current_device(run) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().mot_run_current_device(run, ctypes.byref(p)))
+    return p.value
+
+
+def mot_run_step_index(run) -> int:
+    n = ctypes.c_int64()
+    _check(lib().mot_run_step_index(run, ctypes.byref(n)))
+    return n.value
+
+
+def mot_kernel_launches() -> int:
+    c = ctypes.c_uint64()
+    _check(lib().mot_kernel_launches(ctypes.byref(c)))
+    return c.value
+
+
+def default_options(**kw) -> mot_options:
+    """mot_options with the library defaults (tol 0 = per-precision default)."""
+    o = mot_options(0.0, 500, 1e-4, 6, 0.0, 0)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def mot_run_destroy(run):
+    lib().mot_run_destroy(run)

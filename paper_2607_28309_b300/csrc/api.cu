@@ -1,0 +1,1320 @@
+// api.cu -- C ABI of libmotjvie (declared in include/motjvie.h) and the host
+// orchestration of the device passes: Galerkin tables and spectra, the
+// matrix-free Z0 product (Eq. 11-12), the history right-hand side (Eq. 3),
+// the TFQMR solve of each step and the history ring.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/motjvie.h"
+#include "common.cuh"
+#include "fft.cuh"
+#include "galerkin.cuh"
+#include "krylov.cuh"
+#include "spectral.cuh"
+#include "tables.cuh"
+
+#include <atomic>
+
+namespace mot {
+static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_error(const std::string &msg) { g_err = msg; }
+const char *get_error() { return g_err.c_str(); }
+}  // namespace mot
+
+using namespace mot;
+
+#define MOT_FAIL(code, msg)          \
+    do {                             \
+        ::mot::set_error(msg);       \
+        return code;                 \
+    } while (0)
+
+#define MOT_CHECK_LAUNCH() MOT_CUDA_TRY(cudaGetLastError())
+
+#define MOT_TRY(...)                      \
+    do {                                  \
+        mot_status _s = (__VA_ARGS__);    \
+        if (_s != MOT_OK) return _s;      \
+    } while (0)
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+
+// ---------------------------------------------------------------- device memory
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+mot_status dalloc(DBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return MOT_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (bytes == 0) return MOT_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return MOT_ENOMEM;
+    }
+    b.bytes = bytes;
+    return MOT_OK;
+}
+
+void dfree(DBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int grid_for(long n, int threads = 256) {
+    long g = (n + threads - 1) / threads;
+    if (g > 148 * 16) g = 148 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- Gauss-Legendre (host)
+void gauss_legendre(int n, double *x, double *w) {
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int i = 0; i < n; ++i) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (int it = 0; it < 200; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (fabs(dz) <= 1e-16) break;
+        }
+        double p1 = 1.0, p2 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+constexpr int kGLN = 20;
+
+struct HostRule {
+    double x[kGLN], w[kGLN];
+    HostRule() { gauss_legendre(kGLN, x, w); }
+};
+const HostRule &host_rule() {
+    static HostRule r;
+    return r;
+}
+
+// ---------------------------------------------------------------- table items
+// sorted offsets (a <= b <= c) that fit the sorted extents S and the lags in
+// [k0, k1] whose causal support contains them, enumerated offset-major.
+struct ItemSet {
+    std::vector<TableItem> items;
+    std::vector<int> base, klo, cnt;  // per dense triple index (Rm+1)^3
+    int Rm = 0;
+};
+
+void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
+    int Rm = S[2];
+    is.Rm = Rm;
+    long n3 = (long)(Rm + 1) * (Rm + 1) * (Rm + 1);
+    is.base.assign(n3, -1);
+    is.klo.assign(n3, 0);
+    is.cnt.assign(n3, 0);
+    is.items.clear();
+    for (int a = 0; a <= S[0]; ++a)
+        for (int b = a; b <= S[1]; ++b)
+            for (int c = b; c <= S[2]; ++c) {
+                double lo = 0.0, hi = 0.0;
+                int d[3] = {a, b, c};
+                for (int i = 0; i < 3; ++i) {
+                    double l = std::max(d[i] - 1.0, 0.0), h = d[i] + 1.0;
+                    lo += l * l;
+                    hi += h * h;
+                }
+                lo = sqrt(lo);
+                hi = sqrt(hi);
+                int kb = std::max(k0, (int)floor(lo / rho - 1.0) - 1);
+                int ke = std::min(k1, (int)ceil(hi / rho + 2.0) + 1);
+                long key = ((long)a * (Rm + 1) + b) * (Rm + 1) + c;
+                int first = -1, count = 0, kfirst = 0;
+                for (int k = kb; k <= ke; ++k) {
+                    if (!gk::support(k, rho, a, b, c)) continue;
+                    if (first < 0) {
+                        first = (int)is.items.size();
+                        kfirst = k;
+                    }
+                    // lags of one offset form a contiguous range
+                    is.items.push_back({k, a, b, c});
+                    ++count;
+                }
+                if (first >= 0) {
+                    is.base[key] = first;
+                    is.klo[key] = kfirst;
+                    is.cnt[key] = count;
+                }
+            }
+}
+
+// per-lag map triple -> item (or -1), from the offset-major ranges
+void lag_map(const ItemSet &is, int k, std::vector<int> &map) {
+    map.assign(is.base.size(), -1);
+    for (size_t i = 0; i < is.base.size(); ++i)
+        if (is.base[i] >= 0 && k >= is.klo[i] && k < is.klo[i] + is.cnt[i]) map[i] = is.base[i] + (k - is.klo[i]);
+}
+
+int lag_reach(int k, double rho) { return gk::reach(k, rho); }
+
+// cos / sin coefficient tables of one axis: [K][R+1]
+void axis_coef(int M, int R, bool odd, std::vector<double> &cf) {
+    const double pi = 3.141592653589793238462643383279502884;
+    int K = M / 2 + 1;
+    cf.assign((size_t)K * (R + 1), 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int d = 0; d <= R; ++d) {
+            long m = ((long)k * d) % M;
+            double ang = 2.0 * pi * (double)m / (double)M;
+            double v;
+            if (odd) v = d == 0 ? 0.0 : 2.0 * sin(ang);
+            else v = d == 0 ? 1.0 : 2.0 * cos(ang);
+            cf[(size_t)k * (R + 1) + d] = v;
+        }
+}
+
+}  // namespace
+
+// ============================================================================
+// handles
+// ============================================================================
+struct AxisTw {
+    int M = 0;
+    FftPlan plan{};
+    DBuf tw64, tw32;
+};
+
+struct mot_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+};
+
+struct LagTable {
+    DBuf oct;       // FP64 octant [6][Rz+1][Ry+1][Rx+1]
+    int R[3] = {0, 0, 0};
+    bool ready = false;
+    bool override_ = false;
+};
+
+// event pairs around selected kernels (timing option)
+struct KTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> cls;
+    int used = 0;
+    void begin(cudaStream_t st, int c) {
+        if (!on) return;
+        if ((int)ev.size() < 2 * (used + 1)) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ev.push_back(a);
+            ev.push_back(b);
+        }
+        cls.resize(used + 1);
+        cls[used] = c;
+        cudaEventRecord(ev[2 * used], st);
+    }
+    void end(cudaStream_t st) {
+        if (!on) return;
+        cudaEventRecord(ev[2 * used + 1], st);
+        ++used;
+    }
+    float total(int c) {
+        float acc = 0.f;
+        for (int i = 0; i < used; ++i)
+            if (cls[i] == c) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+                acc += ms;
+            }
+        return acc;
+    }
+    void reset() { used = 0; }
+    ~KTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+enum { kTimeZGreen = 0, kTimeZHist = 1 };
+
+struct mot_problem {
+    mot_ctx *ctx = nullptr;
+    KTimer kt;
+    long mvp_count = 0;
+    int N[3];
+    double h, alpha, rho, dt;
+    int ell;
+    int M0[3], Mh[3], H0, Hh;
+    int K0[3], Kh[3];
+    int r0;
+    std::vector<double> eps_host;
+    DBuf eps;
+    std::vector<AxisTw *> tws;
+    std::vector<LagTable> lags;
+    DBuf L0_64, L0_32;  // [6][K0z][K0y][H0]
+    DBuf Lh_64, Lh_32;  // [ell+1][6][Khz][Khy][Hh]
+    bool hist64 = false, hist32 = false;
+    DBuf glx, glw;
+    // Z0 product workspace
+    DBuf wsA, wsB;
+    mot_options opt;
+};
+
+struct mot_run {
+    mot_problem *p = nullptr;
+    int B = 1;
+    int prec = MOT_FP64;
+    long n = 0;  // next step index
+    std::vector<PlaneWaveDev> pw_host;
+    DBuf pw, inc, J, b, r;
+    DBuf ring, wsAh, wsBh;
+    // Krylov vectors (type of the solve) and scratch
+    DBuf kv[10];
+    DBuf scal, part1, part2, part3, dots;
+    DBuf r32;  // mixed: residual in FP32 / correction
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+AxisTw *get_tw(mot_problem *p, int M) {
+    for (auto *t : p->tws)
+        if (t->M == M) return t;
+    AxisTw *t = new AxisTw();
+    t->M = M;
+    if (!make_plan(M, &t->plan)) {
+        delete t;
+        return nullptr;
+    }
+    std::vector<double2> h64(M);
+    std::vector<float2> h32(M);
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int m = 0; m < M; ++m) {
+        double a = -2.0 * pi * (double)m / (double)M;
+        h64[m] = make_double2(cos(a), sin(a));
+        h32[m] = make_float2((float)cos(a), (float)sin(a));
+    }
+    if (dalloc(t->tw64, sizeof(double2) * M) != MOT_OK || dalloc(t->tw32, sizeof(float2) * M) != MOT_OK) {
+        delete t;
+        return nullptr;
+    }
+    cudaMemcpy(t->tw64.p, h64.data(), sizeof(double2) * M, cudaMemcpyHostToDevice);
+    cudaMemcpy(t->tw32.p, h32.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+    p->tws.push_back(t);
+    return t;
+}
+
+template <typename T> const cplx<T> *twp(AxisTw *t);
+template <> const cplx<double> *twp<double>(AxisTw *t) { return (const double2 *)t->tw64.p; }
+template <> const cplx<float> *twp<float>(AxisTw *t) { return (const float2 *)t->tw32.p; }
+
+const size_t kSmemMax = 200 * 1024;
+
+// raise the dynamic shared-memory limit of one kernel, once per kernel
+template <auto Kern> mot_status allow_smem() {
+    static bool done = false;
+    if (!done) {
+        MOT_CUDA_TRY(cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+        done = true;
+    }
+    return MOT_OK;
+}
+
+// ---------------------------------------------------------------- pass launchers
+template <typename TI, typename T>
+mot_status launch_x_forward(const TI *x, cplx<T> *out, long nrows, int Nx, int H, AxisTw *tw, cudaStream_t st) {
+    const int M = tw->M;
+    int pairs = (int)std::min<long>(8, std::max<long>(1, ((long)(48 * 1024) / ((long)M * sizeof(cplx<T>)) - 1) / 2));
+    size_t smem = (size_t)(2 * pairs + 1) * M * sizeof(cplx<T>);
+    MOT_TRY(allow_smem<k_x_forward<TI, T>>());
+    long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
+    count_launch();
+    k_x_forward<TI, T><<<(unsigned)grid, 256, smem, st>>>(x, out, nrows, Nx, H, tw->plan, twp<T>(tw), pairs);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+template <typename T> int tile_width(int M, int comps) {
+    int tx = sizeof(T) == 4 ? 16 : 8;
+    while (tx > 1 && (size_t)(2 * comps * M * tx + M) * sizeof(cplx<T>) > kSmemMax) tx /= 2;
+    return tx;
+}
+
+template <typename T, int S>
+mot_status launch_axis(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int O1, int O2,
+                       long is1, long is2, long ias, long os1, long os2, long oas, cudaStream_t st) {
+    const int M = tw->M;
+    int tx = tile_width<T>(M, 1);
+    size_t smem = (size_t)(2 * M * tx + M) * sizeof(cplx<T>);
+    MOT_TRY(allow_smem<k_axis<T, S>>());
+    dim3 grid((H + tx - 1) / tx, (unsigned)(O1 * O2));
+    count_launch();
+    k_axis<T, S><<<grid, 256, smem, st>>>(in, out, tw->plan, twp<T>(tw), H, tx, Lin, Lout, O2, is1, is2, ias, os1,
+                                          os2, oas);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+template <typename T, class Epi>
+mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw *tw, Epi epi, cudaStream_t st) {
+    const int M = tw->M;
+    int pairs = (int)std::min<long>(8, std::max<long>(1, (long)(64 * 1024) / ((long)(2 * H + 2 * M + M) * sizeof(cplx<T>))));
+    size_t smem = (size_t)(2 * pairs * H + 2 * pairs * M + M) * sizeof(cplx<T>);
+    MOT_TRY(allow_smem<k_x_inverse<T, Epi>>());
+    long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
+    count_launch();
+    k_x_inverse<T, Epi><<<(unsigned)grid, 256, smem, st>>>(in, nrows, Nx, H, tw->plan, twp<T>(tw), pairs, epi);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+template <typename T> const T *L0_of(mot_problem *p);
+template <> const double *L0_of<double>(mot_problem *p) { return (const double *)p->L0_64.p; }
+template <> const float *L0_of<float>(mot_problem *p) { return (const float *)p->L0_32.p; }
+template <typename T> const T *Lh_of(mot_problem *p);
+template <> const double *Lh_of<double>(mot_problem *p) { return (const double *)p->Lh_64.p; }
+template <> const float *Lh_of<float>(mot_problem *p) { return (const float *)p->Lh_32.p; }
+
+// y = Z0 x (or the residual epilogue) with the FFT in precision T.
+// wsA: nrhs*3*Nz*Ny*H0 complex, wsB: nrhs*3*Nz*M0y*H0 complex.
+template <typename TI, typename T, class Epi>
+mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *wsB, Epi epi, cudaStream_t st) {
+    const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
+    const int H = p->H0, My = p->M0[1];
+    AxisTw *tx = get_tw(p, p->M0[0]), *ty = get_tw(p, p->M0[1]), *tz = get_tw(p, p->M0[2]);
+    if (!tx || !ty || !tz) MOT_FAIL(MOT_EUNSUPPORTED, "FFT size with a prime factor above 5");
+    using C = cplx<T>;
+    C *A = (C *)wsA, *Bf = (C *)wsB;
+    const long nrows = (long)nrhs * 3 * Nz * Ny;
+    const int planes = nrhs * 3 * Nz;
+    MOT_TRY(launch_x_forward<TI, T>(x, A, nrows, Nx, H, tx, st));
+    MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    {
+        int tw = tile_width<T>(p->M0[2], 3);
+        size_t smem = (size_t)(6 * p->M0[2] * tw + p->M0[2]) * sizeof(C);
+        MOT_TRY(allow_smem<k_z_green<T>>());
+        Octant oc = {p->M0[2], p->M0[1], p->K0[2], p->K0[1], H};
+        dim3 grid((H + tw - 1) / tw, (unsigned)(nrhs * My));
+        p->kt.begin(st, kTimeZGreen);
+        count_launch();
+        k_z_green<T><<<grid, 256, smem, st>>>(Bf, L0_of<T>(p), tz->plan, twp<T>(tz), Nz, My, H, tw, oc);
+        p->kt.end(st);
+        p->mvp_count += 1;
+        MOT_CHECK_LAUNCH();
+    }
+    MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+    MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
+    return MOT_OK;
+}
+
+size_t z0_ws_bytes(const mot_problem *p, int nrhs, size_t csize, size_t *a, size_t *b) {
+    *a = (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->H0 * csize;
+    *b = (size_t)nrhs * 3 * p->N[2] * p->M0[1] * p->H0 * csize;
+    return *a + *b;
+}
+
+// ---------------------------------------------------------------- tables
+// octant of lag k from the library's own quadrature (device), into lags[k]
+mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
+    cudaStream_t st = p->ctx->stream;
+    int ext[3];
+    for (int i = 0; i < 3; ++i) ext[i] = p->N[i] - 1;
+    int S[3] = {ext[0], ext[1], ext[2]};
+    std::sort(S, S + 3);
+    int rmax = lag_reach(k1, p->rho);
+    for (int i = 0; i < 3; ++i) S[i] = std::min(S[i], rmax);
+    ItemSet is;
+    build_items(p->rho, S, k0, k1, is);
+    const int nit = (int)is.items.size();
+    DBuf ditems, dA, dmap;
+    MOT_TRY(dalloc(ditems, sizeof(TableItem) * std::max(1, nit)));
+    MOT_TRY(dalloc(dA, sizeof(double) * 6 * std::max(1, nit)));
+    MOT_TRY(dalloc(dmap, sizeof(int) * is.base.size()));
+    MOT_CUDA_TRY(cudaMemcpyAsync(ditems.p, is.items.data(), sizeof(TableItem) * nit, cudaMemcpyHostToDevice, st));
+    if (nit > 0) {
+        count_launch();
+        k_galerkin_items<<<(nit + 63) / 64, 64, 0, st>>>((const TableItem *)ditems.p, nit, p->rho,
+                                                         (const double *)p->glx.p, (const double *)p->glw.p, kGLN,
+                                                         (double *)dA.p);
+        MOT_CHECK_LAUNCH();
+    }
+    std::vector<int> map;
+    for (int k = k0; k <= k1; ++k) {
+        LagTable &L = p->lags[k];
+        if (L.override_) continue;
+        int rk = lag_reach(k, p->rho);
+        for (int i = 0; i < 3; ++i) L.R[i] = std::min(rk, ext[i]);
+        long n = (long)(L.R[0] + 1) * (L.R[1] + 1) * (L.R[2] + 1);
+        MOT_TRY(dalloc(L.oct, sizeof(double) * 6 * n));
+        lag_map(is, k, map);
+        MOT_CUDA_TRY(cudaMemcpyAsync(dmap.p, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, st));
+        count_launch();
+        k_expand_octant<<<grid_for(n), 256, 0, st>>>((const double *)dA.p, (const int *)dmap.p, is.Rm, L.R[0],
+                                                     L.R[1], L.R[2], (double *)L.oct.p);
+        MOT_CHECK_LAUNCH();
+        // map is reused by the next lag: wait for the copy before host reuse
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+        L.ready = true;
+    }
+    MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(ditems);
+    dfree(dA);
+    dfree(dmap);
+    return MOT_OK;
+}
+
+// Lambda of one lag octant on grid M (K = M/2+1), FP64, into dst64 [6][Kz][Ky][Kx]
+mot_status lag_spectrum(mot_problem *p, const LagTable &L, const int M[3], double *dst64) {
+    cudaStream_t st = p->ctx->stream;
+    int K[3] = {M[0] / 2 + 1, M[1] / 2 + 1, M[2] / 2 + 1};
+    int R1[3] = {L.R[0] + 1, L.R[1] + 1, L.R[2] + 1};
+    std::vector<double> ce[3], co[3];
+    for (int a = 0; a < 3; ++a) {
+        axis_coef(M[a], L.R[a], false, ce[a]);
+        axis_coef(M[a], L.R[a], true, co[a]);
+    }
+    DBuf dce[3], dco[3], t1, t2;
+    for (int a = 0; a < 3; ++a) {
+        MOT_TRY(dalloc(dce[a], sizeof(double) * ce[a].size()));
+        MOT_TRY(dalloc(dco[a], sizeof(double) * co[a].size()));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dce[a].p, ce[a].data(), sizeof(double) * ce[a].size(), cudaMemcpyHostToDevice, st));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dco[a].p, co[a].data(), sizeof(double) * co[a].size(), cudaMemcpyHostToDevice, st));
+    }
+    MOT_TRY(dalloc(t1, sizeof(double) * (size_t)R1[2] * R1[1] * K[0]));
+    MOT_TRY(dalloc(t2, sizeof(double) * (size_t)R1[2] * K[1] * K[0]));
+    const long on = (long)R1[0] * R1[1] * R1[2];
+    const long kn = (long)K[0] * K[1] * K[2];
+    const double scale = 1.0 / ((double)M[0] * M[1] * M[2]);
+    // parity per component (x, y, z): 1 = odd
+    const int par[6][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    for (int c = 0; c < 6; ++c) {
+        const double *src = (const double *)L.oct.p + c * on;
+        const double *cx = (const double *)(par[c][0] ? dco[0].p : dce[0].p);
+        const double *cy = (const double *)(par[c][1] ? dco[1].p : dce[1].p);
+        const double *cz = (const double *)(par[c][2] ? dco[2].p : dce[2].p);
+        long n1 = (long)R1[2] * R1[1] * K[0];
+        count_launch();
+        k_axis_sum<<<grid_for(n1), 256, 0, st>>>(src, (double *)t1.p, cx, R1[2] * R1[1], R1[0], K[0], 1);
+        long n2 = (long)R1[2] * K[1] * K[0];
+        count_launch();
+        k_axis_sum<<<grid_for(n2), 256, 0, st>>>((const double *)t1.p, (double *)t2.p, cy, R1[2], R1[1], K[1], K[0]);
+        count_launch();
+        k_axis_sum<<<grid_for(kn), 256, 0, st>>>((const double *)t2.p, dst64 + c * kn, cz, 1, R1[2], K[2],
+                                                 K[1] * K[0]);
+        MOT_CHECK_LAUNCH();
+        double s = c >= 3 ? -scale : scale;
+        count_launch();
+        k_scale_store<double><<<grid_for(kn), 256, 0, st>>>(dst64 + c * kn, dst64 + c * kn, kn, s);
+        MOT_CHECK_LAUNCH();
+    }
+    MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int a = 0; a < 3; ++a) {
+        dfree(dce[a]);
+        dfree(dco[a]);
+    }
+    dfree(t1);
+    dfree(t2);
+    return MOT_OK;
+}
+
+mot_status build_Z0_spectrum(mot_problem *p) {
+    long kn = (long)p->K0[0] * p->K0[1] * p->K0[2];
+    MOT_TRY(dalloc(p->L0_64, sizeof(double) * 6 * kn));
+    MOT_TRY(dalloc(p->L0_32, sizeof(float) * 6 * kn));
+    MOT_TRY(lag_spectrum(p, p->lags[0], p->M0, (double *)p->L0_64.p));
+    count_launch();
+    k_scale_store<float><<<grid_for(6 * kn), 256, 0, p->ctx->stream>>>((const double *)p->L0_64.p,
+                                                                       (float *)p->L0_32.p, 6 * kn, 1.0);
+    MOT_CHECK_LAUNCH();
+    MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+    return MOT_OK;
+}
+
+mot_status build_history_spectra(mot_problem *p, bool want64, bool want32) {
+    if ((!want64 || p->hist64) && (!want32 || p->hist32)) return MOT_OK;
+    bool need_oct = false;
+    for (int k = 1; k <= p->ell; ++k)
+        if (!p->lags[k].ready) need_oct = true;
+    if (need_oct) MOT_TRY(compute_lag_octants(p, 1, p->ell));
+    long kn = (long)p->Kh[0] * p->Kh[1] * p->Kh[2];
+    size_t per = 6 * (size_t)kn;
+    DBuf tmp;
+    MOT_TRY(dalloc(tmp, sizeof(double) * per));
+    if (want64 && !p->hist64) {
+        MOT_TRY(dalloc(p->Lh_64, sizeof(double) * per * (p->ell + 1)));
+        MOT_CUDA_TRY(cudaMemsetAsync(p->Lh_64.p, 0, sizeof(double) * per, p->ctx->stream));
+    }
+    if (want32 && !p->hist32) {
+        MOT_TRY(dalloc(p->Lh_32, sizeof(float) * per * (p->ell + 1)));
+        MOT_CUDA_TRY(cudaMemsetAsync(p->Lh_32.p, 0, sizeof(float) * per, p->ctx->stream));
+    }
+    for (int k = 1; k <= p->ell; ++k) {
+        double *dst = (want64 && !p->hist64) ? (double *)p->Lh_64.p + per * k : (double *)tmp.p;
+        MOT_TRY(lag_spectrum(p, p->lags[k], p->Mh, dst));
+        if (want32 && !p->hist32) {
+            count_launch();
+            k_scale_store<float><<<grid_for(per), 256, 0, p->ctx->stream>>>(dst, (float *)p->Lh_32.p + per * k, per,
+                                                                            1.0);
+            MOT_CHECK_LAUNCH();
+        }
+    }
+    MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+    dfree(tmp);
+    if (want64) p->hist64 = true;
+    if (want32) p->hist32 = true;
+    return MOT_OK;
+}
+
+// host: octant -> full table with reflection signs
+void octant_to_full(const std::vector<double> &oct, const int R[3], double *g) {
+    int nx = 2 * R[0] + 1, ny = 2 * R[1] + 1, nz = 2 * R[2] + 1;
+    long n3 = (long)nx * ny * nz;
+    long on = (long)(R[0] + 1) * (R[1] + 1) * (R[2] + 1);
+    const int pp[6] = {0, 1, 2, 0, 0, 1}, qq[6] = {0, 1, 2, 1, 2, 2};
+    for (int dz = -R[2]; dz <= R[2]; ++dz)
+        for (int dy = -R[1]; dy <= R[1]; ++dy)
+            for (int dx = -R[0]; dx <= R[0]; ++dx) {
+                int d[3] = {dx, dy, dz};
+                long oi = ((long)abs(dz) * (R[1] + 1) + abs(dy)) * (R[0] + 1) + abs(dx);
+                long fi = ((long)(dz + R[2]) * ny + (dy + R[1])) * nx + (dx + R[0]);
+                for (int c = 0; c < 6; ++c) {
+                    double s = 1.0;
+                    if (c >= 3) s = (d[pp[c]] < 0 ? -1.0 : 1.0) * (d[qq[c]] < 0 ? -1.0 : 1.0);
+                    g[c * n3 + fi] = s * oct[c * on + oi];
+                }
+            }
+}
+
+bool finite_all(const double *a, long n) {
+    for (long i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char *mot_last_error(void) { return get_error(); }
+
+mot_status mot_ctx_create(int device, void *cuda_stream, mot_ctx **out) {
+    if (!out) MOT_FAIL(MOT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        MOT_FAIL(MOT_ECUDA, std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= ndev) MOT_FAIL(MOT_EINVAL, "device index out of range");
+    MOT_CUDA_TRY(cudaSetDevice(device));
+    mot_ctx *c = new mot_ctx();
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e2 = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e2 != cudaSuccess) {
+            delete c;
+            MOT_FAIL(MOT_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e2));
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return MOT_OK;
+}
+
+void mot_ctx_destroy(mot_ctx *c) {
+    if (!c) return;
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+mot_status mot_table_host(double rho, int lag, const int32_t R[3], double *g_out) {
+    if (!(rho > 0.0) || !std::isfinite(rho)) MOT_FAIL(MOT_EINVAL, "rho must be finite and > 0");
+    if (lag < 0) MOT_FAIL(MOT_EINVAL, "lag < 0");
+    if (!R || !g_out) MOT_FAIL(MOT_EINVAL, "R or g_out is NULL");
+    for (int i = 0; i < 3; ++i)
+        if (R[i] < 0 || R[i] > 4096) MOT_FAIL(MOT_EINVAL, "table extent out of range");
+    const HostRule &hr = host_rule();
+    gk::Rule q = {hr.x, hr.w, kGLN};
+    int S[3] = {R[0], R[1], R[2]};
+    std::sort(S, S + 3);
+    ItemSet is;
+    build_items(rho, S, lag, lag, is);
+    std::vector<double> A6(6 * std::max<size_t>(1, is.items.size()));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long i = 0; i < (long)is.items.size(); ++i) {
+        const TableItem &it = is.items[i];
+        gk::galerkin_A(q, it.k, rho, it.a, it.b, it.c, &A6[6 * i]);
+    }
+    std::vector<int> map;
+    lag_map(is, lag, map);
+    int Ri[3] = {R[0], R[1], R[2]};
+    long on = (long)(Ri[0] + 1) * (Ri[1] + 1) * (Ri[2] + 1);
+    std::vector<double> oct(6 * on);
+    for (int dz = 0; dz <= Ri[2]; ++dz)
+        for (int dy = 0; dy <= Ri[1]; ++dy)
+            for (int dx = 0; dx <= Ri[0]; ++dx) {
+                double g6[6];
+                expand_one(A6.data(), map.data(), is.Rm, dx, dy, dz, g6);
+                long oi = ((long)dz * (Ri[1] + 1) + dy) * (Ri[0] + 1) + dx;
+                for (int c = 0; c < 6; ++c) oct[c * on + oi] = g6[c];
+            }
+    octant_to_full(oct, Ri, g_out);
+    return MOT_OK;
+}
+
+mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const double *eps_r, double alpha,
+                              const mot_options *opt, mot_problem **out) {
+    if (!ctx || !n || !eps_r || !out) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    *out = nullptr;
+    for (int i = 0; i < 3; ++i)
+        if (n[i] < 1 || n[i] > 4096) MOT_FAIL(MOT_EINVAL, "grid size out of range [1, 4096]");
+    if (!(h > 0.0) || !std::isfinite(h)) MOT_FAIL(MOT_EINVAL, "h must be finite and > 0");
+    if (!(alpha > 0.0) || !std::isfinite(alpha) || alpha > 1e4) MOT_FAIL(MOT_EINVAL, "alpha must be in (0, 1e4]");
+    long nv = (long)n[0] * n[1] * n[2];
+    for (long i = 0; i < nv; ++i)
+        if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
+    mot_options o = {0.0, 500, 1e-4, 6, 0.0, 0};
+    if (opt) o = *opt;
+    if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
+    if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
+    MOT_CUDA_TRY(cudaSetDevice(ctx->device));
+    mot_problem *p = new mot_problem();
+    p->ctx = ctx;
+    p->opt = o;
+    for (int i = 0; i < 3; ++i) p->N[i] = n[i];
+    p->h = h;
+    p->alpha = alpha;
+    p->rho = alpha / sqrt(3.0);
+    p->dt = alpha * h / (kC0 * sqrt(3.0));
+    double rmax = sqrt((double)n[0] * n[0] + (double)n[1] * n[1] + (double)n[2] * n[2]);
+    p->ell = (int)ceil(rmax / p->rho - 1e-12) + 2;
+    p->r0 = lag_reach(0, p->rho);
+    for (int i = 0; i < 3; ++i) {
+        int r = std::min(p->r0, n[i] - 1);
+        p->M0[i] = smooth235(n[i] + r);
+        p->Mh[i] = smooth235(std::max(1, 2 * n[i] - 1));
+        p->K0[i] = p->M0[i] / 2 + 1;
+        p->Kh[i] = p->Mh[i] / 2 + 1;
+    }
+    p->H0 = p->K0[0];
+    p->Hh = p->Kh[0];
+    p->eps_host.assign(eps_r, eps_r + nv);
+    p->lags.resize(p->ell + 1);
+    mot_status s;
+    auto fail = [&](mot_status st) {
+        mot_problem_destroy(p);
+        return st;
+    };
+    if ((s = dalloc(p->eps, sizeof(double) * nv)) != MOT_OK) return fail(s);
+    if (cudaMemcpyAsync(p->eps.p, eps_r, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return fail(MOT_ECUDA);
+    {
+        const HostRule &hr = host_rule();
+        if ((s = dalloc(p->glx, sizeof(double) * kGLN)) != MOT_OK) return fail(s);
+        if ((s = dalloc(p->glw, sizeof(double) * kGLN)) != MOT_OK) return fail(s);
+        cudaMemcpyAsync(p->glx.p, hr.x, sizeof(double) * kGLN, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(p->glw.p, hr.w, sizeof(double) * kGLN, cudaMemcpyHostToDevice, ctx->stream);
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!get_tw(p, p->M0[i]) || !get_tw(p, p->Mh[i])) {
+            set_error("FFT twiddle setup failed");
+            return fail(MOT_ECUDA);
+        }
+    if ((s = compute_lag_octants(p, 0, 0)) != MOT_OK) return fail(s);
+    if ((s = build_Z0_spectrum(p)) != MOT_OK) return fail(s);
+    *out = p;
+    return MOT_OK;
+}
+
+mot_status mot_problem_info_get(const mot_problem *p, mot_problem_info *info) {
+    if (!p || !info) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    for (int i = 0; i < 3; ++i) {
+        info->n[i] = p->N[i];
+        info->M0[i] = p->M0[i];
+        info->Mh[i] = p->Mh[i];
+    }
+    info->r0 = p->r0;
+    info->ell = p->ell;
+    info->rho = p->rho;
+    info->dt = p->dt;
+    return MOT_OK;
+}
+
+void mot_problem_destroy(mot_problem *p) {
+    if (!p) return;
+    cudaSetDevice(p->ctx->device);
+    cudaStreamSynchronize(p->ctx->stream);
+    dfree(p->eps);
+    for (auto *t : p->tws) {
+        dfree(t->tw64);
+        dfree(t->tw32);
+        delete t;
+    }
+    for (auto &L : p->lags) dfree(L.oct);
+    dfree(p->L0_64);
+    dfree(p->L0_32);
+    dfree(p->Lh_64);
+    dfree(p->Lh_32);
+    dfree(p->glx);
+    dfree(p->glw);
+    dfree(p->wsA);
+    dfree(p->wsB);
+    delete p;
+}
+
+mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
+    if (!p || !x_dev || !y_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
+    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    size_t a, b;
+    z0_ws_bytes(p, nrhs, dtype == MOT_F64 ? sizeof(double2) : sizeof(float2), &a, &b);
+    MOT_TRY(dalloc(p->wsA, a));
+    MOT_TRY(dalloc(p->wsB, b));
+    const long pr = (long)p->N[2] * p->N[1];
+    if (dtype == MOT_F64) {
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+        return z0_product<double, double>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+    }
+    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+    return z0_product<float, float>(p, (const float *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+}
+
+mot_status mot_kernel_table(mot_problem *p, int lag, double *g_out, int32_t R_out[3]) {
+    if (!p || !R_out) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (lag < 0 || lag > p->ell) MOT_FAIL(MOT_EINVAL, "lag out of range [0, ell]");
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    LagTable &L = p->lags[lag];
+    if (!L.ready) MOT_TRY(compute_lag_octants(p, lag, lag));
+    for (int i = 0; i < 3; ++i) R_out[i] = L.R[i];
+    if (!g_out) return MOT_OK;
+    long on = (long)(L.R[0] + 1) * (L.R[1] + 1) * (L.R[2] + 1);
+    std::vector<double> oct(6 * on);
+    MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+    MOT_CUDA_TRY(cudaMemcpy(oct.data(), L.oct.p, sizeof(double) * 6 * on, cudaMemcpyDeviceToHost));
+    octant_to_full(oct, L.R, g_out);
+    return MOT_OK;
+}
+
+mot_status mot_set_kernel_table(mot_problem *p, int lag, const double *g, const int32_t R[3]) {
+    if (!p || !g || !R) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (lag < 0 || lag > p->ell) MOT_FAIL(MOT_EINVAL, "lag out of range [0, ell]");
+    if (lag >= 1 && (p->hist64 || p->hist32)) MOT_FAIL(MOT_EINVAL, "history tables already in use; set them before mot_run_create");
+    for (int i = 0; i < 3; ++i)
+        if (R[i] < 0 || R[i] > 4096) MOT_FAIL(MOT_EINVAL, "table extent out of range");
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    int nx = 2 * R[0] + 1, ny = 2 * R[1] + 1, nz = 2 * R[2] + 1;
+    long n3 = (long)nx * ny * nz;
+    if (!finite_all(g, 6 * n3)) MOT_FAIL(MOT_EINVAL, "table has non-finite entries");
+    LagTable &L = p->lags[lag];
+    int Rc[3];
+    for (int i = 0; i < 3; ++i) Rc[i] = std::min<int>(R[i], p->N[i] - 1);
+    if (lag == 0)
+        for (int i = 0; i < 3; ++i)
+            if (Rc[i] > p->M0[i] - p->N[i]) MOT_FAIL(MOT_EINVAL, "lag-0 table reaches beyond the padded grid M0 - N");
+    long on = (long)(Rc[0] + 1) * (Rc[1] + 1) * (Rc[2] + 1);
+    std::vector<double> oct(6 * on);
+    for (int c = 0; c < 6; ++c)
+        for (int dz = 0; dz <= Rc[2]; ++dz)
+            for (int dy = 0; dy <= Rc[1]; ++dy)
+                for (int dx = 0; dx <= Rc[0]; ++dx) {
+                    long fi = ((long)(dz + R[2]) * ny + (dy + R[1])) * nx + (dx + R[0]);
+                    oct[c * on + ((long)dz * (Rc[1] + 1) + dy) * (Rc[0] + 1) + dx] = g[c * n3 + fi];
+                }
+    MOT_TRY(dalloc(L.oct, sizeof(double) * 6 * on));
+    MOT_CUDA_TRY(cudaMemcpy(L.oct.p, oct.data(), sizeof(double) * 6 * on, cudaMemcpyHostToDevice));
+    for (int i = 0; i < 3; ++i) L.R[i] = Rc[i];
+    L.ready = true;
+    L.override_ = true;
+    if (lag == 0) MOT_TRY(build_Z0_spectrum(p));
+    return MOT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// marching runs
+// ============================================================================
+namespace {
+
+// Krylov vector slots
+enum { kRS = 0, kW, kY1, kY2, kV, kD, kAY1, kAY2, kX, kB };
+
+template <typename V> struct KrylovView {
+    V *v[10];
+    TfqmrScal *sc;
+    double *p1, *p2, *p3;
+};
+
+template <typename V> KrylovView<V> kview(mot_run *r) {
+    KrylovView<V> k;
+    for (int i = 0; i < 10; ++i) k.v[i] = (V *)r->kv[i].p;
+    k.sc = (TfqmrScal *)r->scal.p;
+    k.p1 = (double *)r->part1.p;
+    k.p2 = (double *)r->part2.p;
+    k.p3 = (double *)r->part3.p;
+    return k;
+}
+
+template <typename V> mot_status mvp(mot_run *r, const V *x, V *y) {
+    mot_problem *p = r->p;
+    EpiZ0<V, V> e = {x, y, (const double *)p->eps.p, (long)p->N[2] * p->N[1], p->N[0]};
+    return z0_product<V, V>(p, x, r->B, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+}
+
+template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ a, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        w[i] = b[i] - a[i];
+}
+
+// TFQMR on Z0 y = rhs for the batch; x holds x0 on entry (x0 = 0 if zero_x0)
+// and the solution on exit.  Returns iterations (max over the batch).
+template <typename V>
+mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
+                 bool *conv_out) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const int B = r->B;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    const long n = L * B;
+    KrylovView<V> k = kview<V>(r);
+    dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    // r0 = rhs - A x0  (into w)
+    if (zero_x0) {
+        MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
+        MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        MOT_TRY(mvp<V>(r, x, k.v[kAY1]));
+        count_launch();
+        k_sub<V><<<grid_for(n), 256, 0, st>>>(k.v[kW], rhs, k.v[kAY1], n);
+        MOT_CHECK_LAUNCH();
+    }
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kY1], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kRS], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    MOT_CUDA_TRY(cudaMemsetAsync(k.v[kD], 0, sizeof(V) * n, st));
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kW], k.v[kW], L, k.p1);
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(rhs, rhs, L, k.p2);
+    count_launch();
+    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol);
+    count_launch();
+    k_tfqmr_zero_rhs<V><<<gv, 256, 0, st>>>(x, k.sc, L);
+    count_launch();
+    k_tfqmr_zero_done<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B);
+    MOT_CHECK_LAUNCH();
+    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1]));
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kV], k.v[kAY1], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kRS], k.v[kV], L, k.p3);
+    MOT_CHECK_LAUNCH();
+    std::vector<TfqmrScal> hs(B);
+    int it = 0;
+    bool all = false;
+    for (it = 0; it < maxit; ++it) {
+        MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), k.sc, sizeof(TfqmrScal) * B, cudaMemcpyDeviceToHost, st));
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+        all = true;
+        for (int b = 0; b < B; ++b)
+            if (hs[b].conv == 0) all = false;
+        if (all) break;
+        count_launch();
+        k_tfqmr_alpha<<<B, 32, 0, st>>>(k.sc, k.p3);
+        count_launch();
+        k_tfqmr_y2<V><<<gv, 256, 0, st>>>(k.v[kY2], k.v[kY1], k.v[kV], k.sc, L);
+        count_launch();
+        k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY1], k.v[kAY1], k.v[kRS], k.sc, L,
+                                                         k.p1, nullptr);
+        count_launch();
+        k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
+        MOT_CHECK_LAUNCH();
+        MOT_TRY(mvp<V>(r, k.v[kY2], k.v[kAY2]));
+        count_launch();
+        k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L,
+                                                         k.p1, k.p2);
+        count_launch();
+        k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
+        count_launch();
+        k_tfqmr_beta<<<B, 32, 0, st>>>(k.sc, k.p2);
+        count_launch();
+        k_tfqmr_y1<V><<<gv, 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
+        MOT_CHECK_LAUNCH();
+        MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1]));
+        count_launch();
+        k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3);
+        MOT_CHECK_LAUNCH();
+    }
+    count_launch();
+    k_tfqmr_flush<V, V><<<gv, 256, 0, st>>>(x, k.v[kD], k.sc, L, 1);
+    count_launch();
+    k_tfqmr_settle<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B, 1);
+    MOT_CHECK_LAUNCH();
+    MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), k.sc, sizeof(TfqmrScal) * B, cudaMemcpyDeviceToHost, st));
+    MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    int mx = 0;
+    bool conv = true;
+    for (int b = 0; b < B; ++b) {
+        mx = std::max(mx, (hs[b].m + 1) / 2);
+        if (hs[b].conv == 0) conv = false;
+    }
+    *iters_out = mx;
+    *conv_out = conv;
+    return MOT_OK;
+}
+
+template <typename T> void *ring_slot(mot_run *r, long s) {
+    mot_problem *p = r->p;
+    size_t slot = (size_t)r->B * 3 * p->Mh[2] * p->Mh[1] * p->Hh * sizeof(cplx<T>);
+    return (char *)r->ring.p + slot * s;
+}
+
+// Jhat_n = F_Mh{J_n} into ring slot n mod ell
+template <typename T> mot_status ring_push(mot_run *r) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
+    const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
+    AxisTw *tx = get_tw(p, p->Mh[0]), *ty = get_tw(p, My), *tz = get_tw(p, Mz);
+    using C = cplx<T>;
+    C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
+    const long nrows = (long)r->B * 3 * Nz * Ny;
+    MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
+    MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    C *slot = (C *)ring_slot<T>(r, r->n % p->ell);
+    MOT_TRY((launch_axis<T, -1>(Bf, slot, tz, H, Nz, Mz, r->B * 3, My, (long)Nz * My * H, H, (long)My * H,
+                                (long)Mz * My * H, H, (long)My * H, st)));
+    return MOT_OK;
+}
+
+// b_n = E^i_n - eps T(dt) J_{n-1} + (eps - 1) sum_k G_k J_{n-k}
+template <typename T> mot_status history_rhs(mot_run *r) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
+    const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
+    const long nv = (long)Nx * Ny * Nz;
+    AxisTw *tx = get_tw(p, p->Mh[0]), *ty = get_tw(p, My), *tz = get_tw(p, Mz);
+    using C = cplx<T>;
+    C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
+    const double t = (double)r->n * p->dt;
+    count_launch();
+    k_incident<<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
+                                                   (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
+    MOT_CHECK_LAUNCH();
+    const int kmax = (int)std::min<long>(r->n, p->ell);
+    {
+        int tw = tile_width<T>(Mz, 3);
+        size_t smem = (size_t)(6 * Mz * tw + Mz) * sizeof(C);
+        MOT_TRY(allow_smem<k_z_history<T>>());
+        Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
+        dim3 grid((H + tw - 1) / tw, (unsigned)(r->B * My));
+        p->kt.begin(st, kTimeZHist);
+        count_launch();
+        k_z_history<T><<<grid, 256, smem, st>>>((const C *)r->ring.p, Lh_of<T>(p), Bf, tz->plan, twp<T>(tz), Nz, My,
+                                                H, tw, oc, r->B, p->ell, r->n, kmax);
+        p->kt.end(st);
+        MOT_CHECK_LAUNCH();
+    }
+    MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+    EpiHistory e;
+    e.inc = (const double *)r->inc.p;
+    e.pol = nullptr;  // set below
+    e.Jprev = r->n > 0 ? (const double *)r->J.p : nullptr;
+    e.out = (double *)r->b.p;
+    e.eps = (const double *)p->eps.p;
+    e.plane_rows = (long)Nz * Ny;
+    e.Nx = Nx;
+    e.nvox = nv;
+    e.pol = (const double *)((const char *)r->pw.p + r->B * sizeof(PlaneWaveDev));
+    MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
+    return MOT_OK;
+}
+
+mot_status norms(mot_run *r, const double *v, double *out_host) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    count_launch();
+    k_dot_part<double, double><<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, v, L, (double *)r->part1.p);
+    count_launch();
+    k_finish_dot<<<r->B, 32, 0, st>>>((const double *)r->part1.p, (double *)r->dots.p);
+    MOT_CHECK_LAUNCH();
+    MOT_CUDA_TRY(cudaMemcpyAsync(out_host, r->dots.p, sizeof(double) * r->B, cudaMemcpyDeviceToHost, st));
+    MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int b = 0; b < r->B; ++b) out_host[b] = sqrt(out_host[b]);
+    return MOT_OK;
+}
+
+// one MOT step (Eq. 3)
+mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    const long n = L * r->B;
+    const long pr = (long)p->N[2] * p->N[1];
+    const bool mixed = r->prec == MOT_MIXED;
+    p->kt.on = p->opt.timing != 0;
+    p->kt.reset();
+    const long mvp0 = p->mvp_count;
+    cudaEventRecord(r->ev[0], st);
+    if (mixed) MOT_TRY(history_rhs<float>(r));
+    else MOT_TRY(history_rhs<double>(r));
+    cudaEventRecord(r->ev[1], st);
+    int iters = 0, sweeps = 0;
+    bool conv = true;
+    std::vector<double> bn(r->B), rn(r->B);
+    MOT_TRY(norms(r, (const double *)r->b.p, bn.data()));
+    double relres = 0.0;
+    if (!mixed) {
+        const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
+        int it;
+        bool c;
+        MOT_TRY(tfqmr<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, &it, &c));
+        iters = it;
+        conv = c;
+        sweeps = 1;
+        EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p, (const double *)p->eps.p, pr,
+                         p->N[0]};
+        MOT_TRY((z0_product<double, double>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+        MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
+    } else {
+        const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
+        float *r32 = (float *)r->r32.p;
+        float *c32 = r32 + n;
+        for (sweeps = 0; sweeps <= p->opt.max_refine; ++sweeps) {
+            EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
+                             (const double *)p->eps.p, pr, p->N[0]};
+            MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
+            bool done = true;
+            for (int b = 0; b < r->B; ++b)
+                if (rn[b] > tol * bn[b]) done = false;
+            if (done || sweeps == p->opt.max_refine) break;
+            count_launch();
+            k_convert<float, double><<<grid_for(n), 256, 0, st>>>(r32, (const double *)r->r.p, n);
+            MOT_CHECK_LAUNCH();
+            int it;
+            bool c;
+            MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c));
+            iters += it;
+            count_launch();
+            k_add_into<double, float><<<grid_for(n), 256, 0, st>>>((double *)r->J.p, c32, n);
+            MOT_CHECK_LAUNCH();
+        }
+        conv = true;
+        for (int b = 0; b < r->B; ++b)
+            if (rn[b] > tol * bn[b]) conv = false;
+    }
+    for (int b = 0; b < r->B; ++b) relres = std::max(relres, bn[b] > 0 ? rn[b] / bn[b] : 0.0);
+    cudaEventRecord(r->ev[2], st);
+    if (mixed) MOT_TRY(ring_push<float>(r));
+    else MOT_TRY(ring_push<double>(r));
+    cudaEventRecord(r->ev[3], st);
+    if (stats) {
+        MOT_CUDA_TRY(cudaEventSynchronize(r->ev[3]));
+        stats->iters = iters;
+        stats->sweeps = sweeps;
+        stats->relres = relres;
+        cudaEventElapsedTime(&stats->ms_history, r->ev[0], r->ev[1]);
+        cudaEventElapsedTime(&stats->ms_solve, r->ev[1], r->ev[2]);
+        cudaEventElapsedTime(&stats->ms_push, r->ev[2], r->ev[3]);
+        stats->mvps = (int32_t)(p->mvp_count - mvp0);
+        stats->ms_zhist = p->kt.total(kTimeZHist);
+        stats->ms_zgreen = p->kt.total(kTimeZGreen);
+    }
+    p->kt.on = false;
+    r->n += 1;
+    if (!conv) {
+        set_error("TFQMR did not reach the tolerance at step " + std::to_string(r->n - 1) +
+                  " (relres " + std::to_string(relres) + ")");
+        return MOT_ENOTCONV;
+    }
+    return MOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, int precision, mot_run **out) {
+    if (!p || !exc || !out) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (nrhs < 1 || nrhs > 1024) MOT_FAIL(MOT_EINVAL, "nrhs out of range [1, 1024]");
+    if (precision != MOT_FP64 && precision != MOT_MIXED) MOT_FAIL(MOT_EINVAL, "precision must be MOT_FP64 or MOT_MIXED");
+    for (int b = 0; b < nrhs; ++b) {
+        const mot_planewave &w = exc[b];
+        double kk = 0, pp = 0, kp = 0;
+        for (int i = 0; i < 3; ++i) {
+            kk += w.khat[i] * w.khat[i];
+            pp += w.pol[i] * w.pol[i];
+            kp += w.khat[i] * w.pol[i];
+        }
+        if (fabs(kk - 1.0) > 1e-9 || fabs(pp - 1.0) > 1e-9 || fabs(kp) > 1e-9)
+            MOT_FAIL(MOT_EINVAL, "plane wave: khat and pol must be orthogonal unit vectors");
+        if (!(w.sigma > 0.0) || !std::isfinite(w.E0) || !std::isfinite(w.t0) || !std::isfinite(w.f0) ||
+            !std::isfinite(w.sigma))
+            MOT_FAIL(MOT_EINVAL, "plane wave: sigma must be > 0 and all parameters finite");
+    }
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    const bool mixed = precision == MOT_MIXED;
+    MOT_TRY(build_history_spectra(p, !mixed, mixed));
+    mot_run *r = new mot_run();
+    r->p = p;
+    r->B = nrhs;
+    r->prec = precision;
+    auto fail = [&](mot_status s) {
+        mot_run_destroy(r);
+        return s;
+    };
+    const long nv = (long)p->N[0] * p->N[1] * p->N[2];
+    const long n = 3 * nv * nrhs;
+    // plane waves, then pol[B][3] right after them
+    r->pw_host.resize(nrhs);
+    std::vector<double> pol(3 * nrhs);
+    for (int b = 0; b < nrhs; ++b) {
+        PlaneWaveDev d;
+        d.E0 = exc[b].E0;
+        d.sigma = exc[b].sigma;
+        d.t0 = exc[b].t0;
+        d.f0 = exc[b].f0;
+        for (int i = 0; i < 3; ++i) {
+            d.khat[i] = exc[b].khat[i];
+            d.pol[i] = exc[b].pol[i];
+            d.rref[i] = exc[b].khat[i] < 0 ? p->N[i] * p->h : 0.0;
+            pol[3 * b + i] = exc[b].pol[i];
+        }
+        r->pw_host[b] = d;
+    }
+    mot_status s;
+    if ((s = dalloc(r->pw, sizeof(PlaneWaveDev) * nrhs + sizeof(double) * 3 * nrhs)) != MOT_OK) return fail(s);
+    cudaMemcpy(r->pw.p, r->pw_host.data(), sizeof(PlaneWaveDev) * nrhs, cudaMemcpyHostToDevice);
+    cudaMemcpy((char *)r->pw.p + sizeof(PlaneWaveDev) * nrhs, pol.data(), sizeof(double) * 3 * nrhs,
+               cudaMemcpyHostToDevice);
+    const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
+    const size_t vs = mixed ? sizeof(float) : sizeof(double);
+    if ((s = dalloc(r->inc, sizeof(double) * nv * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->J, sizeof(double) * n)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->b, sizeof(double) * n)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->r, sizeof(double) * n)) != MOT_OK) return fail(s);
+    size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
+    if ((s = dalloc(r->ring, ring_bytes)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
+    for (int i = 0; i < 10; ++i)
+        if ((s = dalloc(r->kv[i], vs * n)) != MOT_OK) return fail(s);
+    if (mixed && (s = dalloc(r->r32, sizeof(float) * 2 * n)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->scal, sizeof(TfqmrScal) * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->part1, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->part2, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->part3, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->dots, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
+    // Z0 workspace for the batch in both precisions (FP64 residual / FP32 inner)
+    size_t a, bb;
+    z0_ws_bytes(p, nrhs, sizeof(double2), &a, &bb);
+    if ((s = dalloc(p->wsA, a)) != MOT_OK) return fail(s);
+    if ((s = dalloc(p->wsB, bb)) != MOT_OK) return fail(s);
+    cudaStream_t st = p->ctx->stream;
+    cudaMemsetAsync(r->ring.p, 0, ring_bytes, st);
+    cudaMemsetAsync(r->J.p, 0, sizeof(double) * n, st);
+    for (int i = 0; i < 4; ++i)
+        if (cudaEventCreate(&r->ev[i]) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MOT_ECUDA);
+    *out = r;
+    return MOT_OK;
+}
+
+mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *stats) {
+    if (!r) MOT_FAIL(MOT_EINVAL, "run is NULL");
+    if (nsteps < 0) MOT_FAIL(MOT_EINVAL, "nsteps < 0");
+    MOT_CUDA_TRY(cudaSetDevice(r->p->ctx->device));
+    const long n = 3L * r->p->N[0] * r->p->N[1] * r->p->N[2] * r->B;
+    mot_status result = MOT_OK;
+    for (int s = 0; s < nsteps; ++s) {
+        mot_status st = run_one_step(r, stats ? stats + s : nullptr);
+        if (st != MOT_OK && st != MOT_ENOTCONV) return st;
+        if (st == MOT_ENOTCONV) result = st;
+        if (J_out) {
+            MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)s * n, r->J.p, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                         r->p->ctx->stream));
+        }
+    }
+    if (J_out || stats) MOT_CUDA_TRY(cudaStreamSynchronize(r->p->ctx->stream));
+    return result;
+}
+
+mot_status mot_run_current_device(mot_run *r, const void **J_dev) {
+    if (!r || !J_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    *J_dev = r->J.p;
+    return MOT_OK;
+}
+
+mot_status mot_kernel_launches(uint64_t *count) {
+    if (!count) MOT_FAIL(MOT_EINVAL, "count is NULL");
+    *count = g_launches.load();
+    return MOT_OK;
+}
+
+mot_status mot_run_step_index(const mot_run *r, int64_t *n) {
+    if (!r || !n) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    *n = r->n;
+    return MOT_OK;
+}
+
+void mot_run_destroy(mot_run *r) {
+    if (!r) return;
+    cudaSetDevice(r->p->ctx->device);
+    cudaStreamSynchronize(r->p->ctx->stream);
+    dfree(r->pw);
+    dfree(r->inc);
+    dfree(r->J);
+    dfree(r->b);
+    dfree(r->r);
+    dfree(r->ring);
+    dfree(r->wsAh);
+    dfree(r->wsBh);
+    for (int i = 0; i < 10; ++i) dfree(r->kv[i]);
+    dfree(r->r32);
+    dfree(r->scal);
+    dfree(r->part1);
+    dfree(r->part2);
+    dfree(r->part3);
+    dfree(r->dots);
+    for (int i = 0; i < 4; ++i)
+        if (r->ev[i]) cudaEventDestroy(r->ev[i]);
+    delete r;
+}
+
+}  // extern "C"

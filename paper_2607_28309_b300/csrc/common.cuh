@@ -1,0 +1,43 @@
+// common.cuh -- shared types and helpers of the libmotjvie CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#ifndef MOT_HD
+#define MOT_HD __host__ __device__
+#endif
+
+namespace mot {
+
+// complex helpers on float2 / double2
+template <typename T> struct cx;
+template <> struct cx<float> { using type = float2; };
+template <> struct cx<double> { using type = double2; };
+template <typename T> using cplx = typename cx<T>::type;
+
+template <typename C> MOT_HD inline C cmake(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
+template <typename C> MOT_HD inline C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> MOT_HD inline C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> MOT_HD inline C cmul(C a, C b) { return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C> MOT_HD inline C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
+template <typename C> MOT_HD inline C cconj(C a) { return cmake<C>(a.x, -a.y); }
+// multiply by i (sign +1) or -i (sign -1)
+template <int S, typename C> MOT_HD inline C cmuli(C a) { return S > 0 ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x); }
+
+// thread-local error message + status helpers (host side)
+void set_error(const std::string &msg);
+const char *get_error();
+
+}  // namespace mot
+
+#define MOT_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            ::mot::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));           \
+            return MOT_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)

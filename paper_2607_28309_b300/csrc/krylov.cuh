@@ -1,0 +1,319 @@
+// krylov.cuh -- batched TFQMR (Freund 1993, the solver of Sec. II) vector
+// kernels, FP64 inner products, and the incident right-hand side (Eq. 7-8).
+//
+// Vectors are [B][L] (L = 3 * Nx * Ny * Nz); every right-hand side b keeps
+// its own scalars in TfqmrScal.  Inner products and norms are accumulated in
+// FP64 whatever the vector type, by a deterministic two-level reduction:
+// fixed block partials, then one warp per right-hand side in fixed order.
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+
+namespace mot {
+
+struct TfqmrScal {
+    double rho, alpha, theta, eta, tau, beta;
+    double eta_prev;     // eta of the half step whose x update is pending
+    double bnorm;        // ||b||
+    double tolabs;       // tol * ||b||
+    int m;               // half steps done
+    int conv;            // 1 once tau sqrt(m+1) <= tolabs (or b == 0)
+    int pending;         // 1 if x += eta_prev d is still to be applied
+    int pad;
+};
+
+constexpr int kRedBlocks = 296;  // 2 x 148 SMs
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// part[b*kRedBlocks + blk] = sum a*c over the block's slice;  grid (kRedBlocks, B)
+template <typename TA, typename TC>
+__global__ void __launch_bounds__(kRedThreads) k_dot_part(const TA *__restrict__ a, const TC *__restrict__ c,
+                                                          long L, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const TA *pa = a + (long)b * L;
+    const TC *pc = c + (long)b * L;
+    double s = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        s += (double)pa[i] * (double)pc[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = s;
+}
+
+__device__ __forceinline__ double reduce_parts(const double *part, int b) {
+    // one warp, fixed order
+    double s = 0.0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += 32) s += part[b * kRedBlocks + i];
+    return warp_sum(s);
+}
+
+// ---- initialisation: r = b - A x0 already in w; tau = ||w||, rho = tau^2 --
+// grid B, block 32
+__global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol) {
+    const int b = blockIdx.x;
+    double r2 = reduce_parts(part_r2, b);
+    double b2 = reduce_parts(part_b2, b);
+    if (threadIdx.x == 0) {
+        TfqmrScal s;
+        s.tau = sqrt(r2);
+        s.rho = r2;
+        s.theta = 0.0;
+        s.eta = 0.0;
+        s.alpha = 0.0;
+        s.beta = 0.0;
+        s.eta_prev = 0.0;
+        s.bnorm = sqrt(b2);
+        s.tolabs = tol * s.bnorm;
+        s.m = 0;
+        // b = 0 has the solution 0 whatever x0 is (conv = 3 zeroes x)
+        s.conv = b2 == 0.0 ? 3 : ((s.tau <= s.tolabs || r2 == 0.0) ? 1 : 0);
+        s.pending = 0;
+        s.pad = 0;
+        sc[b] = s;
+    }
+}
+
+// x = 0 for right-hand sides with b = 0 (conv == 3), then mark them done
+template <typename V>
+__global__ void k_tfqmr_zero_rhs(V *__restrict__ x, TfqmrScal *__restrict__ sc, long L) {
+    const int b = blockIdx.y;
+    if (sc[b].conv != 3) return;
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) x[o + i] = V(0);
+}
+
+__global__ void k_tfqmr_zero_done(TfqmrScal *sc, int B) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B && sc[b].conv == 3) sc[b].conv = 1;
+}
+
+// sigma = (r*, v): alpha = rho / sigma.  grid B, block 32
+__global__ void k_tfqmr_alpha(TfqmrScal *sc, const double *part) {
+    const int b = blockIdx.x;
+    double sigma = reduce_parts(part, b);
+    if (threadIdx.x == 0 && !sc[b].conv) {
+        if (sigma == 0.0) sc[b].conv = 2;  // breakdown: keep the current iterate
+        else sc[b].alpha = sc[b].rho / sigma;
+    }
+}
+
+// y2 = y1 - alpha v
+template <typename V>
+__global__ void k_tfqmr_y2(V *__restrict__ y2, const V *__restrict__ y1, const V *__restrict__ v,
+                           const TfqmrScal *__restrict__ sc, long L) {
+    const int b = blockIdx.y;
+    if (sc[b].conv) return;
+    const V al = (V)sc[b].alpha;
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        y2[o + i] = y1[o + i] - al * v[o + i];
+}
+
+// half step: x += eta_prev d (pending); w -= alpha Ay; d = y + (theta^2 eta/alpha) d;
+// partials of ||w||^2 and (optionally) (r*, w).  grid (kRedBlocks, B)
+template <typename V, typename VX>
+__global__ void __launch_bounds__(kRedThreads) k_tfqmr_half(VX *__restrict__ x, V *__restrict__ w, V *__restrict__ d,
+                                                            const V *__restrict__ y, const V *__restrict__ Ay,
+                                                            const V *__restrict__ rs, const TfqmrScal *__restrict__ sc,
+                                                            long L, double *__restrict__ part_w2,
+                                                            double *__restrict__ part_rw) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const TfqmrScal s = sc[b];
+    double w2 = 0.0, rw = 0.0;
+    if (!s.conv) {
+        const V al = (V)s.alpha;
+        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
+        const VX ep = (VX)s.eta_prev;
+        const long o = (long)b * L;
+        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
+            V dold = d[o + i];
+            if (s.pending) x[o + i] += ep * (VX)dold;
+            V wn = w[o + i] - al * Ay[o + i];
+            w[o + i] = wn;
+            d[o + i] = y[o + i] + coef * dold;
+            w2 += (double)wn * (double)wn;
+            if (part_rw) rw += (double)rs[o + i] * (double)wn;
+        }
+    }
+    w2 = block_sum(w2, sh);
+    if (part_rw) rw = block_sum(rw, sh);
+    if (threadIdx.x == 0) {
+        part_w2[b * kRedBlocks + blockIdx.x] = w2;
+        if (part_rw) part_rw[b * kRedBlocks + blockIdx.x] = rw;
+    }
+}
+
+// theta = ||w||/tau, c = 1/sqrt(1+theta^2), tau = tau theta c, eta = c^2 alpha;
+// converged once tau sqrt(m+1) <= tol ||b||.  grid B, block 32
+__global__ void k_tfqmr_half_fin(TfqmrScal *sc, const double *part_w2) {
+    const int b = blockIdx.x;
+    double w2 = reduce_parts(part_w2, b);
+    if (threadIdx.x == 0 && !sc[b].conv) {
+        TfqmrScal s = sc[b];
+        double th = sqrt(w2) / s.tau;
+        double c = 1.0 / sqrt(1.0 + th * th);
+        s.tau = s.tau * th * c;
+        s.theta = th;
+        s.eta = c * c * s.alpha;
+        s.eta_prev = s.eta;
+        s.pending = 1;
+        s.m += 1;
+        if (s.tau * sqrt((double)s.m + 1.0) <= s.tolabs) s.conv = 2;  // 2: pending update still due
+        sc[b] = s;
+    }
+}
+
+// rho_new = (r*, w): beta = rho_new / rho.  grid B, block 32
+__global__ void k_tfqmr_beta(TfqmrScal *sc, const double *part_rw) {
+    const int b = blockIdx.x;
+    double rn = reduce_parts(part_rw, b);
+    if (threadIdx.x == 0 && !sc[b].conv) {
+        if (sc[b].rho == 0.0) { sc[b].conv = 2; return; }
+        sc[b].beta = rn / sc[b].rho;
+        sc[b].rho = rn;
+    }
+}
+
+// y1 = w + beta y2
+template <typename V>
+__global__ void k_tfqmr_y1(V *__restrict__ y1, const V *__restrict__ w, const V *__restrict__ y2,
+                           const TfqmrScal *__restrict__ sc, long L) {
+    const int b = blockIdx.y;
+    if (sc[b].conv) return;
+    const V be = (V)sc[b].beta;
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        y1[o + i] = w[o + i] + be * y2[o + i];
+}
+
+// v = Ay1 + beta (Ay2 + beta v), with the partials of (r*, v).  grid (kRedBlocks, B)
+template <typename V>
+__global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, const V *__restrict__ Ay1,
+                                                         const V *__restrict__ Ay2, const V *__restrict__ rs,
+                                                         const TfqmrScal *__restrict__ sc, long L,
+                                                         double *__restrict__ part) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    double acc = 0.0;
+    if (!sc[b].conv) {
+        const V be = (V)sc[b].beta;
+        const long o = (long)b * L;
+        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
+            V vn = Ay1[o + i] + be * (Ay2[o + i] + be * v[o + i]);
+            v[o + i] = vn;
+            acc += (double)rs[o + i] * (double)vn;
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = acc;
+}
+
+// apply the pending x += eta d of right-hand sides that converged (conv == 2)
+// or that stop at the iteration cap (flush = 1)
+template <typename V, typename VX>
+__global__ void k_tfqmr_flush(VX *__restrict__ x, const V *__restrict__ d, TfqmrScal *__restrict__ sc, long L,
+                              int flush_all) {
+    const int b = blockIdx.y;
+    const TfqmrScal s = sc[b];
+    if (!s.pending || !(s.conv == 2 || flush_all)) return;
+    const VX ep = (VX)s.eta_prev;
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        x[o + i] += ep * (VX)d[o + i];
+}
+
+// mark flushed right-hand sides
+__global__ void k_tfqmr_settle(TfqmrScal *sc, int B, int flush_all) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B && sc[b].pending && (sc[b].conv == 2 || flush_all)) {
+        sc[b].pending = 0;
+        if (sc[b].conv == 2) sc[b].conv = 1;
+    }
+}
+
+// ||v||^2 per right-hand side into out[b] (after k_dot_part). grid B, block 32
+__global__ void k_finish_dot(const double *part, double *out) {
+    double s = reduce_parts(part, blockIdx.x);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// ---- elementwise helpers ----
+template <typename TD, typename TS>
+__global__ void k_convert(TD *__restrict__ dst, const TS *__restrict__ src, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (TD)src[i];
+}
+
+template <typename TD, typename TS>
+__global__ void k_add_into(TD *__restrict__ dst, const TS *__restrict__ src, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] += (TD)src[i];
+}
+
+// ---------------------------------------------------------------------------
+// incident right-hand side (Eq. 7-8):
+//   inc[b][m] = (eps_r(m) - 1) eps0 E0 < dg/dt (tau) >_m
+//   g(tau) = exp(-tau^2 / (2 sigma^2)) cos(2 pi f0 tau) / (sigma sqrt(2 pi)),
+//   tau = t - t0 - khat.(r - r_ref)/c0,
+// voxel average by the 2x2x2 Gauss-Legendre rule.  The Cartesian direction
+// pol[b] multiplies it in the right-hand-side epilogue.
+// ---------------------------------------------------------------------------
+struct PlaneWaveDev {
+    double E0, sigma, t0, f0;
+    double khat[3];
+    double pol[3];
+    double rref[3];
+};
+
+__global__ void k_incident(double *__restrict__ inc, const double *__restrict__ eps,
+                           const PlaneWaveDev *__restrict__ pw, int Nx, int Ny, int Nz, double h, double t,
+                           int nrhs) {
+    const long n = (long)Nx * Ny * Nz;
+    const double c0 = 299792458.0, eps0 = 8.8541878128e-12;
+    const double g0 = 0.21132486540518711775, g1 = 0.78867513459481288225;  // 1/2 -+ 1/(2 sqrt 3)
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n * nrhs; i += (long)gridDim.x * blockDim.x) {
+        long b = i / n, m = i - b * n;
+        double ep = eps[m];
+        if (ep == 1.0) { inc[i] = 0.0; continue; }
+        int mx = (int)(m % Nx), my = (int)((m / Nx) % Ny), mz = (int)(m / ((long)Nx * Ny));
+        const PlaneWaveDev P = pw[b];
+        const double w = 2.0 * 3.141592653589793238462643 * P.f0;
+        const double amp = P.E0 / (P.sigma * 2.5066282746310005024);  // sigma sqrt(2 pi)
+        const double is2 = 1.0 / (P.sigma * P.sigma);
+        double acc = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            double rx = (mx + ((q & 1) ? g1 : g0)) * h - P.rref[0];
+            double ry = (my + ((q & 2) ? g1 : g0)) * h - P.rref[1];
+            double rz = (mz + ((q & 4) ? g1 : g0)) * h - P.rref[2];
+            double tau = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
+            double s, c;
+            sincos(w * tau, &s, &c);
+            acc += exp(-0.5 * tau * tau * is2) * (-tau * is2 * c - w * s);
+        }
+        inc[i] = (ep - 1.0) * eps0 * amp * 0.125 * acc;
+    }
+}
+
+}  // namespace mot

@@ -1,0 +1,105 @@
+// tables.cuh -- device generation of the lag tables g_k(d) and of their
+// circulant spectra Lambda_k (Sec. IV: "precomputed spectral coefficients of
+// the circulant Green-function kernel").
+//
+// Lag tables are computed once per sorted offset 0 <= a <= b <= c (one GPU
+// thread per lag/offset item) and spread to the nonnegative octant with the
+// permutation covariance of the Galerkin kernel.  Because g_pp is even in every
+// coordinate and g_pq (p != q) is odd in d_p and d_q and even in the third, the
+// DFT of the circulant embedding is real and is a product of one-dimensional
+// cosine / sine sums over the octant:
+//   Lambda_pq(k) = sgn * prod_i sum_{d_i = 0..R_i} c_i(k_i, d_i) g_pq(d),
+//   c(k, d) = 1 (d = 0) or 2 cos(2 pi k d / M) on even axes, 2 sin(2 pi k d / M)
+//   on odd axes, sgn = -1 for the mixed components ((-i)^2), and 1/(Mx My Mz)
+//   folded in.  This is the FFT of Eq. 11's kernel written out exactly.
+#pragma once
+
+#include "common.cuh"
+#include "galerkin.cuh"
+
+namespace mot {
+
+// one item: lag k and sorted offset (a, b, c)
+struct TableItem {
+    int k, a, b, c;
+};
+
+__global__ void k_galerkin_items(const TableItem *__restrict__ items, int n, double rho,
+                                 const double *__restrict__ glx, const double *__restrict__ glw, int gln,
+                                 double *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gk::Rule q = {glx, glw, gln};
+    TableItem it = items[i];
+    gk::galerkin_A(q, it.k, rho, it.a, it.b, it.c, out + 6 * (long)i);
+}
+
+__host__ __device__ inline int a6_index(int p, int q) {
+    if (p == q) return p;
+    int s = p + q;  // 1 -> (0,1), 2 -> (0,2), 3 -> (1,2)
+    return 2 + s;
+}
+
+// g on the octant d >= 0 from the sorted-offset values A6 (A00 A11 A22 A01 A02 A12);
+// map[(a*(Rm+1) + b)*(Rm+1) + c] = item index (or -1).  out: [6][Rz+1][Ry+1][Rx+1]
+__host__ __device__ inline void expand_one(const double *A6, const int *map, int Rm, int dx, int dy, int dz,
+                                           double *g6) {
+    int d[3] = {dx, dy, dz}, ax[3] = {0, 1, 2};
+    for (int i = 1; i < 3; ++i) {
+        int j = i;
+        while (j > 0 && d[ax[j - 1]] > d[ax[j]]) {
+            int t = ax[j];
+            ax[j] = ax[j - 1];
+            ax[j - 1] = t;
+            --j;
+        }
+    }
+    long key = ((long)d[ax[0]] * (Rm + 1) + d[ax[1]]) * (Rm + 1) + d[ax[2]];
+    int id = map[key];
+    for (int c = 0; c < 6; ++c) g6[c] = 0.0;
+    if (id < 0) return;
+    int pos[3];
+    for (int j = 0; j < 3; ++j) pos[ax[j]] = j;
+    const double *A = A6 + 6 * (long)id;
+    double tr = A[0] + A[1] + A[2];
+    const int pp[6] = {0, 1, 2, 0, 0, 1}, qq[6] = {0, 1, 2, 1, 2, 2};
+    for (int c = 0; c < 6; ++c) {
+        double v = A[a6_index(pos[pp[c]], pos[qq[c]])];
+        g6[c] = (c < 3) ? v - tr : v;
+    }
+}
+
+__global__ void k_expand_octant(const double *__restrict__ A6, const int *__restrict__ map, int Rm, int Rx, int Ry,
+                                int Rz, double *__restrict__ oct) {
+    long n = (long)(Rx + 1) * (Ry + 1) * (Rz + 1);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        int dx = (int)(i % (Rx + 1)), dy = (int)((i / (Rx + 1)) % (Ry + 1)), dz = (int)(i / ((long)(Rx + 1) * (Ry + 1)));
+        double g6[6];
+        expand_one(A6, map, Rm, dx, dy, dz, g6);
+        for (int c = 0; c < 6; ++c) oct[c * n + i] = g6[c];
+    }
+}
+
+// one separable pass: out[o][k][i] = sum_d coef[k][d] in[o][d][i]
+__global__ void k_axis_sum(const double *__restrict__ in, double *__restrict__ out, const double *__restrict__ coef,
+                           int nouter, int Rin, int K, int ninner) {
+    long n = (long)nouter * K * ninner;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        int i = (int)(t % ninner);
+        int k = (int)((t / ninner) % K);
+        long o = t / ((long)ninner * K);
+        const double *src = in + o * Rin * ninner + i;
+        const double *cf = coef + (long)k * Rin;
+        double acc = 0.0;
+        for (int d = 0; d < Rin; ++d) acc += cf[d] * src[(long)d * ninner];
+        out[t] = acc;
+    }
+}
+
+template <typename T>
+__global__ void k_scale_store(const double *__restrict__ src, T *__restrict__ dst, long n, double s) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (T)(src[i] * s);
+}
+
+}  // namespace mot

@@ -1,0 +1,131 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (no solver arithmetic).
+
+Stands in for the paper's dielectric cubes (Sec. III-B, Sec. V-A) and its 8x8
+nanopillar metasurface (Sec. V-B); no dataset is involved.  Used by the tests,
+bench.py and the smoke check for both the CUDA path and the oracle.
+
+Recipe
+------
+- voxel size h = 10 nm, c0 = 299,792,458 m/s, dt_CFL = h/(c0 sqrt 3);
+- random numbers: SplitMix64 seeded per workload, u = (x >> 11) * 2^-53,
+  drawn per permittivity block with blocks enumerated x fastest;
+- pulse of Eq. 7-8 over a window T = nsteps * alpha * dt_CFL: sigma = T/20,
+  t0 = 5 sigma, sigma_f = 1/(2 pi sigma), f0 = 2.5 sigma_f, f_max = f0 + 3 sigma_f;
+- nanopillars: cylinders of 24-voxel diameter (voxel centre within 12 voxels of
+  the axis) at 32-voxel pitch, axes at 16 + 32 i, occupying z in [8, 72): the
+  lower 43 layers eps_r = 3.5, the upper 21 eps_r = 6.0, background 1.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+C0 = 299792458.0
+H_DEFAULT = 10e-9
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n uniforms in [0, 1) from SplitMix64 (Steele, Lea, Flood 2014)."""
+    out = np.empty(n)
+    x = seed & _MASK
+    for i in range(n):
+        x = (x + 0x9E3779B97F4A7C15) & _MASK
+        z = x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        z ^= z >> 31
+        out[i] = (z >> 11) * 2.0**-53
+    return out
+
+
+def block_eps(N, block: int, lo: float, hi: float, seed: int) -> np.ndarray:
+    """eps_r uniform in [lo, hi] per block^3 sub-block; array [Nz][Ny][Nx]."""
+    Nx, Ny, Nz = N
+    bx, by, bz = (-(-Nx // block), -(-Ny // block), -(-Nz // block))
+    u = splitmix64(seed, bx * by * bz).reshape(bz, by, bx)
+    vals = lo + (hi - lo) * u
+    iz = np.arange(Nz) // block
+    iy = np.arange(Ny) // block
+    ix = np.arange(Nx) // block
+    return np.ascontiguousarray(vals[iz[:, None, None], iy[None, :, None], ix[None, None, :]])
+
+
+def pillar_eps(nx: int, ny: int, Nz: int = 80, pitch: int = 32, diameter: int = 24, z0: int = 8,
+               base: int = 43, cap: int = 21, eps_base: float = 3.5, eps_cap: float = 6.0,
+               layer_eps=None) -> np.ndarray:
+    """nx x ny pillar array on a (pitch*nx) x (pitch*ny) x Nz grid.
+    layer_eps, if given, is a list of (eps_base, eps_cap) per pillar (x fastest)."""
+    Nx, Ny = pitch * nx, pitch * ny
+    eps = np.ones((Nz, Ny, Nx))
+    r = diameter / 2.0
+    yy, xx = np.meshgrid(np.arange(pitch) + 0.5, np.arange(pitch) + 0.5, indexing="ij")
+    disk = (xx - pitch / 2.0) ** 2 + (yy - pitch / 2.0) ** 2 <= r * r
+    for j in range(ny):
+        for i in range(nx):
+            eb, ec = (eps_base, eps_cap) if layer_eps is None else layer_eps[j * nx + i]
+            sl = (slice(j * pitch, (j + 1) * pitch), slice(i * pitch, (i + 1) * pitch))
+            for z in range(z0, z0 + base):
+                eps[z][sl][disk] = eb
+            for z in range(z0 + base, z0 + base + cap):
+                eps[z][sl][disk] = ec
+    return eps
+
+
+def dt_cfl(h: float = H_DEFAULT) -> float:
+    return h / (C0 * math.sqrt(3.0))
+
+
+def pulse(nsteps: int, alpha: float, h: float = H_DEFAULT, khat=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), E0=1.0):
+    """Gaussian-modulated plane wave (Eq. 7-8) fitted to the window nsteps*alpha*dt_CFL."""
+    T = nsteps * alpha * dt_cfl(h)
+    sigma = T / 20.0
+    sf = 1.0 / (2.0 * math.pi * sigma)
+    return {"E0": E0, "sigma": sigma, "t0": 5.0 * sigma, "f0": 2.5 * sf, "khat": tuple(khat), "pol": tuple(pol)}
+
+
+def pulse_fmax(pw) -> float:
+    return pw["f0"] + 3.0 / (2.0 * math.pi * pw["sigma"])
+
+
+def oblique_set(nsteps: int, alpha: float, h: float = H_DEFAULT, angles_deg=(0, 10, 20, 30, 40, 50, 60, 70)):
+    """8 incidence angles x 2 polarisations: khat = (sin t, 0, cos t), TE pol = y,
+    TM pol = (cos t, 0, -sin t)."""
+    out = []
+    for a in angles_deg:
+        t = math.radians(a)
+        k = (math.sin(t), 0.0, math.cos(t))
+        out.append(pulse(nsteps, alpha, h, khat=k, pol=(0.0, 1.0, 0.0)))
+        out.append(pulse(nsteps, alpha, h, khat=k, pol=(math.cos(t), 0.0, -math.sin(t))))
+    return out
+
+
+# ---------------------------------------------------------------- named workloads
+def cube16(seed: int = 1):
+    """16^3 cube, eps_r U[2,4] per 4^3 block, x-pol along +z, alpha 4, 100 steps, FP64."""
+    N = (16, 16, 16)
+    return {"name": "cube16_a4", "N": N, "h": H_DEFAULT, "eps": block_eps(N, 4, 2.0, 4.0, seed), "alpha": 4.0,
+            "steps": 100, "exc": [pulse(100, 4.0)]}
+
+
+def cube64(alpha: float = 8.0, seed: int = 2):
+    """64^3 cube, eps_r U[1.5,6] per 8^3 block; window 400 dt_CFL -> 400/alpha steps."""
+    N = (64, 64, 64)
+    steps = int(round(400 / alpha))
+    return {"name": f"cube64_a{int(alpha)}", "N": N, "h": H_DEFAULT, "eps": block_eps(N, 8, 1.5, 6.0, seed),
+            "alpha": float(alpha), "steps": steps, "exc": [pulse(steps, alpha)]}
+
+
+def pillars8x8():
+    """8x8 pillars on 256x256x80, normal incidence along -z, x-pol, alpha 8, 200 steps."""
+    eps = pillar_eps(8, 8)
+    return {"name": "pillars8x8_a8", "N": (256, 256, 80), "h": H_DEFAULT, "eps": eps, "alpha": 8.0, "steps": 200,
+            "exc": [pulse(200, 8.0, khat=(0.0, 0.0, -1.0))]}
+
+
+def cube64_batch16(seed: int = 4):
+    """64^3 cube, eps_r U[2,4] per 4^3 block, 16 oblique plane waves, alpha 8, 200 steps."""
+    N = (64, 64, 64)
+    return {"name": "cube64_b16_a8", "N": N, "h": H_DEFAULT, "eps": block_eps(N, 4, 2.0, 4.0, seed), "alpha": 8.0,
+            "steps": 200, "exc": oblique_set(200, 8.0)}

@@ -1,0 +1,183 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 unless stated):
+- FP64 Z0 FFT product vs the oracle's direct product:            1e-10
+- FP32 Z0 FFT product vs the oracle:                             1e-5 (measured value reported)
+- library lag tables vs the oracle's tables:                      1e-12 absolute
+- FP64 march vs the oracle march (exact solve), per step, scaled
+  by max_n ||J_n||:                                                1e-9
+- mixed FP32/FP64 march vs the oracle, same scaling:               1e-5
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2607_28309_b300 as mot
+from paper_2607_28309_b300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2607_28309_b300 import build
+
+    build.build()
+    c = mot.mot_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    torch.cuda.synchronize()
+    mot.mot_ctx_destroy(c)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _apply(prob, x_np, nrhs, dtype):
+    tdt = torch.float64 if dtype == mot.MOT_F64 else torch.float32
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).to("cuda", tdt)
+    y = torch.empty_like(x)
+    mot.mot_apply_Z0(prob, x, y, nrhs, dtype)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+GRIDS = [((5, 6, 7), 4.0), ((12, 12, 12), 8.0), ((16, 9, 11), 16.0), ((20, 20, 20), 1.0), ((1, 1, 1), 4.0),
+         ((1, 2, 3), 8.0), ((3, 17, 2), 2.0), ((33, 8, 10), 4.0)]
+
+
+@pytest.mark.parametrize("N,alpha", GRIDS)
+def test_z0_fft_product_matches_direct(ctx, orc, N, alpha):
+    rng = np.random.default_rng(sum(N) + int(alpha))
+    eps = rng.uniform(1.0, 6.0, size=N[::-1])
+    prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+    try:
+        rho = alpha / math.sqrt(3)
+        R = orc.table_extent(0, rho, N)
+        g = orc.lag_table(0, rho, R)
+        # the library's own table equals the oracle's
+        Rl, gl = mot.mot_kernel_table(prob, 0)
+        assert tuple(Rl) == tuple(R)
+        assert np.abs(gl - g).max() <= 1e-12
+        for nrhs in (1, 2):
+            x = rng.standard_normal((nrhs, 3) + N[::-1])
+            ref = np.stack([orc.Zk_apply(0, N, eps, R, g, x[b]) for b in range(nrhs)])
+            y64 = _apply(prob, x, nrhs, mot.MOT_F64)
+            assert _rel(y64, ref) <= 1e-10
+            y32 = _apply(prob, x, nrhs, mot.MOT_F32)
+            assert _rel(y32, ref) <= 1e-5
+        # the same product with the oracle's table loaded into the FFT path
+        mot.mot_set_kernel_table(prob, 0, g, R)
+        x = rng.standard_normal((1, 3) + N[::-1])
+        assert _rel(_apply(prob, x, 1, mot.MOT_F64), orc.Zk_apply(0, N, eps, R, g, x[0])[None]) <= 1e-10
+    finally:
+        mot.mot_problem_destroy(prob)
+
+
+def _march_pair(ctx, orc, N, eps, alpha, exc, steps, precision):
+    prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+    try:
+        run = mot.mot_run_create(prob, exc, precision)
+        try:
+            nv = int(np.prod(N))
+            J = np.zeros((steps, len(exc), 3, nv))
+            mot.mot_run_step(run, steps, J)
+        finally:
+            mot.mot_run_destroy(run)
+    finally:
+        mot.mot_problem_destroy(prob)
+    return J
+
+
+def _mot_errors(Jg, Jo):
+    steps = Jo.shape[0]
+    Jo = Jo.reshape(steps, -1)
+    Jg = Jg.reshape(steps, -1)
+    scale = np.linalg.norm(Jo, axis=1).max()
+    return np.linalg.norm(Jg - Jo, axis=1) / scale
+
+
+def test_mot_small_fp64_and_mixed(ctx, orc):
+    N = (6, 5, 7)
+    eps = synthetic.block_eps(N, 2, 2.0, 4.0, 21)
+    alpha, steps = 4.0, 30
+    exc = [synthetic.pulse(steps, alpha), synthetic.pulse(steps, alpha, pol=(0.0, 1.0, 0.0))]
+    P = orc.Problem(N, 10e-9, eps, alpha)
+    Jo = P.march(exc, steps)
+    e64 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64), Jo)
+    assert e64.max() <= 1e-9, e64.max()
+    e32 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_MIXED), Jo)
+    assert e32.max() <= 1e-5, e32.max()
+
+
+def test_mot_oblique_batch(ctx, orc):
+    N = (8, 8, 8)
+    eps = synthetic.block_eps(N, 4, 2.0, 4.0, 4)
+    alpha, steps = 8.0, 16
+    exc = synthetic.oblique_set(steps, alpha, angles_deg=(0, 30, 70))
+    Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
+    e64 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64), Jo)
+    assert e64.max() <= 1e-9, e64.max()
+
+
+def test_zero_contrast_gives_zero_current(ctx):
+    N = (7, 6, 5)
+    J = _march_pair(ctx, None, N, np.ones(N[::-1]), 4.0, [synthetic.pulse(20, 4.0)], 20, mot.MOT_FP64)
+    assert np.all(J == 0.0)
+    J = _march_pair(ctx, None, N, np.ones(N[::-1]), 4.0, [synthetic.pulse(20, 4.0)], 20, mot.MOT_MIXED)
+    assert np.all(J == 0.0)
+
+
+def test_cube16_full_march(ctx, orc):
+    """16^3 cube, eps_r U[2,4] per 4^3 block, alpha 4, 100 steps: FP64 and mixed."""
+    w = synthetic.cube16()
+    P = orc.Problem(w["N"], w["h"], w["eps"], w["alpha"])
+    Jo = P.march(w["exc"], w["steps"])
+    e64 = _mot_errors(_march_pair(ctx, orc, w["N"], w["eps"], w["alpha"], w["exc"], w["steps"], mot.MOT_FP64), Jo)
+    assert e64.max() <= 1e-9, e64.max()
+    e32 = _mot_errors(_march_pair(ctx, orc, w["N"], w["eps"], w["alpha"], w["exc"], w["steps"], mot.MOT_MIXED), Jo)
+    assert e32.max() <= 1e-5, e32.max()
+
+
+@pytest.mark.parametrize("which", ["cube64_a8", "cube64_a16", "pillars8x8", "cube64_b16"])
+def test_full_size_product_sampled_rows(ctx, orc, which):
+    """Z0 product at the full workload sizes (the bench's launch configuration),
+    1024 rows checked one by one against the oracle's direct sum."""
+    if which == "cube64_a8":
+        w = synthetic.cube64(8.0)
+    elif which == "cube64_a16":
+        w = synthetic.cube64(16.0)
+    elif which == "pillars8x8":
+        w = synthetic.pillars8x8()
+    else:
+        w = synthetic.cube64_batch16()
+    N, eps, alpha = w["N"], w["eps"], w["alpha"]
+    nrhs = len(w["exc"])
+    rng = np.random.default_rng(123)
+    nv = int(np.prod(N))
+    x = rng.standard_normal((nrhs, 3, nv))
+    prob = mot.mot_problem_create(ctx, N, w["h"], eps, alpha)
+    try:
+        rho = alpha / math.sqrt(3)
+        R = orc.table_extent(0, rho, N)
+        g = orc.lag_table(0, rho, R)
+        y64 = _apply(prob, x, nrhs, mot.MOT_F64)
+        y32 = _apply(prob, x, nrhs, mot.MOT_F32)
+    finally:
+        mot.mot_problem_destroy(prob)
+    bsel = rng.integers(0, nrhs, 1024)
+    psel = rng.integers(0, 3, 1024)
+    msel = rng.integers(0, nv, 1024)
+    ref = np.empty(1024)
+    for b in np.unique(bsel):
+        sel = bsel == b
+        ref[sel] = orc.Zk_rows(0, N, eps, R, g, x[b].reshape(3, N[2], N[1], N[0]), psel[sel], msel[sel])
+    got64 = y64[bsel, psel, msel]
+    got32 = y32[bsel, psel, msel]
+    assert _rel(got64, ref) <= 1e-10
+    assert _rel(got32, ref) <= 1e-5

@@ -15,6 +15,8 @@ import math
 import numpy as np
 import pytest
 
+from paper_2607_28309_b300 import synthetic
+
 
 def _dense_by_loops(orc, k, N, eps, R, g):
     Nx, Ny, Nz = N
@@ -78,7 +80,7 @@ def _cube(orc, N, alpha, eps, nsteps, pws):
 
 def test_zero_contrast_gives_zero_current(orc):
     N = (4, 4, 4)
-    pw = orc.gaussian_pulse_for(30, 4, 10e-9)
+    pw = synthetic.pulse(30, 4, 10e-9)
     P, J = _cube(orc, N, 4, np.ones(N[::-1]), 30, [pw])
     assert np.all(J == 0.0)
 
@@ -88,7 +90,7 @@ def test_linearity(orc):
     rng = np.random.default_rng(2)
     eps = rng.uniform(2, 4, size=N[::-1])
     h = 10e-9
-    base = orc.gaussian_pulse_for(40, 4, h)
+    base = synthetic.pulse(40, 4, h)
     px = dict(base, pol=(1.0, 0.0, 0.0))
     py = dict(base, pol=(0.0, 1.0, 0.0))
     pxy = dict(base, pol=(1 / math.sqrt(2), 1 / math.sqrt(2), 0.0), E0=math.sqrt(2))
@@ -115,7 +117,7 @@ def test_single_voxel_clausius_mossotti(orc):
     h, alpha, eps = 10e-9, 2.0, 5.0
     errs = []
     for nsteps in (400, 800):
-        pw = orc.gaussian_pulse_for(nsteps, alpha, h)
+        pw = synthetic.pulse(nsteps, alpha, h)
         P = orc.Problem((1, 1, 1), h, np.full((1, 1, 1), eps), alpha)
         J = P.march([pw], nsteps)[:, 0, 0, 0, 0, 0]
         b = np.array([orc.incident((1, 1, 1), h, np.full((1, 1, 1), eps), pw, n * P.dt)[0, 0, 0, 0] for n in range(nsteps)])
@@ -134,7 +136,7 @@ def test_time_step_refinement_converges(orc):
     traces = {}
     for alpha in (8, 4, 2, 1):
         n = T_steps_cfl // alpha
-        pw = orc.gaussian_pulse_for(n, alpha, h)
+        pw = synthetic.pulse(n, alpha, h)
         P = orc.Problem(N, h, eps, alpha)
         J = P.march([pw], n)[:, 0]
         traces[alpha] = J[:: 8 // alpha][: T_steps_cfl // 8]  # samples every 8 dt_CFL
