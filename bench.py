@@ -240,6 +240,7 @@ def native(args, ws, rank, local):
     e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         e_all0.record(stream)
         for i in range(K):
             evs[i][0].record(stream)
@@ -250,6 +251,7 @@ def native(args, ws, rank, local):
                           s.ms_push))
         e_all1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = mot.mot_kernel_launches() - l0
     barrier(ws)
     elapsed = e_all0.elapsed_time(e_all1) / 1e3

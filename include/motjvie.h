@@ -25,7 +25,7 @@
  *   pointers handed out (mot_run_current_device) stay valid until the next
  *   mot_run_step or mot_run_destroy on that run.
  * - Streams: all device work of a context is ordered on the context's stream
- *   (the one given to mot_ctx_create, or a library-created one when NULL).
+ *   (the one given to mot_ctx_create; NULL = the legacy default stream).
  *   Calls that return host data synchronise that stream before returning.
  * - Threads: handles are not thread-safe; use one context per host thread.
  */
@@ -119,8 +119,8 @@ typedef struct mot_run mot_run;
 const char *mot_last_error(void);
 
 /* Context on CUDA device `device`, ordering all work on `cuda_stream` (a
- * cudaStream_t, borrowed; NULL -> the library creates and owns a stream).
- * Errors: MOT_EINVAL (bad device), MOT_ECUDA.                                  */
+ * cudaStream_t, borrowed; NULL is the CUDA legacy default stream, which is also
+ * PyTorch's default stream).  Errors: MOT_EINVAL (bad device), MOT_ECUDA.      */
 mot_status mot_ctx_create(int device, void *cuda_stream, mot_ctx **out);
 void mot_ctx_destroy(mot_ctx *ctx);
 

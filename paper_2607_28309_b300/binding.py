@@ -132,6 +132,7 @@ def mot_last_error() -> str:
 
 def mot_ctx_create(device: int = 0, cuda_stream: int | None = None):
     out = ctypes.c_void_p()
+    # cuda_stream None or 0: the legacy default stream (PyTorch's default stream)
     _check(lib().mot_ctx_create(int(device), ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(out)))
     return out
 

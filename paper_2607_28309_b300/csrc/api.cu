@@ -266,7 +266,7 @@ enum { kTimeZGreen = 0, kTimeZHist = 1 };
 struct mot_problem {
     mot_ctx *ctx = nullptr;
     KTimer kt;
-    long mvp_count = 0;
+    bool capturing = false;
     int N[3];
     double h, alpha, rho, dt;
     int ell;
@@ -286,8 +286,18 @@ struct mot_problem {
     mot_options opt;
 };
 
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *x = nullptr;
+    int body_kernels = 0;
+};
+
 struct mot_run {
     mot_problem *p = nullptr;
+    cudaStream_t cap = nullptr;  // capture stream for the solve graphs
+    LoopGraph loop64, loop32;
+    DBuf ctl;                    // device loop control: iteration count, cap
     int B = 1;
     int prec = MOT_FP64;
     long n = 0;  // next step index
@@ -421,11 +431,10 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
         MOT_TRY(allow_smem<k_z_green<T>>());
         Octant oc = {p->M0[2], p->M0[1], p->K0[2], p->K0[1], H};
         dim3 grid((H + tw - 1) / tw, (unsigned)(nrhs * My));
-        p->kt.begin(st, kTimeZGreen);
+        if (!p->capturing) p->kt.begin(st, kTimeZGreen);
         count_launch();
         k_z_green<T><<<grid, 256, smem, st>>>(Bf, L0_of<T>(p), tz->plan, twp<T>(tz), Nz, My, H, tw, oc);
-        p->kt.end(st);
-        p->mvp_count += 1;
+        if (!p->capturing) p->kt.end(st);
         MOT_CHECK_LAUNCH();
     }
     MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
@@ -639,16 +648,9 @@ mot_status mot_ctx_create(int device, void *cuda_stream, mot_ctx **out) {
     MOT_CUDA_TRY(cudaSetDevice(device));
     mot_ctx *c = new mot_ctx();
     c->device = device;
-    if (cuda_stream) {
-        c->stream = (cudaStream_t)cuda_stream;
-    } else {
-        cudaError_t e2 = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-        if (e2 != cudaSuccess) {
-            delete c;
-            MOT_FAIL(MOT_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e2));
-        }
-        c->own_stream = true;
-    }
+    // NULL is the CUDA legacy default stream (the stream PyTorch uses by default)
+    c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = false;
     *out = c;
     return MOT_OK;
 }
@@ -889,10 +891,10 @@ template <typename V> KrylovView<V> kview(mot_run *r) {
     return k;
 }
 
-template <typename V> mot_status mvp(mot_run *r, const V *x, V *y) {
+template <typename V> mot_status mvp(mot_run *r, const V *x, V *y, cudaStream_t st) {
     mot_problem *p = r->p;
     EpiZ0<V, V> e = {x, y, (const double *)p->eps.p, (long)p->N[2] * p->N[1], p->N[0]};
-    return z0_product<V, V>(p, x, r->B, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+    return z0_product<V, V>(p, x, r->B, p->wsA.p, p->wsB.p, e, st);
 }
 
 template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ a, long n) {
@@ -900,11 +902,108 @@ template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restri
         w[i] = b[i] - a[i];
 }
 
+// loop control of a graph-captured solve: count the iteration and keep
+// looping while some right-hand side is active and the cap is not reached
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const TfqmrScal *sc, int B, int *ctl) {
+    __shared__ int active;
+    if (threadIdx.x == 0) active = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += blockDim.x)
+        if (sc[b].conv == 0) active = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int it = ctl[0] + 1;
+        ctl[0] = it;
+        cudaGraphSetConditional(h, (active && it < ctl[1]) ? 1u : 0u);
+    }
+}
+
+// one TFQMR iteration (two half steps, two Z0 products) on stream st
+template <typename V> mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st) {
+    mot_problem *p = r->p;
+    const int B = r->B;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    KrylovView<V> k = kview<V>(r);
+    dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    count_launch();
+    k_tfqmr_alpha<<<B, 32, 0, st>>>(k.sc, k.p3);
+    count_launch();
+    k_tfqmr_y2<V><<<gv, 256, 0, st>>>(k.v[kY2], k.v[kY1], k.v[kV], k.sc, L);
+    count_launch();
+    k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY1], k.v[kAY1], k.v[kRS], k.sc, L,
+                                                     k.p1, nullptr);
+    count_launch();
+    k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
+    MOT_CHECK_LAUNCH();
+    MOT_TRY(mvp<V>(r, k.v[kY2], k.v[kAY2], st));
+    count_launch();
+    k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L,
+                                                     k.p1, k.p2);
+    count_launch();
+    k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
+    count_launch();
+    k_tfqmr_beta<<<B, 32, 0, st>>>(k.sc, k.p2);
+    count_launch();
+    k_tfqmr_y1<V><<<gv, 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
+    MOT_CHECK_LAUNCH();
+    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
+    count_launch();
+    k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+// build the graph: while (cond) { tfqmr_body; k_loop_cond }
+template <typename V> mot_status build_loop_graph(mot_run *r, V *x, LoopGraph &G) {
+    mot_problem *p = r->p;
+    cudaGraph_t g = nullptr;
+    MOT_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    MOT_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    MOT_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const unsigned long long l0 = g_launches.load();
+    p->capturing = true;
+    MOT_CUDA_TRY(cudaStreamBeginCaptureToGraph(r->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    mot_status s = tfqmr_body<V>(r, x, r->cap);
+    count_launch();
+    k_loop_cond<<<1, 32, 0, r->cap>>>(h, (const TfqmrScal *)r->scal.p, r->B, (int *)r->ctl.p);
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(r->cap, &out);
+    p->capturing = false;
+    const unsigned long long l1 = g_launches.load();
+    g_launches.fetch_sub(l1 - l0);  // captured, not launched
+    if (s != MOT_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        MOT_FAIL(MOT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&G.exec, g, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        MOT_FAIL(MOT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    G.graph = g;
+    G.x = x;
+    G.body_kernels = (int)(l1 - l0);
+    return MOT_OK;
+}
+
 // TFQMR on Z0 y = rhs for the batch; x holds x0 on entry (x0 = 0 if zero_x0)
-// and the solution on exit.  Returns iterations (max over the batch).
+// and the solution on exit.  The iteration loop runs as one graph launch.
+// iters_out: iterations (max over the batch); mvps_out: Z0 products applied.
 template <typename V>
 mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
-                 bool *conv_out) {
+                 bool *conv_out, int *mvps_out) {
     mot_problem *p = r->p;
     cudaStream_t st = p->ctx->stream;
     const int B = r->B;
@@ -912,12 +1011,14 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     const long n = L * B;
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    int mvps = 0;
     // r0 = rhs - A x0  (into w)
     if (zero_x0) {
         MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
         MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
     } else {
-        MOT_TRY(mvp<V>(r, x, k.v[kAY1]));
+        MOT_TRY(mvp<V>(r, x, k.v[kAY1], st));
+        ++mvps;
         count_launch();
         k_sub<V><<<grid_for(n), 256, 0, st>>>(k.v[kW], rhs, k.v[kAY1], n);
         MOT_CHECK_LAUNCH();
@@ -936,54 +1037,30 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     count_launch();
     k_tfqmr_zero_done<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B);
     MOT_CHECK_LAUNCH();
-    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1]));
+    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
+    ++mvps;
     MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kV], k.v[kAY1], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
     count_launch();
     k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kRS], k.v[kV], L, k.p3);
     MOT_CHECK_LAUNCH();
-    std::vector<TfqmrScal> hs(B);
-    int it = 0;
-    bool all = false;
-    for (it = 0; it < maxit; ++it) {
-        MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), k.sc, sizeof(TfqmrScal) * B, cudaMemcpyDeviceToHost, st));
-        MOT_CUDA_TRY(cudaStreamSynchronize(st));
-        all = true;
-        for (int b = 0; b < B; ++b)
-            if (hs[b].conv == 0) all = false;
-        if (all) break;
-        count_launch();
-        k_tfqmr_alpha<<<B, 32, 0, st>>>(k.sc, k.p3);
-        count_launch();
-        k_tfqmr_y2<V><<<gv, 256, 0, st>>>(k.v[kY2], k.v[kY1], k.v[kV], k.sc, L);
-        count_launch();
-        k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY1], k.v[kAY1], k.v[kRS], k.sc, L,
-                                                         k.p1, nullptr);
-        count_launch();
-        k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
-        MOT_CHECK_LAUNCH();
-        MOT_TRY(mvp<V>(r, k.v[kY2], k.v[kAY2]));
-        count_launch();
-        k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L,
-                                                         k.p1, k.p2);
-        count_launch();
-        k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
-        count_launch();
-        k_tfqmr_beta<<<B, 32, 0, st>>>(k.sc, k.p2);
-        count_launch();
-        k_tfqmr_y1<V><<<gv, 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
-        MOT_CHECK_LAUNCH();
-        MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1]));
-        count_launch();
-        k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3);
-        MOT_CHECK_LAUNCH();
-    }
+    // the iteration loop: one graph launch
+    LoopGraph &G = sizeof(V) == 8 ? r->loop64 : r->loop32;
+    if (G.exec && G.x != (void *)x) MOT_FAIL(MOT_EINVAL, "solve graph bound to another vector");
+    if (!G.exec) MOT_TRY(build_loop_graph<V>(r, x, G));
+    int ctl_h[2] = {0, maxit};
+    MOT_CUDA_TRY(cudaMemcpyAsync(r->ctl.p, ctl_h, sizeof(ctl_h), cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaGraphLaunch(G.exec, st));
     count_launch();
     k_tfqmr_flush<V, V><<<gv, 256, 0, st>>>(x, k.v[kD], k.sc, L, 1);
     count_launch();
     k_tfqmr_settle<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B, 1);
     MOT_CHECK_LAUNCH();
+    std::vector<TfqmrScal> hs(B);
     MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), k.sc, sizeof(TfqmrScal) * B, cudaMemcpyDeviceToHost, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(ctl_h, r->ctl.p, sizeof(ctl_h), cudaMemcpyDeviceToHost, st));
     MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    g_launches.fetch_add((unsigned long long)G.body_kernels * ctl_h[0]);
+    mvps += 2 * ctl_h[0];
     int mx = 0;
     bool conv = true;
     for (int b = 0; b < B; ++b) {
@@ -992,6 +1069,7 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     }
     *iters_out = mx;
     *conv_out = conv;
+    *mvps_out = mvps;
     return MOT_OK;
 }
 
@@ -1088,7 +1166,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     const bool mixed = r->prec == MOT_MIXED;
     p->kt.on = p->opt.timing != 0;
     p->kt.reset();
-    const long mvp0 = p->mvp_count;
+    int mvps = 0;
     cudaEventRecord(r->ev[0], st);
     if (mixed) MOT_TRY(history_rhs<float>(r));
     else MOT_TRY(history_rhs<double>(r));
@@ -1102,13 +1180,16 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
         int it;
         bool c;
-        MOT_TRY(tfqmr<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, &it, &c));
+        int nm;
+        MOT_TRY(tfqmr<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, &it, &c, &nm));
+        mvps += nm;
         iters = it;
         conv = c;
         sweeps = 1;
         EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p, (const double *)p->eps.p, pr,
                          p->N[0]};
         MOT_TRY((z0_product<double, double>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+        ++mvps;
         MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
     } else {
         const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
@@ -1118,6 +1199,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
                              (const double *)p->eps.p, pr, p->N[0]};
             MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            ++mvps;
             MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
             bool done = true;
             for (int b = 0; b < r->B; ++b)
@@ -1128,7 +1210,9 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             MOT_CHECK_LAUNCH();
             int it;
             bool c;
-            MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c));
+            int nm;
+            MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm));
+            mvps += nm;
             iters += it;
             count_launch();
             k_add_into<double, float><<<grid_for(n), 256, 0, st>>>((double *)r->J.p, c32, n);
@@ -1151,7 +1235,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         cudaEventElapsedTime(&stats->ms_history, r->ev[0], r->ev[1]);
         cudaEventElapsedTime(&stats->ms_solve, r->ev[1], r->ev[2]);
         cudaEventElapsedTime(&stats->ms_push, r->ev[2], r->ev[3]);
-        stats->mvps = (int32_t)(p->mvp_count - mvp0);
+        stats->mvps = (int32_t)mvps;
         stats->ms_zhist = p->kt.total(kTimeZHist);
         stats->ms_zgreen = p->kt.total(kTimeZGreen);
     }
@@ -1216,6 +1300,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
             d.rref[i] = exc[b].khat[i] < 0 ? p->N[i] * p->h : 0.0;
             pol[3 * b + i] = exc[b].pol[i];
         }
+        planewave_factors(d, p->h);
         r->pw_host[b] = d;
     }
     mot_status s;
@@ -1241,6 +1326,8 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->part2, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->part3, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->dots, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->ctl, sizeof(int) * 2)) != MOT_OK) return fail(s);
+    if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
     // Z0 workspace for the batch in both precisions (FP64 residual / FP32 inner)
     size_t a, bb;
     z0_ws_bytes(p, nrhs, sizeof(double2), &a, &bb);
@@ -1314,6 +1401,12 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->dots);
     for (int i = 0; i < 4; ++i)
         if (r->ev[i]) cudaEventDestroy(r->ev[i]);
+    for (LoopGraph *G : {&r->loop64, &r->loop32}) {
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        if (G->graph) cudaGraphDestroy(G->graph);
+    }
+    dfree(r->ctl);
+    if (r->cap) cudaStreamDestroy(r->cap);
     delete r;
 }
 

@@ -285,32 +285,63 @@ struct PlaneWaveDev {
     double khat[3];
     double pol[3];
     double rref[3];
+    // factorisation of the 2x2x2 Gauss average: the point offsets are
+    // +-a (a = h/(2 sqrt 3)) per axis, so tau = tau_c - delta(s) with
+    // delta(s) = sum_i s_i beta_i, beta_i = khat_i a / c0, and
+    //   E(tau_c - delta) = E(tau_c) prod_i exp(s_i beta_i tau_c / sigma^2) C(s),
+    //   E(tau) = exp(-tau^2/(2 sigma^2) + i w tau), C(s) = exp(-delta^2/(2 sigma^2) - i w delta).
+    double beta[3];
+    double Cre[8], Cim[8], delta[8];
 };
 
+// host: fill beta, C(s), delta(s) of a plane wave for voxel size h
+inline void planewave_factors(PlaneWaveDev &P, double h) {
+    const double c0 = 299792458.0;
+    const double a = h / (2.0 * 1.7320508075688772935);
+    const double w = 2.0 * 3.141592653589793238462643 * P.f0;
+    for (int i = 0; i < 3; ++i) P.beta[i] = P.khat[i] * a / c0;
+    for (int q = 0; q < 8; ++q) {
+        double d = 0.0;
+        for (int i = 0; i < 3; ++i) d += ((q >> i) & 1 ? 1.0 : -1.0) * P.beta[i];
+        double mag = exp(-0.5 * d * d / (P.sigma * P.sigma));
+        P.Cre[q] = mag * cos(w * d);
+        P.Cim[q] = -mag * sin(w * d);
+        P.delta[q] = d;
+    }
+}
+
+// inc[b][m] = (eps_r(m) - 1) eps0 E0 (1/8) sum_s g'(tau_c - delta(s)),
+// g'(tau) = Re[(-tau/sigma^2 + i w) E(tau)] / (sigma sqrt(2 pi))
 __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ eps,
                            const PlaneWaveDev *__restrict__ pw, int Nx, int Ny, int Nz, double h, double t,
                            int nrhs) {
     const long n = (long)Nx * Ny * Nz;
     const double c0 = 299792458.0, eps0 = 8.8541878128e-12;
-    const double g0 = 0.21132486540518711775, g1 = 0.78867513459481288225;  // 1/2 -+ 1/(2 sqrt 3)
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n * nrhs; i += (long)gridDim.x * blockDim.x) {
         long b = i / n, m = i - b * n;
         double ep = eps[m];
         if (ep == 1.0) { inc[i] = 0.0; continue; }
         int mx = (int)(m % Nx), my = (int)((m / Nx) % Ny), mz = (int)(m / ((long)Nx * Ny));
-        const PlaneWaveDev P = pw[b];
+        const PlaneWaveDev &P = pw[b];
         const double w = 2.0 * 3.141592653589793238462643 * P.f0;
         const double amp = P.E0 / (P.sigma * 2.5066282746310005024);  // sigma sqrt(2 pi)
         const double is2 = 1.0 / (P.sigma * P.sigma);
+        double rx = (mx + 0.5) * h - P.rref[0], ry = (my + 0.5) * h - P.rref[1], rz = (mz + 0.5) * h - P.rref[2];
+        double tc = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
+        double s, c;
+        sincos(w * tc, &s, &c);
+        double g = exp(-0.5 * tc * tc * is2);
+        double Er = g * c, Ei = g * s;
+        double u0 = exp(P.beta[0] * tc * is2), u1 = exp(P.beta[1] * tc * is2), u2 = exp(P.beta[2] * tc * is2);
+        double v0 = 1.0 / u0, v1 = 1.0 / u1, v2 = 1.0 / u2;
         double acc = 0.0;
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            double rx = (mx + ((q & 1) ? g1 : g0)) * h - P.rref[0];
-            double ry = (my + ((q & 2) ? g1 : g0)) * h - P.rref[1];
-            double rz = (mz + ((q & 4) ? g1 : g0)) * h - P.rref[2];
-            double tau = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
-            double s, c;
-            sincos(w * tau, &s, &c);
-            acc += exp(-0.5 * tau * tau * is2) * (-tau * is2 * c - w * s);
+            double f = ((q & 1) ? u0 : v0) * ((q & 2) ? u1 : v1) * ((q & 4) ? u2 : v2);
+            double zr = f * (Er * P.Cre[q] - Ei * P.Cim[q]);
+            double zi = f * (Er * P.Cim[q] + Ei * P.Cre[q]);
+            double tau = tc - P.delta[q];
+            acc += -tau * is2 * zr - w * zi;  // Re[(-tau/sigma^2 + i w)(zr + i zi)]
         }
         inc[i] = (ep - 1.0) * eps0 * amp * 0.125 * acc;
     }
