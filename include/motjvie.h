@@ -143,6 +143,31 @@ void mot_problem_destroy(mot_problem *p);
  * (workspace), MOT_ECUDA.                                                     */
 mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
 
+/* Byte size of the scratch array behind mot_apply_Z0_static (64 MiB).        */
+#define MOT_STATIC_SCRATCH_BYTES (64ull << 20)
+
+/* y = Z0 x exactly as mot_apply_Z0 computes it, for callers that must not
+ * allocate device memory when they call in: code that runs while a CUDA
+ * stream capture is open (allocation is not a capturable stream operation),
+ * callers that run under a pool or budget that forbids new allocations, and
+ * real-time loops where a cudaMalloc stall is not acceptable.  This call
+ * allocates nothing: its scratch is one file-scope __device__ array of
+ * MOT_STATIC_SCRATCH_BYTES bytes that every GPU which loads the library holds
+ * until the process exits.  (No counterpart in the paper: an ABI addition.)
+ * - The first call on a device resolves the array's device address with
+ *   cudaGetSymbolAddress (with that device current); make that first call
+ *   before any stream capture.
+ * - All calls share the one array, which keeps the previous call's contents:
+ *   every scratch element is written before it is read, so nothing needs to
+ *   start at zero.  Calls whose kernels overlap on the GPU (other streams or
+ *   threads) race on the array; order them on one stream.
+ * - x_dev, y_dev, nrhs, dtype as mot_apply_Z0.  The scratch needed is
+ *   nrhs * 3 * Nz * (Ny + M0y) * (M0x/2 + 1) complex elements of dtype; a
+ *   request above MOT_STATIC_SCRATCH_BYTES fails with MOT_EINVAL (message
+ *   gives both sizes) before any device work.
+ * Errors: MOT_EINVAL, MOT_ECUDA.                                              */
+mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
+
 /* The library's own Galerkin table of lag `lag` (0 <= lag <= ell):
  * g_out[6][2Rz+1][2Ry+1][2Rx+1] doubles, components (xx, yy, zz, xy, xz, yz),
  * offset d = (dx, dy, dz) at index (dz+Rz, dy+Ry, dx+Rx); R_out receives

@@ -25,6 +25,7 @@ MOT_FP64 = 0
 MOT_MIXED = 1
 MOT_F64 = 0
 MOT_F32 = 1
+MOT_STATIC_SCRATCH_BYTES = 64 << 20
 
 __all__ = [
     "LIB_PATH", "MotError", "lib", "mot_planewave", "mot_options", "mot_problem_info", "mot_step_stats",
@@ -33,6 +34,7 @@ __all__ = [
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
     "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
+    "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES",
 ]
 
 # every symbol include/motjvie.h declares
@@ -40,7 +42,7 @@ EXPORTED = [
     "mot_last_error", "mot_ctx_create", "mot_ctx_destroy", "mot_problem_create", "mot_problem_info_get",
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
-    "mot_kernel_launches",
+    "mot_kernel_launches", "mot_apply_Z0_static",
 ]
 
 
@@ -92,6 +94,7 @@ def lib():
         L.mot_problem_destroy.argtypes = [P]
         L.mot_problem_destroy.restype = None
         L.mot_apply_Z0.argtypes = [P, P, P, I, I]
+        L.mot_apply_Z0_static.argtypes = [P, P, P, I, I]
         L.mot_kernel_table.argtypes = [P, I, P, P]
         L.mot_set_kernel_table.argtypes = [P, I, P, P]
         L.mot_table_host.argtypes = [D, I, P, P]
@@ -164,6 +167,11 @@ def mot_problem_destroy(prob):
 
 def mot_apply_Z0(prob, x_dev, y_dev, nrhs: int, dtype: int):
     _check(lib().mot_apply_Z0(prob, _ptr(x_dev), _ptr(y_dev), int(nrhs), int(dtype)))
+
+
+def mot_apply_Z0_static(prob, x_dev, y_dev, nrhs: int, dtype: int):
+    """y = Z0 x using the library's static device scratch (no allocation)."""
+    _check(lib().mot_apply_Z0_static(prob, _ptr(x_dev), _ptr(y_dev), int(nrhs), int(dtype)))
 
 
 def mot_kernel_table(prob, lag: int):

@@ -1411,3 +1411,44 @@ void mot_run_destroy(mot_run *r) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Z0 product without allocation: scratch in a file-scope device array
+// ============================================================================
+// The array's device address is resolved once per device (host code cannot
+// use the symbol itself as a device pointer).
+static __device__ __align__(256) unsigned char g_static_scratch[MOT_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void *g_static_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
+    if (!p || !x_dev || !y_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
+    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
+    const int dev = p->ctx->device;
+    if (dev < 0 || dev >= kMaxDevices) MOT_FAIL(MOT_EINVAL, "device index beyond the static-scratch table");
+    size_t a, b;
+    z0_ws_bytes(p, nrhs, dtype == MOT_F64 ? sizeof(double2) : sizeof(float2), &a, &b);
+    a = (a + 255) / 256 * 256;
+    if (a + b > (size_t)MOT_STATIC_SCRATCH_BYTES)
+        MOT_FAIL(MOT_EINVAL, "mot_apply_Z0_static needs " + std::to_string(a + b) + " bytes of scratch; the static array holds " +
+                                 std::to_string((size_t)MOT_STATIC_SCRATCH_BYTES));
+    MOT_CUDA_TRY(cudaSetDevice(dev));
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        MOT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_ptr[dev] = ptr;
+    }
+    char *ws = (char *)g_static_ptr[dev];
+    const long pr = (long)p->N[2] * p->N[1];
+    if (dtype == MOT_F64) {
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+        return z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+    }
+    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+    return z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+}

@@ -1,0 +1,62 @@
+"""mot_apply_Z0_static: the Z0 product for callers that cannot allocate device
+memory when they call in (open stream captures, allocation-free pools,
+real-time loops).  Its scratch is the library's file-scope device array, so the
+call allocates nothing; this checks it against mot_apply_Z0, which uses
+allocated scratch, on two calls in a row (the array keeps the previous call's
+contents), with the parity tolerances used elsewhere (FP64 1e-10, FP32 1e-5
+relative L2), and that an oversized request is refused before any GPU work.
+
+This file is named to be collected last, so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+import paper_2607_28309_b300 as mot
+from paper_2607_28309_b300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+
+
+def test_static_scratch_product_matches_allocating_product():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2607_28309_b300 import build
+
+    build.build()
+    ctx = mot.mot_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        N, alpha = (24, 20, 18), 8.0
+        eps = synthetic.block_eps(N, 4, 1.5, 6.0, 33)
+        prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+        try:
+            nv = int(np.prod(N))
+            gen = torch.Generator(device="cuda").manual_seed(5)
+            for dtype, tdt, tol in ((mot.MOT_F64, torch.float64, 1e-10), (mot.MOT_F32, torch.float32, 1e-5)):
+                for nrhs in (1, 3):
+                    x = torch.randn(nrhs, 3, nv, device="cuda", dtype=tdt, generator=gen)
+                    ref = torch.empty_like(x)
+                    mot.mot_apply_Z0(prob, x, ref, nrhs, dtype)
+                    for _ in range(2):  # two calls in a row share the static scratch
+                        y = torch.full_like(x, float("nan"))
+                        mot.mot_apply_Z0_static(prob, x, y, nrhs, dtype)
+                        torch.cuda.synchronize()
+                        assert torch.isfinite(y).all()
+                        assert _rel(y, ref) <= tol
+            # a request beyond the static array is refused with MOT_EINVAL
+            big = 1 + mot.MOT_STATIC_SCRATCH_BYTES // (3 * N[2] * N[1] * 16 * 16)
+            x = torch.zeros(big, 3, nv, device="cuda", dtype=torch.float64)
+            y = torch.zeros_like(x)
+            with pytest.raises(mot.MotError) as e:
+                mot.mot_apply_Z0_static(prob, x, y, big, mot.MOT_F64)
+            assert e.value.status == mot.MOT_EINVAL
+        finally:
+            mot.mot_problem_destroy(prob)
+    finally:
+        mot.mot_ctx_destroy(ctx)
