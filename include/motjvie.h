@@ -87,6 +87,9 @@ typedef struct {
                          kernels of every step with CUDA events (fills
                          ms_zhist / ms_zgreen of mot_step_stats; adds event
                          overhead).  Default 0                                     */
+    int guess;        /* initial guess of each step's solve (the paper does not
+                         specify one): 0 = J_{n-1}; 1 = 2 J_{n-1} - J_{n-2}
+                         (linear extrapolation, default)                           */
 } mot_options;
 
 typedef struct {

@@ -3,6 +3,7 @@
 // matrix-free Z0 product (Eq. 11-12), the history right-hand side (Eq. 3),
 // the TFQMR solve of each step and the history ring.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -18,6 +19,7 @@
 #include "tables.cuh"
 
 #include <atomic>
+#include <mutex>
 
 namespace mot {
 static thread_local std::string g_err;
@@ -173,6 +175,40 @@ void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
             }
 }
 
+// process-wide cache of quadrature results: the lag tables depend only on
+// rho, the table extents and the lag range (not on eps_r), so problems that
+// share them reuse the A values instead of recomputing the quadrature
+struct TableCacheEntry {
+    double rho;
+    int S[3], k0, k1;
+    std::vector<double> A6;
+};
+std::mutex g_tcache_mu;
+std::vector<TableCacheEntry> g_tcache;
+constexpr size_t kTableCacheEntries = 8;
+
+bool tcache_get(double rho, const int S[3], int k0, int k1, std::vector<double> &A6) {
+    std::lock_guard<std::mutex> lk(g_tcache_mu);
+    for (auto &e : g_tcache)
+        if (e.rho == rho && e.S[0] == S[0] && e.S[1] == S[1] && e.S[2] == S[2] && e.k0 == k0 && e.k1 == k1) {
+            A6 = e.A6;
+            return true;
+        }
+    return false;
+}
+
+void tcache_put(double rho, const int S[3], int k0, int k1, std::vector<double> &&A6) {
+    std::lock_guard<std::mutex> lk(g_tcache_mu);
+    if (g_tcache.size() >= kTableCacheEntries) g_tcache.erase(g_tcache.begin());
+    TableCacheEntry e;
+    e.rho = rho;
+    for (int i = 0; i < 3; ++i) e.S[i] = S[i];
+    e.k0 = k0;
+    e.k1 = k1;
+    e.A6 = std::move(A6);
+    g_tcache.push_back(std::move(e));
+}
+
 // per-lag map triple -> item (or -1), from the offset-major ranges
 void lag_map(const ItemSet &is, int k, std::vector<int> &map) {
     map.assign(is.base.size(), -1);
@@ -205,7 +241,8 @@ void axis_coef(int M, int R, bool odd, std::vector<double> &cf) {
 // ============================================================================
 struct AxisTw {
     int M = 0;
-    FftPlan plan{};
+    FftPlan plan{};    // FP32 passes
+    FftPlan plan64{};  // FP64 passes (radix <= 9: register pressure)
     DBuf tw64, tw32;
 };
 
@@ -274,7 +311,7 @@ struct mot_problem {
     int K0[3], Kh[3];
     int r0;
     std::vector<double> eps_host;
-    DBuf eps;
+    DBuf eps, eps32;  // eps_r in FP64 and FP32
     std::vector<AxisTw *> tws;
     std::vector<LagTable> lags;
     DBuf L0_64, L0_32;  // [6][K0z][K0y][H0]
@@ -302,7 +339,7 @@ struct mot_run {
     int prec = MOT_FP64;
     long n = 0;  // next step index
     std::vector<PlaneWaveDev> pw_host;
-    DBuf pw, inc, J, b, r;
+    DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
     DBuf ring, wsAh, wsBh;
     // Krylov vectors (type of the solve) and scratch
     DBuf kv[10];
@@ -318,7 +355,10 @@ AxisTw *get_tw(mot_problem *p, int M) {
         if (t->M == M) return t;
     AxisTw *t = new AxisTw();
     t->M = M;
-    if (!make_plan(M, &t->plan)) {
+    // largest register radix of the FP32 passes (tuning knob, default 16)
+    int max_radix = 16;
+    if (const char *ev = getenv("MOTJVIE_MAX_RADIX")) max_radix = std::max(2, atoi(ev));
+    if (!make_plan(M, &t->plan, max_radix) || !make_plan(M, &t->plan64, std::min(max_radix, 9))) {
         delete t;
         return nullptr;
     }
@@ -340,11 +380,18 @@ AxisTw *get_tw(mot_problem *p, int M) {
     return t;
 }
 
+template <typename T> const FftPlan &planp(AxisTw *t);
+template <> const FftPlan &planp<double>(AxisTw *t) { return t->plan64; }
+template <> const FftPlan &planp<float>(AxisTw *t) { return t->plan; }
+
 template <typename T> const cplx<T> *twp(AxisTw *t);
 template <> const cplx<double> *twp<double>(AxisTw *t) { return (const double2 *)t->tw64.p; }
 template <> const cplx<float> *twp<float>(AxisTw *t) { return (const float2 *)t->tw32.p; }
 
 const size_t kSmemMax = 200 * 1024;
+// block sizes: the pencil passes are latency-bound at small grids, so they use
+// large CTAs to keep enough warps resident
+constexpr int kZThreads = 512;
 
 // raise the dynamic shared-memory limit of one kernel, once per kernel
 template <auto Kern> mot_status allow_smem() {
@@ -365,13 +412,13 @@ mot_status launch_x_forward(const TI *x, cplx<T> *out, long nrows, int Nx, int H
     MOT_TRY(allow_smem<k_x_forward<TI, T>>());
     long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
     count_launch();
-    k_x_forward<TI, T><<<(unsigned)grid, 256, smem, st>>>(x, out, nrows, Nx, H, tw->plan, twp<T>(tw), pairs);
+    k_x_forward<TI, T><<<(unsigned)grid, 256, smem, st>>>(x, out, nrows, Nx, H, planp<T>(tw), twp<T>(tw), pairs);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
 
 template <typename T> int tile_width(int M, int comps) {
-    int tx = sizeof(T) == 4 ? 16 : 8;
+    int tx = comps > 1 ? (sizeof(T) == 4 ? 8 : 4) : (sizeof(T) == 4 ? 16 : 8);
     while (tx > 1 && (size_t)(2 * comps * M * tx + M) * sizeof(cplx<T>) > kSmemMax) tx /= 2;
     return tx;
 }
@@ -385,7 +432,7 @@ mot_status launch_axis(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int L
     MOT_TRY(allow_smem<k_axis<T, S>>());
     dim3 grid((H + tx - 1) / tx, (unsigned)(O1 * O2));
     count_launch();
-    k_axis<T, S><<<grid, 256, smem, st>>>(in, out, tw->plan, twp<T>(tw), H, tx, Lin, Lout, O2, is1, is2, ias, os1,
+    k_axis<T, S><<<grid, kZThreads, smem, st>>>(in, out, planp<T>(tw), twp<T>(tw), H, tx, Lin, Lout, O2, is1, is2, ias, os1,
                                           os2, oas);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
@@ -399,10 +446,36 @@ mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw
     MOT_TRY(allow_smem<k_x_inverse<T, Epi>>());
     long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
     count_launch();
-    k_x_inverse<T, Epi><<<(unsigned)grid, 256, smem, st>>>(in, nrows, Nx, H, tw->plan, twp<T>(tw), pairs, epi);
+    k_x_inverse<T, Epi><<<(unsigned)grid, 256, smem, st>>>(in, nrows, Nx, H, planp<T>(tw), twp<T>(tw), pairs, epi);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
+
+template <typename TI, typename T>
+mot_status launch_xy_forward(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, int H, AxisTw *tx, AxisTw *ty,
+                             cudaStream_t st) {
+    size_t smem = xy_smem_bytes<T>(tx->M, ty->M, H, Ny);
+    MOT_TRY(allow_smem<k_xy_forward<TI, T>>());
+    count_launch();
+    k_xy_forward<TI, T><<<planes, kXYThreadsOf<T>, smem, st>>>(x, out, Nx, Ny, H, planp<T>(tx), planp<T>(ty), twp<T>(tx), twp<T>(ty));
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+template <typename T, class Epi>
+mot_status launch_xy_inverse(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, int H, AxisTw *tx, AxisTw *ty,
+                             Epi epi, cudaStream_t st) {
+    size_t smem = xy_smem_bytes<T>(tx->M, ty->M, H, Ny);
+    MOT_TRY(allow_smem<k_xy_inverse<T, Epi>>());
+    count_launch();
+    k_xy_inverse<T, Epi><<<planes, kXYThreadsOf<T>, smem, st>>>(in, Nx, Ny, Nz, H, planp<T>(tx), planp<T>(ty), twp<T>(tx), twp<T>(ty), epi);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+template <typename T> const T *eps_of(mot_problem *p);
+template <> const double *eps_of<double>(mot_problem *p) { return (const double *)p->eps.p; }
+template <> const float *eps_of<float>(mot_problem *p) { return (const float *)p->eps32.p; }
 
 template <typename T> const T *L0_of(mot_problem *p);
 template <> const double *L0_of<double>(mot_problem *p) { return (const double *)p->L0_64.p; }
@@ -423,8 +496,13 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
     C *A = (C *)wsA, *Bf = (C *)wsB;
     const long nrows = (long)nrhs * 3 * Nz * Ny;
     const int planes = nrhs * 3 * Nz;
-    MOT_TRY(launch_x_forward<TI, T>(x, A, nrows, Nx, H, tx, st));
-    MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    const size_t xy_smem = xy_smem_bytes<T>(p->M0[0], My, H, Ny);
+    const bool fused = xy_smem <= kSmemMax;
+    if (fused) MOT_TRY(launch_xy_forward<TI, T>(x, Bf, planes, Nx, Ny, H, tx, ty, st));
+    else {
+        MOT_TRY(launch_x_forward<TI, T>(x, A, nrows, Nx, H, tx, st));
+        MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    }
     {
         int tw = tile_width<T>(p->M0[2], 3);
         size_t smem = (size_t)(6 * p->M0[2] * tw + p->M0[2]) * sizeof(C);
@@ -433,12 +511,15 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
         dim3 grid((H + tw - 1) / tw, (unsigned)(nrhs * My));
         if (!p->capturing) p->kt.begin(st, kTimeZGreen);
         count_launch();
-        k_z_green<T><<<grid, 256, smem, st>>>(Bf, L0_of<T>(p), tz->plan, twp<T>(tz), Nz, My, H, tw, oc);
+        k_z_green<T><<<grid, kZThreads, smem, st>>>(Bf, L0_of<T>(p), planp<T>(tz), twp<T>(tz), Nz, My, H, tw, oc);
         if (!p->capturing) p->kt.end(st);
         MOT_CHECK_LAUNCH();
     }
-    MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
-    MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
+    if (fused) MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
+    else {
+        MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+        MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
+    }
     return MOT_OK;
 }
 
@@ -465,13 +546,21 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
     MOT_TRY(dalloc(ditems, sizeof(TableItem) * std::max(1, nit)));
     MOT_TRY(dalloc(dA, sizeof(double) * 6 * std::max(1, nit)));
     MOT_TRY(dalloc(dmap, sizeof(int) * is.base.size()));
-    MOT_CUDA_TRY(cudaMemcpyAsync(ditems.p, is.items.data(), sizeof(TableItem) * nit, cudaMemcpyHostToDevice, st));
-    if (nit > 0) {
+    std::vector<double> cached;
+    if (nit > 0 && tcache_get(p->rho, S, k0, k1, cached) && cached.size() == 6 * (size_t)nit) {
+        MOT_CUDA_TRY(cudaMemcpyAsync(dA.p, cached.data(), sizeof(double) * 6 * nit, cudaMemcpyHostToDevice, st));
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (nit > 0) {
+        MOT_CUDA_TRY(cudaMemcpyAsync(ditems.p, is.items.data(), sizeof(TableItem) * nit, cudaMemcpyHostToDevice, st));
         count_launch();
         k_galerkin_items<<<(nit + 63) / 64, 64, 0, st>>>((const TableItem *)ditems.p, nit, p->rho,
                                                          (const double *)p->glx.p, (const double *)p->glw.p, kGLN,
                                                          (double *)dA.p);
         MOT_CHECK_LAUNCH();
+        std::vector<double> A6(6 * (size_t)nit);
+        MOT_CUDA_TRY(cudaMemcpyAsync(A6.data(), dA.p, sizeof(double) * 6 * nit, cudaMemcpyDeviceToHost, st));
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+        tcache_put(p->rho, S, k0, k1, std::move(A6));
     }
     std::vector<int> map;
     for (int k = k0; k <= k1; ++k) {
@@ -707,10 +796,11 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     long nv = (long)n[0] * n[1] * n[2];
     for (long i = 0; i < nv; ++i)
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
-    mot_options o = {0.0, 500, 1e-4, 6, 0.0, 0};
+    mot_options o = {0.0, 500, 1e-4, 6, 0.0, 0, 1};
     if (opt) o = *opt;
     if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
+    if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
     MOT_CUDA_TRY(cudaSetDevice(ctx->device));
     mot_problem *p = new mot_problem();
     p->ctx = ctx;
@@ -742,6 +832,12 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     if ((s = dalloc(p->eps, sizeof(double) * nv)) != MOT_OK) return fail(s);
     if (cudaMemcpyAsync(p->eps.p, eps_r, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
         return fail(MOT_ECUDA);
+    {
+        std::vector<float> e32(eps_r, eps_r + nv);
+        if ((s = dalloc(p->eps32, sizeof(float) * nv)) != MOT_OK) return fail(s);
+        if (cudaMemcpy(p->eps32.p, e32.data(), sizeof(float) * nv, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(MOT_ECUDA);
+    }
     {
         const HostRule &hr = host_rule();
         if ((s = dalloc(p->glx, sizeof(double) * kGLN)) != MOT_OK) return fail(s);
@@ -779,6 +875,7 @@ void mot_problem_destroy(mot_problem *p) {
     cudaSetDevice(p->ctx->device);
     cudaStreamSynchronize(p->ctx->stream);
     dfree(p->eps);
+    dfree(p->eps32);
     for (auto *t : p->tws) {
         dfree(t->tw64);
         dfree(t->tw32);
@@ -808,10 +905,10 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
     MOT_TRY(dalloc(p->wsB, b));
     const long pr = (long)p->N[2] * p->N[1];
     if (dtype == MOT_F64) {
-        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
         return z0_product<double, double>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
     }
-    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
 }
 
@@ -893,8 +990,17 @@ template <typename V> KrylovView<V> kview(mot_run *r) {
 
 template <typename V> mot_status mvp(mot_run *r, const V *x, V *y, cudaStream_t st) {
     mot_problem *p = r->p;
-    EpiZ0<V, V> e = {x, y, (const double *)p->eps.p, (long)p->N[2] * p->N[1], p->N[0]};
+    EpiZ0<V, V> e = {x, y, eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0]};
     return z0_product<V, V>(p, x, r->B, p->wsA.p, p->wsB.p, e, st);
+}
+
+// x0 = 2 J_{n-1} - J_{n-2} in J, and J_{n-1} saved into J2
+__global__ void k_extrapolate(double *__restrict__ J, double *__restrict__ J2, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double a = J[i];
+        J[i] = 2.0 * a - J2[i];
+        J2[i] = a;
+    }
 }
 
 template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ a, long n) {
@@ -1089,8 +1195,12 @@ template <typename T> mot_status ring_push(mot_run *r) {
     using C = cplx<T>;
     C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
     const long nrows = (long)r->B * 3 * Nz * Ny;
-    MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
-    MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    if (xy_smem_bytes<T>(p->Mh[0], My, H, Ny) <= kSmemMax) {
+        MOT_TRY((launch_xy_forward<double, T>((const double *)r->J.p, Bf, r->B * 3 * Nz, Nx, Ny, H, tx, ty, st)));
+    } else {
+        MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
+        MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+    }
     C *slot = (C *)ring_slot<T>(r, r->n % p->ell);
     MOT_TRY((launch_axis<T, -1>(Bf, slot, tz, H, Nz, Mz, r->B * 3, My, (long)Nz * My * H, H, (long)My * H,
                                 (long)Mz * My * H, H, (long)My * H, st)));
@@ -1109,24 +1219,29 @@ template <typename T> mot_status history_rhs(mot_run *r) {
     C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
     const double t = (double)r->n * p->dt;
     count_launch();
-    k_incident<<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
-                                                   (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
+    if (sizeof(T) == 4)
+        k_incident<true><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
+                                                             (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
+    else
+        k_incident<false><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
+                                                              (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
     MOT_CHECK_LAUNCH();
     const int kmax = (int)std::min<long>(r->n, p->ell);
     {
-        int tw = tile_width<T>(Mz, 3);
-        size_t smem = (size_t)(6 * Mz * tw + Mz) * sizeof(C);
-        MOT_TRY(allow_smem<k_z_history<T>>());
+        // ~100 KB of shared memory per CTA keeps two CTAs resident per SM
+        int tw = sizeof(T) == 4 ? 8 : 4;
+        while (tw > 1 && (size_t)(12 * Mz * tw + Mz) * sizeof(C) > 112 * 1024) tw /= 2;
+        size_t smem = (size_t)(12 * Mz * tw + Mz) * sizeof(C);
+        MOT_TRY(allow_smem<k_z_history2<T>>());
         Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
-        dim3 grid((H + tw - 1) / tw, (unsigned)(r->B * My));
+        dim3 grid((H + tw - 1) / tw, (unsigned)(r->B * (My / 2 + 1)));
         p->kt.begin(st, kTimeZHist);
         count_launch();
-        k_z_history<T><<<grid, 256, smem, st>>>((const C *)r->ring.p, Lh_of<T>(p), Bf, tz->plan, twp<T>(tz), Nz, My,
-                                                H, tw, oc, r->B, p->ell, r->n, kmax);
+        k_z_history2<T><<<grid, kZThreads, smem, st>>>((const C *)r->ring.p, Lh_of<T>(p), Bf, planp<T>(tz), twp<T>(tz), Nz, My,
+                                                 H, tw, oc, r->B, p->ell, r->n, kmax);
         p->kt.end(st);
         MOT_CHECK_LAUNCH();
     }
-    MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
     EpiHistory e;
     e.inc = (const double *)r->inc.p;
     e.pol = nullptr;  // set below
@@ -1137,7 +1252,12 @@ template <typename T> mot_status history_rhs(mot_run *r) {
     e.Nx = Nx;
     e.nvox = nv;
     e.pol = (const double *)((const char *)r->pw.p + r->B * sizeof(PlaneWaveDev));
-    MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
+    if (xy_smem_bytes<T>(p->Mh[0], My, H, Ny) <= kSmemMax) {
+        MOT_TRY((launch_xy_inverse<T, EpiHistory>(Bf, r->B * 3 * Nz, Nx, Ny, Nz, H, tx, ty, e, st)));
+    } else {
+        MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+        MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
+    }
     return MOT_OK;
 }
 
@@ -1171,6 +1291,11 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     if (mixed) MOT_TRY(history_rhs<float>(r));
     else MOT_TRY(history_rhs<double>(r));
     cudaEventRecord(r->ev[1], st);
+    if (p->opt.guess == 1) {
+        count_launch();
+        k_extrapolate<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, n);
+        MOT_CHECK_LAUNCH();
+    }
     int iters = 0, sweeps = 0;
     bool conv = true;
     std::vector<double> bn(r->B), rn(r->B);
@@ -1312,6 +1437,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     const size_t vs = mixed ? sizeof(float) : sizeof(double);
     if ((s = dalloc(r->inc, sizeof(double) * nv * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->J, sizeof(double) * n)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->J2, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->b, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->r, sizeof(double) * n)) != MOT_OK) return fail(s);
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
@@ -1336,6 +1462,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     cudaStream_t st = p->ctx->stream;
     cudaMemsetAsync(r->ring.p, 0, ring_bytes, st);
     cudaMemsetAsync(r->J.p, 0, sizeof(double) * n, st);
+    cudaMemsetAsync(r->J2.p, 0, sizeof(double) * n, st);
     for (int i = 0; i < 4; ++i)
         if (cudaEventCreate(&r->ev[i]) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MOT_ECUDA);
@@ -1387,6 +1514,7 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->pw);
     dfree(r->inc);
     dfree(r->J);
+    dfree(r->J2);
     dfree(r->b);
     dfree(r->r);
     dfree(r->ring);
@@ -1446,9 +1574,9 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
     char *ws = (char *)g_static_ptr[dev];
     const long pr = (long)p->N[2] * p->N[1];
     if (dtype == MOT_F64) {
-        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
         return z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
     }
-    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, (const double *)p->eps.p, pr, p->N[0]};
+    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
 }

@@ -17,22 +17,54 @@ namespace mot {
 
 constexpr int kMaxStages = 12;
 
+// division by a runtime constant d for dividends below 2^24:
+// q = (x * m) >> s with s = 24 + ceil(log2 d), m = ceil(2^s / d)  (Granlund-Montgomery)
+struct FastDiv {
+    unsigned int m;
+    int s;
+};
+__host__ __device__ inline FastDiv make_fastdiv(unsigned int d) {
+    int l = 0;
+    while ((1u << l) < d) ++l;
+    FastDiv f;
+    f.s = 24 + l;
+    f.m = (unsigned int)(((1ull << f.s) + d - 1) / d);
+    return f;
+}
+__host__ __device__ __forceinline__ unsigned int fdiv(unsigned int x, FastDiv f) {
+    return (unsigned int)(((unsigned long long)x * f.m) >> f.s);
+}
+
 struct FftPlan {
     int M;
     int nstage;
     int radix[kMaxStages];
+    FastDiv ns_div[kMaxStages];   // division by Ns (product of earlier radices)
+    FastDiv nbf_div[kMaxStages];  // division by M / radix
 };
 
-// host: split M into radices 4, 2 (at most one), 3, 5; returns false if M has
-// another prime factor
-inline bool make_plan(int M, FftPlan *pl) {
+// host: split M into radices (16 when max_radix allows, then 9, 8, 4, 2, 3,
+// 5: fewer, register-resident stages); false if M has another prime factor
+inline bool make_plan(int M, FftPlan *pl, int max_radix = 16) {
     pl->M = M;
     pl->nstage = 0;
     int m = M;
+    if (max_radix >= 16)
+        while (m % 16 == 0) { pl->radix[pl->nstage++] = 16; m /= 16; }
+    if (max_radix >= 9)
+        while (m % 9 == 0) { pl->radix[pl->nstage++] = 9; m /= 9; }
+    if (max_radix >= 8)
+        while (m % 8 == 0) { pl->radix[pl->nstage++] = 8; m /= 8; }
     while (m % 4 == 0) { pl->radix[pl->nstage++] = 4; m /= 4; }
     while (m % 2 == 0) { pl->radix[pl->nstage++] = 2; m /= 2; }
     while (m % 3 == 0) { pl->radix[pl->nstage++] = 3; m /= 3; }
     while (m % 5 == 0) { pl->radix[pl->nstage++] = 5; m /= 5; }
+    int ns = 1;
+    for (int s = 0; s < pl->nstage; ++s) {
+        pl->ns_div[s] = make_fastdiv((unsigned)ns);
+        pl->nbf_div[s] = make_fastdiv((unsigned)(M / pl->radix[s]));
+        ns *= pl->radix[s];
+    }
     return m == 1 && pl->nstage <= kMaxStages;
 }
 
@@ -91,20 +123,104 @@ template <int S, typename C> __device__ __forceinline__ void dft5(C *v) {
     v[3] = csub(b2, d2);
 }
 
+// cos / sin of 2 pi j / N for the register-resident composite radices
+template <int N> struct Root;
+template <> struct Root<8> {
+    static constexpr double h = 0.70710678118654752440;  // cos(pi/4)
+    __host__ __device__ static constexpr double c(int j) {
+        return (j & 7) == 0 ? 1.0 : (j & 7) == 1 ? h : (j & 7) == 2 ? 0.0 : (j & 7) == 3 ? -h
+             : (j & 7) == 4 ? -1.0 : (j & 7) == 5 ? -h : (j & 7) == 6 ? 0.0 : h;
+    }
+    __host__ __device__ static constexpr double s(int j) { return c(j + 6); }  // sin x = cos(x - pi/2)
+};
+template <> struct Root<16> {
+    static constexpr double a = 0.92387953251128675613, b = 0.38268343236508977173, h = 0.70710678118654752440;
+    __host__ __device__ static constexpr double c(int j) {
+        return (j & 15) == 0 ? 1.0 : (j & 15) == 1 ? a : (j & 15) == 2 ? h : (j & 15) == 3 ? b
+             : (j & 15) == 4 ? 0.0 : (j & 15) == 5 ? -b : (j & 15) == 6 ? -h : (j & 15) == 7 ? -a
+             : (j & 15) == 8 ? -1.0 : (j & 15) == 9 ? -a : (j & 15) == 10 ? -h : (j & 15) == 11 ? -b
+             : (j & 15) == 12 ? 0.0 : (j & 15) == 13 ? b : (j & 15) == 14 ? h : a;
+    }
+    __host__ __device__ static constexpr double s(int j) { return c(j + 12); }
+};
+template <> struct Root<9> {
+    // cos / sin of 2 pi j / 9, j = 0..8
+    static constexpr double c1 = 0.76604444311897803520, s1 = 0.64278760968653932632;
+    static constexpr double c2 = 0.17364817766693034885, s2 = 0.98480775301220805936;
+    static constexpr double c3 = -0.5, s3 = 0.86602540378443864676;
+    static constexpr double c4 = -0.93969262078590838405, s4 = 0.34202014332566873304;
+    __host__ __device__ static constexpr double c(int j) {
+        return (j % 9) == 0 ? 1.0 : (j % 9) == 1 ? c1 : (j % 9) == 2 ? c2 : (j % 9) == 3 ? c3 : (j % 9) == 4 ? c4
+             : (j % 9) == 5 ? c4 : (j % 9) == 6 ? c3 : (j % 9) == 7 ? c2 : c1;
+    }
+    __host__ __device__ static constexpr double s(int j) {
+        return (j % 9) == 0 ? 0.0 : (j % 9) == 1 ? s1 : (j % 9) == 2 ? s2 : (j % 9) == 3 ? s3 : (j % 9) == 4 ? s4
+             : (j % 9) == 5 ? -s4 : (j % 9) == 6 ? -s3 : (j % 9) == 7 ? -s2 : -s1;
+    }
+};
+
+template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C *v);
+
+// N1 x N2 Cooley-Tukey in registers: x[t + N2 m] -> DFT_N1 over m, twiddle
+// W_N^(t k1), DFT_N2 over t -> X[k1 + N1 k2]; all indices compile-time
+template <int N1, int N2, int S, typename C> __device__ __forceinline__ void dft_nested(C *v) {
+    using T = decltype(C::x);
+    constexpr int N = N1 * N2;
+    C a[N];
+#pragma unroll
+    for (int t = 0; t < N2; ++t) {
+        C col[N1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) col[m] = v[t + N2 * m];
+        dft_small<N1, S>(col);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            C x = col[k1];
+            if ((t * k1) % N != 0) {
+                const T c = T(Root<N>::c((t * k1) % N)), s = T(S * Root<N>::s((t * k1) % N));
+                x = cmake<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+            }
+            a[t + N2 * k1] = x;
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        C row[N2];
+#pragma unroll
+        for (int t = 0; t < N2; ++t) row[t] = a[t + N2 * k1];
+        dft_small<N2, S>(row);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k1 + N1 * k2] = row[k2];
+    }
+}
+
+template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C *v) {
+    if constexpr (N == 1) return;
+    else if constexpr (N == 2) dft2<S>(v);
+    else if constexpr (N == 3) dft3<S>(v);
+    else if constexpr (N == 4) dft4<S>(v);
+    else if constexpr (N == 5) dft5<S>(v);
+    else if constexpr (N == 8) dft_nested<4, 2, S>(v);
+    else if constexpr (N == 9) dft_nested<3, 3, S>(v);
+    else if constexpr (N == 16) dft_nested<4, 4, S>(v);
+}
+
 // one Stockham stage over nb pencils; src/dst share the (ps, es) layout.
 // When batch_fast is set consecutive threads walk consecutive pencils (good
 // for column pencils with ps = 1), else consecutive butterflies of a pencil.
 template <int S, int R, typename C>
 __device__ __forceinline__ void fft_stage(const C *__restrict__ src, C *__restrict__ dst, int M, int Ns,
-                                          int nb, int ps, int es, const C *__restrict__ tw, bool batch_fast) {
+                                          FastDiv fns, FastDiv fnbf, int nb, FastDiv fnb, int ps, int es,
+                                          const C *__restrict__ tw, bool batch_fast) {
     const int nbf = M / R;  // butterflies per pencil
     const int total = nb * nbf;
     const int tstep = M / (Ns * R);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int p, j;
-        if (batch_fast) { p = it % nb; j = it / nb; }
-        else { j = it % nbf; p = it / nbf; }
-        const int k = j % Ns;
+        if (batch_fast) { j = (int)fdiv((unsigned)it, fnb); p = it - j * nb; }
+        else { p = (int)fdiv((unsigned)it, fnbf); j = it - p * nbf; }
+        const int jh = (int)fdiv((unsigned)j, fns);
+        const int k = j - jh * Ns;
         const C *s = src + p * ps;
         C *d = dst + p * ps;
         C v[R];
@@ -118,11 +234,8 @@ __device__ __forceinline__ void fft_stage(const C *__restrict__ src, C *__restri
                 v[r] = cmul(v[r], w);
             }
         }
-        if (R == 2) dft2<S>(v);
-        if (R == 3) dft3<S>(v);
-        if (R == 4) dft4<S>(v);
-        if (R == 5) dft5<S>(v);
-        const int base = (j / Ns) * Ns * R + k;
+        dft_small<R, S>(v);
+        const int base = jh * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) d[(base + r * Ns) * es] = v[r];
     }
@@ -133,13 +246,18 @@ __device__ __forceinline__ void fft_stage(const C *__restrict__ src, C *__restri
 template <int S, typename C>
 __device__ C *block_fft(C *a, C *b, const FftPlan &pl, int nb, int ps, int es, const C *tw, bool batch_fast) {
     int Ns = 1;
+    const FastDiv fnb = make_fastdiv((unsigned)nb);
     for (int s = 0; s < pl.nstage; ++s) {
         const int R = pl.radix[s];
+        const FastDiv fns = pl.ns_div[s], fnbf = pl.nbf_div[s];
         switch (R) {
-            case 2: fft_stage<S, 2>(a, b, pl.M, Ns, nb, ps, es, tw, batch_fast); break;
-            case 3: fft_stage<S, 3>(a, b, pl.M, Ns, nb, ps, es, tw, batch_fast); break;
-            case 4: fft_stage<S, 4>(a, b, pl.M, Ns, nb, ps, es, tw, batch_fast); break;
-            default: fft_stage<S, 5>(a, b, pl.M, Ns, nb, ps, es, tw, batch_fast); break;
+            case 2: fft_stage<S, 2>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            case 3: fft_stage<S, 3>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            case 4: fft_stage<S, 4>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            case 5: fft_stage<S, 5>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            case 8: fft_stage<S, 8>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            case 9: fft_stage<S, 9>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
+            default: fft_stage<S, 16>(a, b, pl.M, Ns, fns, fnbf, nb, fnb, ps, es, tw, batch_fast); break;
         }
         __syncthreads();
         C *t = a;

@@ -312,6 +312,9 @@ inline void planewave_factors(PlaneWaveDev &P, double h) {
 
 // inc[b][m] = (eps_r(m) - 1) eps0 E0 (1/8) sum_s g'(tau_c - delta(s)),
 // g'(tau) = Re[(-tau/sigma^2 + i w) E(tau)] / (sigma sqrt(2 pi))
+// FAST: transcendentals in FP32 after an FP64 reduction of the phase to
+// [-pi, pi] (relative error ~1e-7, used by the mixed-precision path); else FP64.
+template <bool FAST>
 __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ eps,
                            const PlaneWaveDev *__restrict__ pw, int Nx, int Ny, int Nz, double h, double t,
                            int nrhs) {
@@ -328,11 +331,27 @@ __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ 
         const double is2 = 1.0 / (P.sigma * P.sigma);
         double rx = (mx + 0.5) * h - P.rref[0], ry = (my + 0.5) * h - P.rref[1], rz = (mz + 0.5) * h - P.rref[2];
         double tc = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
-        double s, c;
-        sincos(w * tc, &s, &c);
-        double g = exp(-0.5 * tc * tc * is2);
+        double s, c, g, u0, u1, u2;
+        if (FAST) {
+            const double twopi = 6.283185307179586476925287;
+            double ph = w * tc;
+            ph -= twopi * rint(ph / twopi);
+            float sf, cf;
+            sincosf((float)ph, &sf, &cf);
+            s = sf;
+            c = cf;
+            g = expf((float)(-0.5 * tc * tc * is2));
+            u0 = expf((float)(P.beta[0] * tc * is2));
+            u1 = expf((float)(P.beta[1] * tc * is2));
+            u2 = expf((float)(P.beta[2] * tc * is2));
+        } else {
+            sincos(w * tc, &s, &c);
+            g = exp(-0.5 * tc * tc * is2);
+            u0 = exp(P.beta[0] * tc * is2);
+            u1 = exp(P.beta[1] * tc * is2);
+            u2 = exp(P.beta[2] * tc * is2);
+        }
         double Er = g * c, Ei = g * s;
-        double u0 = exp(P.beta[0] * tc * is2), u1 = exp(P.beta[1] * tc * is2), u2 = exp(P.beta[2] * tc * is2);
         double v0 = 1.0 / u0, v1 = 1.0 / u1, v2 = 1.0 / u2;
         double acc = 0.0;
 #pragma unroll

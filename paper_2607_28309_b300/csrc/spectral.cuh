@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_x_forward(const TI *__restrict__ x, cpl
 // grid = (ceil(H/tx), O1*O2); dynamic smem: (2*M*tx + M) complex
 // ---------------------------------------------------------------------------
 template <typename T, int S>
-__global__ void __launch_bounds__(256) k_axis(const cplx<T> *__restrict__ in, cplx<T> *__restrict__ out,
+__global__ void __launch_bounds__(512) k_axis(const cplx<T> *__restrict__ in, cplx<T> *__restrict__ out,
                                               FftPlan pl, const cplx<T> *__restrict__ tw_g, int H, int tx,
                                               int Lin, int Lout, int O2, long is1, long is2, long ias,
                                               long os1, long os2, long oas) {
@@ -96,6 +96,113 @@ __global__ void __launch_bounds__(256) k_axis(const cplx<T> *__restrict__ in, cp
     for (int i = threadIdx.x; i < Lout * tx; i += blockDim.x) {
         int e = i / tx, c = i - e * tx;
         if (c < w) dst[e * oas + c] = res[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused xy passes over whole planes (used when a plane fits in shared memory):
+// forward: pad + R2C along x (row pairs) and FFT along y in one CTA per plane,
+//   in [P][Ny][Nx] real -> out [P][My][H] complex;
+// inverse: IFFT along y (keep y < Ny) and C2R along x (keep x < Nx) with the
+//   epilogue, in [P][My][H] -> epilogue(row = plane*Ny + y, x, G).
+// dynamic smem: (Mx + My + 2*My*H + 2*ceil(Ny/2)*Mx) complex
+// ---------------------------------------------------------------------------
+// CTA size of the plane kernels: FP64 butterflies need more registers
+template <typename T> constexpr int kXYThreadsOf = 512;
+
+template <typename T>
+__host__ __device__ inline size_t xy_smem_bytes(int Mx, int My, int H, int Ny) {
+    return (size_t)(Mx + My + 2 * My * H + 2 * ((Ny + 1) / 2) * Mx) * sizeof(cplx<T>);
+}
+
+template <typename TI, typename T>
+__global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
+                                                    int Ny, int H, FftPlan px, FftPlan py,
+                                                    const cplx<T> *__restrict__ twx_g,
+                                                    const cplx<T> *__restrict__ twy_g) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mx = px.M, My = py.M, np = (Ny + 1) / 2;
+    C *twx = reinterpret_cast<C *>(smem_raw);
+    C *twy = twx + Mx;
+    C *Pl = twy + My;
+    C *Q = Pl + My * H;
+    C *A = Q + My * H;
+    C *Bb = A + np * Mx;
+    load_twiddles(twx, twx_g, Mx);
+    load_twiddles(twy, twy_g, My);
+    const long plane = blockIdx.x;
+    const TI *src = x + plane * (long)Ny * Nx;
+    const FastDiv fNx = make_fastdiv((unsigned)Nx), fMx = make_fastdiv((unsigned)Mx), fH = make_fastdiv((unsigned)H);
+    // rows y and y+1 -> one complex pencil; padded columns and a missing odd row are 0
+    for (int i = threadIdx.x; i < np * Mx; i += blockDim.x) {
+        int pr = (int)fdiv((unsigned)i, fMx), e = i - pr * Mx;
+        T re = T(0), im = T(0);
+        if (e < Nx) {
+            re = (T)src[(long)(2 * pr) * Nx + e];
+            if (2 * pr + 1 < Ny) im = (T)src[(long)(2 * pr + 1) * Nx + e];
+        }
+        A[i] = cmake<C>(re, im);
+    }
+    __syncthreads();
+    C *rx = block_fft<-1>(A, Bb, px, np, Mx, 1, twx, false);
+    for (int i = threadIdx.x; i < My * H; i += blockDim.x) {
+        int y = (int)fdiv((unsigned)i, fH), k = i - y * H;
+        C v = cmake<C>(T(0), T(0));
+        if (y < Ny) {
+            const C *row = rx + (y >> 1) * Mx;
+            C z = row[k], zm = cconj(row[k == 0 ? 0 : Mx - k]);
+            if ((y & 1) == 0) { C s2 = cadd(z, zm); v = cmake<C>(T(0.5) * s2.x, T(0.5) * s2.y); }
+            else { C d2 = csub(z, zm); v = cmake<C>(T(0.5) * d2.y, T(-0.5) * d2.x); }
+        }
+        Pl[i] = v;
+    }
+    __syncthreads();
+    C *ry = block_fft<-1>(Pl, Q, py, H, 1, H, twy, true);
+    C *dst = out + plane * (long)My * H;
+    for (int i = threadIdx.x; i < My * H; i += blockDim.x) dst[i] = ry[i];
+    (void)fNx;
+}
+
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_inverse(const cplx<T> *__restrict__ in, int Nx, int Ny, int Nz,
+                                                    int H, FftPlan px, FftPlan py, const cplx<T> *__restrict__ twx_g,
+                                                    const cplx<T> *__restrict__ twy_g, Epi epi) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mx = px.M, My = py.M, np = (Ny + 1) / 2;
+    C *twx = reinterpret_cast<C *>(smem_raw);
+    C *twy = twx + Mx;
+    C *Pl = twy + My;
+    C *Q = Pl + My * H;
+    C *A = Q + My * H;
+    C *Bb = A + np * Mx;
+    load_twiddles(twx, twx_g, Mx);
+    load_twiddles(twy, twy_g, My);
+    const long plane = blockIdx.x;
+    const C *src = in + plane * (long)My * H;
+    for (int i = threadIdx.x; i < My * H; i += blockDim.x) Pl[i] = src[i];
+    __syncthreads();
+    C *ry = block_fft<+1>(Pl, Q, py, H, 1, H, twy, true);
+    const FastDiv fNx = make_fastdiv((unsigned)Nx), fMx = make_fastdiv((unsigned)Mx);
+    for (int i = threadIdx.x; i < np * Mx; i += blockDim.x) {
+        int pr = (int)fdiv((unsigned)i, fMx), k = i - pr * Mx;
+        int kk = k < H ? k : Mx - k;
+        bool cj = k >= H;
+        C a = ry[(2 * pr) * H + kk];
+        C b = (2 * pr + 1 < Ny) ? ry[(2 * pr + 1) * H + kk] : cmake<C>(T(0), T(0));
+        // the DC and (even M) Nyquist bins of a real sequence are real
+        if (kk == 0 || 2 * kk == Mx) { a.y = T(0); b.y = T(0); }
+        if (cj) { a = cconj(a); b = cconj(b); }
+        A[i] = cmake<C>(a.x - b.y, a.y + b.x);
+    }
+    __syncthreads();
+    C *rx = block_fft<+1>(A, Bb, px, np, Mx, 1, twx, false);
+    const auto pe = epi.bind(plane, Nz, Ny * Nx);
+    for (int i = threadIdx.x; i < Ny * Nx; i += blockDim.x) {
+        int y = (int)fdiv((unsigned)i, fNx);
+        C z = rx[(y >> 1) * Mx + (i - y * Nx)];
+        pe(i, (y & 1) ? z.y : z.x);
     }
 }
 
@@ -128,7 +235,7 @@ __device__ __forceinline__ void green_mul(const T *__restrict__ L, long cstride,
 // grid = (ceil(H/tx), B*My); dynamic smem: (6*Mz*tx + Mz) complex
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_z_green(cplx<T> *__restrict__ buf, const T *__restrict__ L,
+__global__ void __launch_bounds__(512) k_z_green(cplx<T> *__restrict__ buf, const T *__restrict__ L,
                                                  FftPlan pl, const cplx<T> *__restrict__ tw_g, int Nz,
                                                  int My, int H, int tx, Octant oc) {
     using C = cplx<T>;
@@ -234,6 +341,86 @@ __global__ void __launch_bounds__(256) k_z_history(const cplx<T> *__restrict__ r
 }
 
 // ---------------------------------------------------------------------------
+// history z pass over the mirrored row pair (ky, My - ky): both rows fold to
+// the same Green-spectrum octant row (odd components change sign), so each
+// Lambda_k value is read once for the two rows.  grid = (ceil(H/tx), B*(My/2+1));
+// pencils in smem: [e][row r][q][c], 6*tx of them; smem (12*Mz*tx + Mz) complex
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_z_history2(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
+                                                    cplx<T> *__restrict__ out, FftPlan pl,
+                                                    const cplx<T> *__restrict__ tw_g, int Nz, int My, int H, int tx,
+                                                    Octant oc, int nrhs, int ell, long n, int kmax) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    const int M = pl.M;
+    const int npp = 6 * tx;  // pencils
+    C *a = tw + M;
+    C *b = a + M * npp;
+    load_twiddles(tw, tw_g, M);
+    const int half = My / 2 + 1;
+    const int bb = blockIdx.y / half, j = blockIdx.y - bb * half;
+    const int ky0 = j, ky1 = My - j;
+    const bool two = (ky1 != ky0) && (ky1 < My);  // j = 0 and (even My) j = My/2 are self-mirrored
+    const int kx0 = blockIdx.x * tx;
+    const int w = min(tx, H - kx0);
+    const long plane = (long)My * H;
+    const long slot_comp = (long)M * plane;
+    const long slot_size = (long)nrhs * 3 * slot_comp;
+    const long cs = (long)oc.Kz * oc.Ky * oc.H;
+    for (int i = threadIdx.x; i < M * tx; i += blockDim.x) {
+        const int kz = i / tx, c = i - kz * tx;
+        C acc0[3], acc1[3];
+        for (int q = 0; q < 3; ++q) { acc0[q] = cmake<C>(T(0), T(0)); acc1[q] = acc0[q]; }
+        if (c < w) {
+            const int fz = (2 * kz > M) ? M - kz : kz;
+            const float sz = (2 * kz > M) ? -1.f : 1.f;
+            const long lidx = ((long)fz * oc.Ky + j) * oc.H + kx0 + c;
+            const long r0 = (long)bb * 3 * slot_comp + (long)kz * plane + (long)ky0 * H + kx0 + c;
+            const long r1 = r0 + (long)(ky1 - ky0) * H;
+            long s = (n - 1) % ell;
+            if (s < 0) s += ell;
+#pragma unroll 2
+            for (int k = 1; k <= kmax; ++k) {
+                const T *L = Lh + (long)k * 6 * cs + lidx;
+                const T gxx = L[0], gyy = L[cs], gzz = L[2 * cs];
+                const T gxy = L[3 * cs], gxz = sz * L[4 * cs], gyz = sz * L[5 * cs];
+                const C *R = ring + s * slot_size;
+                C u0 = R[r0], u1 = R[r0 + slot_comp], u2 = R[r0 + 2 * slot_comp];
+                // row ky0 (sy = +1)
+                acc0[0] = cmake<C>(acc0[0].x + gxx * u0.x + gxy * u1.x + gxz * u2.x, acc0[0].y + gxx * u0.y + gxy * u1.y + gxz * u2.y);
+                acc0[1] = cmake<C>(acc0[1].x + gxy * u0.x + gyy * u1.x + gyz * u2.x, acc0[1].y + gxy * u0.y + gyy * u1.y + gyz * u2.y);
+                acc0[2] = cmake<C>(acc0[2].x + gxz * u0.x + gyz * u1.x + gzz * u2.x, acc0[2].y + gxz * u0.y + gyz * u1.y + gzz * u2.y);
+                if (two) {
+                    // row ky1 = My - ky0 (sy = -1: xy and yz change sign)
+                    C v0 = R[r1], v1 = R[r1 + slot_comp], v2 = R[r1 + 2 * slot_comp];
+                    acc1[0] = cmake<C>(acc1[0].x + gxx * v0.x - gxy * v1.x + gxz * v2.x, acc1[0].y + gxx * v0.y - gxy * v1.y + gxz * v2.y);
+                    acc1[1] = cmake<C>(acc1[1].x - gxy * v0.x + gyy * v1.x - gyz * v2.x, acc1[1].y - gxy * v0.y + gyy * v1.y - gyz * v2.y);
+                    acc1[2] = cmake<C>(acc1[2].x + gxz * v0.x - gyz * v1.x + gzz * v2.x, acc1[2].y + gxz * v0.y - gyz * v1.y + gzz * v2.y);
+                }
+                s = (s == 0) ? ell - 1 : s - 1;
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            a[kz * npp + q * tx + c] = acc0[q];
+            a[kz * npp + (3 + q) * tx + c] = acc1[q];
+        }
+    }
+    __syncthreads();
+    C *res = block_fft<+1>(a, b, pl, npp, 1, npp, tw, true);
+    const long comp = (long)Nz * plane;
+    for (int i = threadIdx.x; i < Nz * npp; i += blockDim.x) {
+        const int e = i / npp, rr = i - e * npp, g = rr / tx, c = rr - g * tx;
+        if (c >= w) continue;
+        const int row = g / 3, q = g - 3 * row;
+        if (row == 1 && !two) continue;
+        const int ky = row == 0 ? ky0 : ky1;
+        out[(long)bb * 3 * comp + q * comp + (long)e * plane + (long)ky * H + kx0 + c] = res[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // x pass, inverse (C2R) with a fused epilogue.  Rows 2p, 2p+1 of half spectra
 // A, B become Z[k] = A[k] + i B[k] (Hermitian extension for k > M/2), inverse
 // FFT, and a = Re z, b = Im z for e < Nx.  The epilogue receives the Green
@@ -282,20 +469,39 @@ __global__ void __launch_bounds__(256) k_x_inverse(const cplx<T> *__restrict__ i
 }
 
 // ----- epilogues (row = ((b*3 + p)*Nz + z)*Ny + y, element row*Nx + e) -----
+// operator()(row, e, G) serves the row-wise C2R kernel; bind(plane) returns a
+// functor for one whole (b, p, z) plane, element i = y*Nx + x, used by the
+// plane kernel with all per-plane index arithmetic done once.
 
-// Z0 product (Eq. 12): y = eps T(0) x - (eps - 1) G
+// Z0 product (Eq. 12): y = eps T(0) x - (eps - 1) G, in the precision of y
+// (eps given in that precision too)
 template <typename TX, typename TY>
 struct EpiZ0 {
     const TX *x;
     TY *y;
-    const double *eps;
+    const TY *eps;
     long plane_rows;  // Nz * Ny
     int Nx;
     __device__ __forceinline__ void operator()(long row, int e, double g) const {
         long idx = row * Nx + e;
         long m = (row % plane_rows) * Nx + e;
-        double ep = eps[m];
-        y[idx] = (TY)(ep * 0.5 * (double)x[idx] - (ep - 1.0) * g);
+        TY ep = eps[m];
+        y[idx] = ep * TY(0.5) * (TY)x[idx] - (ep - TY(1)) * (TY)g;
+    }
+    struct Plane {
+        const TX *x;
+        TY *y;
+        const TY *eps;
+        __device__ __forceinline__ void operator()(int i, TY g) const {
+            TY ep = eps[i];
+            y[i] = ep * TY(0.5) * (TY)x[i] - (ep - TY(1)) * g;
+        }
+    };
+    // plane = (b*3 + p)*Nz + z; Ny*Nx = plane_rows/Nz*Nx is recovered from Nz
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        long off = plane * (long)NyNx;
+        long zoff = (plane % Nz) * (long)NyNx;
+        return Plane{x + off, y + off, eps + zoff};
     }
 };
 
@@ -311,6 +517,20 @@ struct EpiResidual {
         long m = (row % plane_rows) * Nx + e;
         double ep = eps[m];
         r[idx] = b[idx] - (ep * 0.5 * x[idx] - (ep - 1.0) * g);
+    }
+    struct Plane {
+        const double *x, *b;
+        double *r;
+        const double *eps;
+        __device__ __forceinline__ void operator()(int i, double g) const {
+            double ep = eps[i];
+            r[i] = b[i] - (ep * 0.5 * x[i] - (ep - 1.0) * g);
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        long off = plane * (long)NyNx;
+        long zoff = (plane % Nz) * (long)NyNx;
+        return Plane{x + off, b + off, r + off, eps + zoff};
     }
 };
 
@@ -337,6 +557,25 @@ struct EpiHistory {
         double v = inc[bb * nvox + m] * pol[bb * 3 + p] + (ep - 1.0) * g;
         if (Jprev) v -= ep * 0.5 * Jprev[idx];
         out[idx] = v;
+    }
+    struct Plane {
+        const double *inc, *Jprev, *eps;
+        double *out;
+        double pol;
+        __device__ __forceinline__ void operator()(int i, double g) const {
+            double ep = eps[i];
+            double v = inc[i] * pol + (ep - 1.0) * g;
+            if (Jprev) v -= ep * 0.5 * Jprev[i];
+            out[i] = v;
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        long off = plane * (long)NyNx;
+        long bp = plane / Nz, z = plane - bp * Nz;
+        long bb = bp / 3;
+        int p = (int)(bp - 3 * bb);
+        long zoff = z * (long)NyNx;
+        return Plane{inc + bb * nvox + zoff, Jprev ? Jprev + off : nullptr, eps + zoff, out + off, pol[bb * 3 + p]};
     }
 };
 
