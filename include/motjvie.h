@@ -78,7 +78,7 @@ typedef struct {
     double tol;       /* TFQMR relative residual target (paper: 1e-6, Sec. V-A).
                          Default 1e-11 for MOT_FP64, 1e-6 (outer) for MOT_MIXED   */
     int maxit;        /* TFQMR iteration cap per solve (default 500)             */
-    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-4)      */
+    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-6)      */
     int max_refine;   /* MOT_MIXED refinement sweeps cap (default 6)              */
     double delta;     /* diagonal shift of the delta-regularised MOT,
                          Z_n + delta I (Sec. II; the paper uses 0).  Only 0 is
@@ -88,8 +88,12 @@ typedef struct {
                          ms_zhist / ms_zgreen of mot_step_stats; adds event
                          overhead).  Default 0                                     */
     int guess;        /* initial guess of each step's solve (the paper does not
-                         specify one): 0 = J_{n-1}; 1 = 2 J_{n-1} - J_{n-2}
-                         (linear extrapolation, default)                           */
+                         specify one): 0 = J_{n-1} (default); 1 = 2 J_{n-1} -
+                         J_{n-2} (linear extrapolation)                            */
+    int graph;        /* 1 (default): after the first step each step is one CUDA
+                         graph launch whose loops and tests run on the device; 0:
+                         host-driven steps (needed for the timing option's
+                         per-kernel times)                                         */
 } mot_options;
 
 typedef struct {
@@ -106,12 +110,14 @@ typedef struct {
     int32_t iters;     /* TFQMR iterations (sum over refinement sweeps)          */
     int32_t sweeps;    /* refinement sweeps (1 for MOT_FP64)                     */
     double relres;     /* final ||b - Z0 J_n|| / ||b|| (max over the batch)       */
-    float ms_history;  /* device time of the right-hand side (incident + history) */
-    float ms_solve;    /* device time of the solve                               */
-    float ms_push;     /* device time of the history-ring update                 */
+    float ms_history;  /* device time of the right-hand side (0 in graph mode)  */
+    float ms_solve;    /* device time of the solve (graph mode: the whole step) */
+    float ms_push;     /* device time of the ring update (0 in graph mode)      */
     int32_t mvps;      /* Z0 products applied in the step                        */
     float ms_zhist;    /* history z-pass kernel time (timing option, else 0)     */
-    float ms_zgreen;   /* summed Z0 spectral z-pass kernel time (timing option)  */
+    float ms_zgreen;   /* mean time of the step's timed Z0 spectral z passes
+                          (timing option with graph = 0; those outside the
+                          TFQMR loop graph)                                      */
 } mot_step_stats;
 
 typedef struct mot_ctx mot_ctx;

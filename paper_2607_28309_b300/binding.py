@@ -60,7 +60,7 @@ class mot_planewave(ctypes.Structure):
 class mot_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("delta", ctypes.c_double), ("timing", ctypes.c_int),
-                ("guess", ctypes.c_int)]
+                ("guess", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class mot_problem_info(ctypes.Structure):
@@ -246,7 +246,7 @@ def mot_kernel_launches() -> int:
 
 def default_options(**kw) -> mot_options:
     """mot_options with the library defaults (tol 0 = per-precision default)."""
-    o = mot_options(0.0, 500, 1e-4, 6, 0.0, 0, 1)
+    o = mot_options(0.0, 500, 1e-6, 6, 0.0, 0, 0, 1)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <string>
 #include <vector>
 
@@ -283,6 +284,11 @@ struct KTimer {
         cudaEventRecord(ev[2 * used + 1], st);
         ++used;
     }
+    int count(int c) const {
+        int k = 0;
+        for (int i = 0; i < used; ++i) k += cls[i] == c;
+        return k;
+    }
     float total(int c) {
         float acc = 0.f;
         for (int i = 0; i < used; ++i)
@@ -346,6 +352,15 @@ struct mot_run {
     DBuf scal, part1, part2, part3, dots;
     DBuf r32;  // mixed: residual in FP32 / correction
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // whole-step graph (graph mode)
+    cudaStream_t cap2 = nullptr, cap3 = nullptr;
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    DBuf sdev;      // StepDev
+    DBuf sstats;    // per-step device stats of one mot_run_step call
+    DBuf b2, r2;    // ||b||^2, ||r||^2 per right-hand side
+    int sstats_cap = 0;
+    int k_fixed = 0, k_outer = 0, k_inner = 0;  // kernels per step / per sweep / per TFQMR iteration
 };
 
 namespace {
@@ -425,7 +440,8 @@ template <typename T> int tile_width(int M, int comps) {
 
 template <typename T, int S>
 mot_status launch_axis(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int O1, int O2,
-                       long is1, long is2, long ias, long os1, long os2, long oas, cudaStream_t st) {
+                       long is1, long is2, long ias, long os1, long os2, long oas, cudaStream_t st,
+                       const long long *nptr = nullptr, int ell = 1, long slot_stride = 0) {
     const int M = tw->M;
     int tx = tile_width<T>(M, 1);
     size_t smem = (size_t)(2 * M * tx + M) * sizeof(cplx<T>);
@@ -433,7 +449,7 @@ mot_status launch_axis(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int L
     dim3 grid((H + tx - 1) / tx, (unsigned)(O1 * O2));
     count_launch();
     k_axis<T, S><<<grid, kZThreads, smem, st>>>(in, out, planp<T>(tw), twp<T>(tw), H, tx, Lin, Lout, O2, is1, is2, ias, os1,
-                                          os2, oas);
+                                          os2, oas, nptr, ell, slot_stride);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
@@ -451,9 +467,64 @@ mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw
     return MOT_OK;
 }
 
+// specialised plane kernels for the compiled (Mx, My) shapes; false -> generic
+template <typename TI, typename T, int RX1, int RX2, int RY1, int RY2>
+bool xy_forward_r_go(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
+    const size_t smem = xy_r_smem_bytes<T, RX1, RX2, RY1, RY2>(Ny);
+    if (smem > kSmemMax) return false;
+    if (allow_smem<k_xy_forward_r<TI, T, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
+    count_launch();
+    k_xy_forward_r<TI, T, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(x, out, Nx, Ny, twp<T>(tx), twp<T>(ty));
+    return true;
+}
+
+template <typename T, class Epi, int RX1, int RX2, int RY1, int RY2>
+bool xy_inverse_r_go(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw *tx, AxisTw *ty, Epi epi,
+                     cudaStream_t st) {
+    const size_t smem = xy_r_smem_bytes<T, RX1, RX2, RY1, RY2>(Ny);
+    if (smem > kSmemMax) return false;
+    if (allow_smem<k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
+    count_launch();
+    k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(in, Nx, Ny, Nz, twp<T>(tx), twp<T>(ty), epi);
+    return true;
+}
+
+inline bool specialised_off() {
+    static const bool off = getenv("MOTJVIE_GENERIC_FFT") && atoi(getenv("MOTJVIE_GENERIC_FFT")) != 0;
+    return off;
+}
+
+template <typename TI, typename T>
+bool xy_forward_r(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
+    if (specialised_off() || tx->M != ty->M) return false;
+    switch (tx->M) {
+        case 20: return xy_forward_r_go<TI, T, 5, 4, 5, 4>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 32: return xy_forward_r_go<TI, T, 8, 4, 8, 4>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 72: return xy_forward_r_go<TI, T, 9, 8, 9, 8>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 128: return xy_forward_r_go<TI, T, 16, 8, 16, 8>(x, out, planes, Nx, Ny, tx, ty, st);
+        default: return false;
+    }
+}
+
+template <typename T, class Epi>
+bool xy_inverse_r(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw *tx, AxisTw *ty, Epi epi, cudaStream_t st) {
+    if (specialised_off() || tx->M != ty->M) return false;
+    switch (tx->M) {
+        case 20: return xy_inverse_r_go<T, Epi, 5, 4, 5, 4>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
+        case 32: return xy_inverse_r_go<T, Epi, 8, 4, 8, 4>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
+        case 72: return xy_inverse_r_go<T, Epi, 9, 8, 9, 8>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
+        case 128: return xy_inverse_r_go<T, Epi, 16, 8, 16, 8>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
+        default: return false;
+    }
+}
+
 template <typename TI, typename T>
 mot_status launch_xy_forward(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, int H, AxisTw *tx, AxisTw *ty,
                              cudaStream_t st) {
+    if (xy_forward_r<TI, T>(x, out, planes, Nx, Ny, tx, ty, st)) {
+        MOT_CHECK_LAUNCH();
+        return MOT_OK;
+    }
     size_t smem = xy_smem_bytes<T>(tx->M, ty->M, H, Ny);
     MOT_TRY(allow_smem<k_xy_forward<TI, T>>());
     count_launch();
@@ -465,12 +536,46 @@ mot_status launch_xy_forward(const TI *x, cplx<T> *out, int planes, int Nx, int 
 template <typename T, class Epi>
 mot_status launch_xy_inverse(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, int H, AxisTw *tx, AxisTw *ty,
                              Epi epi, cudaStream_t st) {
+    if (xy_inverse_r<T, Epi>(in, planes, Nx, Ny, Nz, tx, ty, epi, st)) {
+        MOT_CHECK_LAUNCH();
+        return MOT_OK;
+    }
     size_t smem = xy_smem_bytes<T>(tx->M, ty->M, H, Ny);
     MOT_TRY(allow_smem<k_xy_inverse<T, Epi>>());
     count_launch();
     k_xy_inverse<T, Epi><<<planes, kXYThreadsOf<T>, smem, st>>>(in, Nx, Ny, Nz, H, planp<T>(tx), planp<T>(ty), twp<T>(tx), twp<T>(ty), epi);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
+}
+
+template <typename T> const T *L0_of(mot_problem *p);
+
+// specialised z pass when M0z = R1 * R2 is one of the compiled shapes;
+// returns false to fall back to the generic pass
+template <typename T, int R1, int R2> bool z_green_r_go(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
+    const int My = p->M0[1], H = p->H0, Nz = p->N[2];
+    const size_t smem = (size_t)(R1 * R2 + 3 * 32 * (R1 * R2 + 1)) * sizeof(cplx<T>);
+    if (allow_smem<k_z_green_r<T, R1, R2>>() != MOT_OK) return false;
+    Octant oc = {p->M0[2], My, p->K0[2], p->K0[1], H};
+    dim3 grid((My * H + 31) / 32, (unsigned)nrhs);
+    if (!p->capturing) p->kt.begin(st, kTimeZGreen);
+    count_launch();
+    k_z_green_r<T, R1, R2><<<grid, 32 * R2, smem, st>>>(Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H, oc);
+    if (!p->capturing) p->kt.end(st);
+    return true;
+}
+
+template <typename T> bool launch_z_green_r(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
+    if (specialised_off()) return false;
+    switch (p->M0[2]) {
+        case 20: return z_green_r_go<T, 5, 4>(p, Bf, tz, nrhs, st);
+        case 32: return z_green_r_go<T, 8, 4>(p, Bf, tz, nrhs, st);
+        case 64: return z_green_r_go<T, 8, 8>(p, Bf, tz, nrhs, st);
+        case 72: return z_green_r_go<T, 9, 8>(p, Bf, tz, nrhs, st);
+        case 80: return z_green_r_go<T, 5, 16>(p, Bf, tz, nrhs, st);
+        case 128: return z_green_r_go<T, 16, 8>(p, Bf, tz, nrhs, st);
+        default: return false;
+    }
 }
 
 template <typename T> const T *eps_of(mot_problem *p);
@@ -503,7 +608,9 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
         MOT_TRY(launch_x_forward<TI, T>(x, A, nrows, Nx, H, tx, st));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
     }
-    {
+    if (launch_z_green_r<T>(p, Bf, tz, nrhs, st)) {
+        MOT_CHECK_LAUNCH();
+    } else {
         int tw = tile_width<T>(p->M0[2], 3);
         size_t smem = (size_t)(6 * p->M0[2] * tw + p->M0[2]) * sizeof(C);
         MOT_TRY(allow_smem<k_z_green<T>>());
@@ -796,11 +903,12 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     long nv = (long)n[0] * n[1] * n[2];
     for (long i = 0; i < nv; ++i)
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
-    mot_options o = {0.0, 500, 1e-4, 6, 0.0, 0, 1};
+    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 0, 1};
     if (opt) o = *opt;
     if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
     if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
+    if (o.graph != 0 && o.graph != 1) MOT_FAIL(MOT_EINVAL, "graph must be 0 or 1");
     MOT_CUDA_TRY(cudaSetDevice(ctx->device));
     mot_problem *p = new mot_problem();
     p->ctx = ctx;
@@ -1186,9 +1294,9 @@ template <typename T> void *ring_slot(mot_run *r, long s) {
 }
 
 // Jhat_n = F_Mh{J_n} into ring slot n mod ell
-template <typename T> mot_status ring_push(mot_run *r) {
+// nptr (graph mode): the slot index comes from device memory
+template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const long long *nptr = nullptr) {
     mot_problem *p = r->p;
-    cudaStream_t st = p->ctx->stream;
     const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
     const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
     AxisTw *tx = get_tw(p, p->Mh[0]), *ty = get_tw(p, My), *tz = get_tw(p, Mz);
@@ -1201,16 +1309,16 @@ template <typename T> mot_status ring_push(mot_run *r) {
         MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
     }
-    C *slot = (C *)ring_slot<T>(r, r->n % p->ell);
+    const long slot_elems = (long)r->B * 3 * Mz * My * H;
+    C *slot = nptr ? (C *)r->ring.p : (C *)ring_slot<T>(r, r->n % p->ell);
     MOT_TRY((launch_axis<T, -1>(Bf, slot, tz, H, Nz, Mz, r->B * 3, My, (long)Nz * My * H, H, (long)My * H,
-                                (long)Mz * My * H, H, (long)My * H, st)));
+                                (long)Mz * My * H, H, (long)My * H, st, nptr, p->ell, slot_elems)));
     return MOT_OK;
 }
 
 // b_n = E^i_n - eps T(dt) J_{n-1} + (eps - 1) sum_k G_k J_{n-k}
-template <typename T> mot_status history_rhs(mot_run *r) {
+template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const long long *nptr = nullptr) {
     mot_problem *p = r->p;
-    cudaStream_t st = p->ctx->stream;
     const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
     const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
     const long nv = (long)Nx * Ny * Nz;
@@ -1221,10 +1329,12 @@ template <typename T> mot_status history_rhs(mot_run *r) {
     count_launch();
     if (sizeof(T) == 4)
         k_incident<true><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
-                                                             (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
+                                                             (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B,
+                                                             nptr, p->dt);
     else
         k_incident<false><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
-                                                              (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B);
+                                                              (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B,
+                                                              nptr, p->dt);
     MOT_CHECK_LAUNCH();
     const int kmax = (int)std::min<long>(r->n, p->ell);
     {
@@ -1235,17 +1345,17 @@ template <typename T> mot_status history_rhs(mot_run *r) {
         MOT_TRY(allow_smem<k_z_history2<T>>());
         Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
         dim3 grid((H + tw - 1) / tw, (unsigned)(r->B * (My / 2 + 1)));
-        p->kt.begin(st, kTimeZHist);
+        if (!p->capturing) p->kt.begin(st, kTimeZHist);
         count_launch();
         k_z_history2<T><<<grid, kZThreads, smem, st>>>((const C *)r->ring.p, Lh_of<T>(p), Bf, planp<T>(tz), twp<T>(tz), Nz, My,
-                                                 H, tw, oc, r->B, p->ell, r->n, kmax);
-        p->kt.end(st);
+                                                 H, tw, oc, r->B, p->ell, r->n, kmax, nptr);
+        if (!p->capturing) p->kt.end(st);
         MOT_CHECK_LAUNCH();
     }
     EpiHistory e;
     e.inc = (const double *)r->inc.p;
     e.pol = nullptr;  // set below
-    e.Jprev = r->n > 0 ? (const double *)r->J.p : nullptr;
+    e.Jprev = (nptr || r->n > 0) ? (const double *)r->J.p : nullptr;  // J = 0 before the first step
     e.out = (double *)r->b.p;
     e.eps = (const double *)p->eps.p;
     e.plane_rows = (long)Nz * Ny;
@@ -1288,8 +1398,8 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     p->kt.reset();
     int mvps = 0;
     cudaEventRecord(r->ev[0], st);
-    if (mixed) MOT_TRY(history_rhs<float>(r));
-    else MOT_TRY(history_rhs<double>(r));
+    if (mixed) MOT_TRY(history_rhs<float>(r, st));
+    else MOT_TRY(history_rhs<double>(r, st));
     cudaEventRecord(r->ev[1], st);
     if (p->opt.guess == 1) {
         count_launch();
@@ -1349,8 +1459,8 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     }
     for (int b = 0; b < r->B; ++b) relres = std::max(relres, bn[b] > 0 ? rn[b] / bn[b] : 0.0);
     cudaEventRecord(r->ev[2], st);
-    if (mixed) MOT_TRY(ring_push<float>(r));
-    else MOT_TRY(ring_push<double>(r));
+    if (mixed) MOT_TRY(ring_push<float>(r, st));
+    else MOT_TRY(ring_push<double>(r, st));
     cudaEventRecord(r->ev[3], st);
     if (stats) {
         MOT_CUDA_TRY(cudaEventSynchronize(r->ev[3]));
@@ -1362,7 +1472,8 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         cudaEventElapsedTime(&stats->ms_push, r->ev[2], r->ev[3]);
         stats->mvps = (int32_t)mvps;
         stats->ms_zhist = p->kt.total(kTimeZHist);
-        stats->ms_zgreen = p->kt.total(kTimeZGreen);
+        const int ng = p->kt.count(kTimeZGreen);
+        stats->ms_zgreen = ng > 0 ? p->kt.total(kTimeZGreen) / ng : 0.f;
     }
     p->kt.on = false;
     r->n += 1;
@@ -1371,6 +1482,332 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
                   " (relres " + std::to_string(relres) + ")");
         return MOT_ENOTCONV;
     }
+    return MOT_OK;
+}
+
+// ============================================================================
+// graph mode: one CUDA graph per MOT step, control kept on the device
+// ============================================================================
+struct StepDev {
+    long long n;     // index of the step being computed
+    int iters;       // TFQMR iterations of the step (sum over sweeps)
+    int sweeps;      // refinement sweeps
+    int mvps;        // Z0 products
+    int notconv;     // 1 if the step missed its tolerance
+    double relres;   // max_b ||b - Z0 J|| / ||b||
+    int nstat;       // index of this step within the current mot_run_step call
+    int loops;       // TFQMR loop-body executions of the step (sum over solves)
+};
+
+struct StepStatDev {
+    int iters, sweeps, mvps, notconv;
+    double relres;
+    int loops, pad;
+};
+
+__global__ void k_step_begin(StepDev *s) {
+    if (threadIdx.x == 0) {
+        s->iters = 0;
+        s->sweeps = 0;
+        s->mvps = 0;
+        s->notconv = 0;
+        s->relres = 0.0;
+        s->loops = 0;
+    }
+}
+
+// start of an inner TFQMR loop: reset its iteration counter and condition
+__global__ void k_cond_set(cudaGraphConditionalHandle h, int *ctl, int maxit) {
+    if (threadIdx.x == 0) {
+        ctl[0] = 0;
+        ctl[1] = maxit;
+        cudaGraphSetConditional(h, 1u);
+    }
+}
+
+// after a solve: iterations, products, convergence into the step record
+__global__ void k_solve_stats(const TfqmrScal *sc, int B, const int *ctl, StepDev *s, int init_mvps, int mark) {
+    if (threadIdx.x == 0) {
+        int mx = 0, bad = 0;
+        for (int b = 0; b < B; ++b) {
+            int it = (sc[b].m + 1) / 2;
+            mx = it > mx ? it : mx;
+            if (sc[b].conv == 0) bad = 1;
+        }
+        s->iters += mx;
+        s->mvps += init_mvps + 2 * ctl[0];
+        s->loops += ctl[0];
+        if (mark && bad) s->notconv = 1;
+    }
+}
+
+// refinement control: stop once every ||r_b|| <= tol ||b_b|| or after
+// max_refine sweeps; counts the residual product that preceded it
+__global__ void k_refine_cond(cudaGraphConditionalHandle h, const double *b2, const double *r2, int B, double tol,
+                              int max_refine, StepDev *s, int after_sweep) {
+    if (threadIdx.x == 0) {
+        int done = 1;
+        double rel = 0.0;
+        for (int b = 0; b < B; ++b) {
+            double bn = sqrt(b2[b]), rn = sqrt(r2[b]);
+            if (rn > tol * bn) done = 0;
+            double q = bn > 0.0 ? rn / bn : 0.0;
+            rel = q > rel ? q : rel;
+        }
+        s->relres = rel;
+        s->mvps += 1;
+        if (after_sweep) s->sweeps += 1;
+        int cont = (!done && s->sweeps < max_refine) ? 1 : 0;
+        if (!done && !cont) s->notconv = 1;
+        cudaGraphSetConditional(h, (unsigned)cont);
+    }
+}
+
+// FP64 path: relative residual after the solve
+__global__ void k_fp64_finish(const double *b2, const double *r2, int B, StepDev *s) {
+    if (threadIdx.x == 0) {
+        double rel = 0.0;
+        for (int b = 0; b < B; ++b) {
+            double bn = sqrt(b2[b]), rn = sqrt(r2[b]);
+            double q = bn > 0.0 ? rn / bn : 0.0;
+            rel = q > rel ? q : rel;
+        }
+        s->relres = rel;
+        s->mvps += 1;
+        s->sweeps = 1;
+    }
+}
+
+__global__ void k_step_end(StepDev *s, StepStatDev *out, int cap) {
+    if (threadIdx.x == 0) {
+        int i = s->nstat;
+        if (i >= 0 && i < cap) {
+            StepStatDev d;
+            d.iters = s->iters;
+            d.sweeps = s->sweeps;
+            d.mvps = s->mvps;
+            d.notconv = s->notconv;
+            d.relres = s->relres;
+            d.loops = s->loops;
+            d.pad = 0;
+            out[i] = d;
+        }
+        s->nstat = i + 1;
+        s->n += 1;
+    }
+}
+
+// squared 2-norms of the batch vectors into out[B] (device only)
+mot_status dev_norms2(mot_run *r, const double *v, double *out, cudaStream_t st) {
+    mot_problem *p = r->p;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    count_launch();
+    k_dot_part<double, double><<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, v, L, (double *)r->part1.p);
+    count_launch();
+    k_finish_dot<<<r->B, 32, 0, st>>>((const double *)r->part1.p, out);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+// conditional WHILE node inserted into the graph being captured on st; the
+// body is captured on bst by fn(bst); work captured on st afterwards depends
+// on the node.  The handle is created on `owner` before fn runs and is also
+// returned so kernels captured before the node can set it.
+struct WhileNode {
+    cudaGraphConditionalHandle h;
+    cudaGraph_t owner;
+};
+
+mot_status while_handle(cudaStream_t st, WhileNode &w, unsigned defv) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    MOT_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive || !g) MOT_FAIL(MOT_ECUDA, "stream is not capturing");
+    MOT_CUDA_TRY(cudaGraphConditionalHandleCreate(&w.h, g, defv, cudaGraphCondAssignDefault));
+    w.owner = g;
+    return MOT_OK;
+}
+
+template <class F>
+mot_status while_insert(cudaStream_t st, cudaStream_t bst, const WhileNode &w, F fn, int *body_kernels = nullptr) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    MOT_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = w.h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    MOT_CUDA_TRY(cudaGraphAddNode(&node, g, dv.data(), nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MOT_CUDA_TRY(cudaStreamBeginCaptureToGraph(bst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const unsigned long long b0 = g_launches.load();
+    mot_status s = fn(bst);
+    if (body_kernels) *body_kernels = (int)(g_launches.load() - b0);
+    cudaGraph_t tmp = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(bst, &tmp);
+    if (s != MOT_OK) return s;
+    if (ce != cudaSuccess) MOT_FAIL(MOT_ECUDA, std::string("body capture: ") + cudaGetErrorString(ce));
+    MOT_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return MOT_OK;
+}
+
+// TFQMR solve captured on st (init kernels, WHILE node with the iteration
+// body captured on bst, flush), solve statistics into the step record
+template <typename V>
+mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, cudaStream_t st,
+                         cudaStream_t bst, int mark_notconv) {
+    mot_problem *p = r->p;
+    const int B = r->B;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    const long n = L * B;
+    KrylovView<V> k = kview<V>(r);
+    dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    int init_mvps = 1;
+    if (zero_x0) {
+        MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
+        MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        MOT_TRY(mvp<V>(r, x, k.v[kAY1], st));
+        init_mvps = 2;
+        count_launch();
+        k_sub<V><<<grid_for(n), 256, 0, st>>>(k.v[kW], rhs, k.v[kAY1], n);
+        MOT_CHECK_LAUNCH();
+    }
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kY1], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kRS], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    MOT_CUDA_TRY(cudaMemsetAsync(k.v[kD], 0, sizeof(V) * n, st));
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kW], k.v[kW], L, k.p1);
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(rhs, rhs, L, k.p2);
+    count_launch();
+    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol);
+    count_launch();
+    k_tfqmr_zero_rhs<V><<<gv, 256, 0, st>>>(x, k.sc, L);
+    count_launch();
+    k_tfqmr_zero_done<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B);
+    MOT_CHECK_LAUNCH();
+    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kV], k.v[kAY1], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
+    count_launch();
+    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kRS], k.v[kV], L, k.p3);
+    WhileNode w;
+    MOT_TRY(while_handle(st, w, 1));
+    count_launch();
+    k_cond_set<<<1, 32, 0, st>>>(w.h, (int *)r->ctl.p, maxit);
+    MOT_CHECK_LAUNCH();
+    MOT_TRY(while_insert(st, bst, w, [&](cudaStream_t cs) -> mot_status {
+        MOT_TRY(tfqmr_body<V>(r, x, cs));
+        count_launch();
+        k_loop_cond<<<1, 32, 0, cs>>>(w.h, (const TfqmrScal *)r->scal.p, r->B, (int *)r->ctl.p);
+        MOT_CHECK_LAUNCH();
+        return MOT_OK;
+    }, &r->k_inner));
+    count_launch();
+    k_tfqmr_flush<V, V><<<gv, 256, 0, st>>>(x, k.v[kD], k.sc, L, 1);
+    count_launch();
+    k_solve_stats<<<1, 32, 0, st>>>(k.sc, B, (const int *)r->ctl.p, (StepDev *)r->sdev.p, init_mvps, mark_notconv);
+    count_launch();
+    k_tfqmr_settle<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B, 1);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+// capture one whole MOT step (Eq. 3) into r->step_graph
+mot_status build_step_graph(mot_run *r) {
+    mot_problem *p = r->p;
+    const bool mixed = r->prec == MOT_MIXED;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    const long n = L * r->B;
+    const long pr = (long)p->N[2] * p->N[1];
+    StepDev *sd = (StepDev *)r->sdev.p;
+    const long long *nptr = (const long long *)r->sdev.p;  // StepDev::n is the first member
+    cudaStream_t st = r->cap;
+    p->capturing = true;
+    const unsigned long long l0 = g_launches.load();
+    MOT_CUDA_TRY(cudaGraphCreate(&r->step_graph, 0));
+    MOT_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, r->step_graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    auto body = [&]() -> mot_status {
+        count_launch();
+        k_step_begin<<<1, 32, 0, st>>>(sd);
+        MOT_CHECK_LAUNCH();
+        if (mixed) MOT_TRY(history_rhs<float>(r, st, nptr));
+        else MOT_TRY(history_rhs<double>(r, st, nptr));
+        if (p->opt.guess == 1) {
+            count_launch();
+            k_extrapolate<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, n);
+            MOT_CHECK_LAUNCH();
+        }
+        MOT_TRY(dev_norms2(r, (const double *)r->b.p, (double *)r->b2.p, st));
+        if (!mixed) {
+            const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
+            MOT_TRY(tfqmr_capture<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, st,
+                                          r->cap2, 1));
+            EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
+                             (const double *)p->eps.p, pr, p->N[0]};
+            MOT_TRY((z0_product<double, double>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, st));
+            count_launch();
+            k_fp64_finish<<<1, 32, 0, st>>>((const double *)r->b2.p, (const double *)r->r2.p, r->B, sd);
+            MOT_CHECK_LAUNCH();
+            MOT_TRY(ring_push<double>(r, st, nptr));
+        } else {
+            const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
+            float *r32 = (float *)r->r32.p;
+            float *c32 = r32 + n;
+            EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
+                             (const double *)p->eps.p, pr, p->N[0]};
+            // residual of the initial guess, then sweeps while it misses tol
+            MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, st));
+            WhileNode wo;
+            MOT_TRY(while_handle(st, wo, 0));
+            count_launch();
+            k_refine_cond<<<1, 32, 0, st>>>(wo.h, (const double *)r->b2.p, (const double *)r->r2.p, r->B, tol,
+                                            p->opt.max_refine, sd, 0);
+            MOT_CHECK_LAUNCH();
+            MOT_TRY(while_insert(st, r->cap2, wo, [&](cudaStream_t cs) -> mot_status {
+                count_launch();
+                k_convert<float, double><<<grid_for(n), 256, 0, cs>>>(r32, (const double *)r->r.p, n);
+                MOT_CHECK_LAUNCH();
+                MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0));
+                count_launch();
+                k_add_into<double, float><<<grid_for(n), 256, 0, cs>>>((double *)r->J.p, c32, n);
+                MOT_CHECK_LAUNCH();
+                MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, cs)));
+                MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, cs));
+                count_launch();
+                k_refine_cond<<<1, 32, 0, cs>>>(wo.h, (const double *)r->b2.p, (const double *)r->r2.p, r->B, tol,
+                                                p->opt.max_refine, sd, 1);
+                MOT_CHECK_LAUNCH();
+                return MOT_OK;
+            }, &r->k_outer));
+            r->k_outer -= r->k_inner;  // the nested loop body is counted per iteration
+            MOT_TRY(ring_push<float>(r, st, nptr));
+        }
+        count_launch();
+        k_step_end<<<1, 32, 0, st>>>(sd, (StepStatDev *)r->sstats.p, r->sstats_cap);
+        MOT_CHECK_LAUNCH();
+        return MOT_OK;
+    };
+    r->k_outer = 0;
+    r->k_inner = 0;
+    mot_status s = body();
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(st, &out);
+    p->capturing = false;
+    const unsigned long long captured = g_launches.load() - l0;
+    g_launches.fetch_sub(captured);  // captured, not launched: counted per executed step
+    r->k_fixed = (int)captured - r->k_outer - r->k_inner;
+    if (s != MOT_OK) return s;
+    if (ce != cudaSuccess) MOT_FAIL(MOT_ECUDA, std::string("step capture: ") + cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&r->step_exec, r->step_graph, 0);
+    if (ie != cudaSuccess) MOT_FAIL(MOT_ECUDA, std::string("step graph instantiate: ") + cudaGetErrorString(ie));
     return MOT_OK;
 }
 
@@ -1454,6 +1891,15 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->dots, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->ctl, sizeof(int) * 2)) != MOT_OK) return fail(s);
     if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithFlags(&r->cap2, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithFlags(&r->cap3, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
+    r->sstats_cap = 1024;
+    if ((s = dalloc(r->sdev, sizeof(StepDev))) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->sstats, sizeof(StepStatDev) * r->sstats_cap)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->b2, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->r2, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
+    cudaMemsetAsync(r->sdev.p, 0, sizeof(StepDev), p->ctx->stream);
+
     // Z0 workspace for the batch in both precisions (FP64 residual / FP32 inner)
     size_t a, bb;
     z0_ws_bytes(p, nrhs, sizeof(double2), &a, &bb);
@@ -1476,7 +1922,69 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     MOT_CUDA_TRY(cudaSetDevice(r->p->ctx->device));
     const long n = 3L * r->p->N[0] * r->p->N[1] * r->p->N[2] * r->B;
     mot_status result = MOT_OK;
+    // graph mode (default): after one eager step (which sets every kernel's
+    // attributes), each step is one graph launch with its control on the
+    // device; MOTJVIE_EAGER=1 keeps host-driven steps
+    const bool eager_env = r->p->opt.graph == 0;
+    if (!eager_env && r->n >= 1 && nsteps > 0) {
+        cudaStream_t st = r->p->ctx->stream;
+        if (!r->step_exec) MOT_TRY(build_step_graph(r));
+        // device step index follows the host's
+        long long n0 = r->n;
+        MOT_CUDA_TRY(cudaMemcpyAsync(r->sdev.p, &n0, sizeof(long long), cudaMemcpyHostToDevice, st));
+        int done = 0;
+        while (done < nsteps) {
+            const int chunk = std::min(nsteps - done, r->sstats_cap);
+            MOT_CUDA_TRY(cudaMemsetAsync((char *)r->sdev.p + offsetof(StepDev, nstat), 0, sizeof(int), st));
+            for (int i = 0; i < chunk; ++i) {
+                const int sidx = done + i;
+                if (stats) MOT_CUDA_TRY(cudaEventRecord(r->ev[0], st));
+                MOT_CUDA_TRY(cudaGraphLaunch(r->step_exec, st));
+                r->n += 1;
+                if (J_out)
+                    MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)sidx * n, r->J.p, sizeof(double) * n,
+                                                 cudaMemcpyDeviceToHost, st));
+                if (stats) {
+                    MOT_CUDA_TRY(cudaEventRecord(r->ev[3], st));
+                    MOT_CUDA_TRY(cudaEventSynchronize(r->ev[3]));
+                    mot_step_stats &S = stats[sidx];
+                    memset(&S, 0, sizeof(S));
+                    if (cudaEventElapsedTime(&S.ms_solve, r->ev[0], r->ev[3]) != cudaSuccess) {
+                        S.ms_solve = 0.f;
+                        cudaGetLastError();
+                    }
+                }
+            }
+            std::vector<StepStatDev> hs(chunk);
+            MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), r->sstats.p, sizeof(StepStatDev) * chunk, cudaMemcpyDeviceToHost, st));
+            MOT_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int i = 0; i < chunk; ++i) {
+                // kernels the step graph executed: fixed part, each refinement
+                // sweep's body, each TFQMR loop iteration
+                g_launches.fetch_add((unsigned long long)(r->k_fixed + r->k_outer * hs[i].sweeps +
+                                                          r->k_inner * hs[i].loops));
+                if (hs[i].notconv) {
+                    result = MOT_ENOTCONV;
+                    set_error("tolerance not reached at step " + std::to_string(r->n - chunk + i) + " (relres " +
+                              std::to_string(hs[i].relres) + ")");
+                }
+                if (stats) {
+                    mot_step_stats &S = stats[done + i];
+                    S.iters = hs[i].iters;
+                    S.sweeps = hs[i].sweeps;
+                    S.relres = hs[i].relres;
+                    S.mvps = hs[i].mvps;
+                }
+            }
+            done += chunk;
+        }
+        return result;
+    }
     for (int s = 0; s < nsteps; ++s) {
+        if (!eager_env && r->n >= 1) {  // switch to graph mode after the first step
+            mot_status g = mot_run_step(r, nsteps - s, J_out ? J_out + (size_t)s * n : nullptr, stats ? stats + s : nullptr);
+            return g != MOT_OK ? g : result;
+        }
         mot_status st = run_one_step(r, stats ? stats + s : nullptr);
         if (st != MOT_OK && st != MOT_ENOTCONV) return st;
         if (st == MOT_ENOTCONV) result = st;
@@ -1534,7 +2042,15 @@ void mot_run_destroy(mot_run *r) {
         if (G->graph) cudaGraphDestroy(G->graph);
     }
     dfree(r->ctl);
+    if (r->step_exec) cudaGraphExecDestroy(r->step_exec);
+    if (r->step_graph) cudaGraphDestroy(r->step_graph);
+    dfree(r->sdev);
+    dfree(r->sstats);
+    dfree(r->b2);
+    dfree(r->r2);
     if (r->cap) cudaStreamDestroy(r->cap);
+    if (r->cap2) cudaStreamDestroy(r->cap2);
+    if (r->cap3) cudaStreamDestroy(r->cap3);
     delete r;
 }
 

@@ -292,6 +292,7 @@ struct PlaneWaveDev {
     //   E(tau) = exp(-tau^2/(2 sigma^2) + i w tau), C(s) = exp(-delta^2/(2 sigma^2) - i w delta).
     double beta[3];
     double Cre[8], Cim[8], delta[8];
+    float delta_over_sigma[8];  // delta(s) / sigma for the FP32 path
 };
 
 // host: fill beta, C(s), delta(s) of a plane wave for voxel size h
@@ -307,6 +308,7 @@ inline void planewave_factors(PlaneWaveDev &P, double h) {
         P.Cre[q] = mag * cos(w * d);
         P.Cim[q] = -mag * sin(w * d);
         P.delta[q] = d;
+        P.delta_over_sigma[q] = (float)(d / P.sigma);
     }
 }
 
@@ -314,10 +316,12 @@ inline void planewave_factors(PlaneWaveDev &P, double h) {
 // g'(tau) = Re[(-tau/sigma^2 + i w) E(tau)] / (sigma sqrt(2 pi))
 // FAST: transcendentals in FP32 after an FP64 reduction of the phase to
 // [-pi, pi] (relative error ~1e-7, used by the mixed-precision path); else FP64.
+// nptr (graph mode): t = (*nptr) * dt instead of the argument t
 template <bool FAST>
 __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ eps,
                            const PlaneWaveDev *__restrict__ pw, int Nx, int Ny, int Nz, double h, double t,
-                           int nrhs) {
+                           int nrhs, const long long *__restrict__ nptr, double dt) {
+    if (nptr) t = (double)(*nptr) * dt;
     const long n = (long)Nx * Ny * Nz;
     const double c0 = 299792458.0, eps0 = 8.8541878128e-12;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n * nrhs; i += (long)gridDim.x * blockDim.x) {
@@ -331,36 +335,50 @@ __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ 
         const double is2 = 1.0 / (P.sigma * P.sigma);
         double rx = (mx + 0.5) * h - P.rref[0], ry = (my + 0.5) * h - P.rref[1], rz = (mz + 0.5) * h - P.rref[2];
         double tc = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
-        double s, c, g, u0, u1, u2;
+        double acc;
         if (FAST) {
+            // phase reduced to [-pi, pi] in FP64, the rest in FP32 (relative error ~1e-7)
             const double twopi = 6.283185307179586476925287;
             double ph = w * tc;
             ph -= twopi * rint(ph / twopi);
             float sf, cf;
             sincosf((float)ph, &sf, &cf);
-            s = sf;
-            c = cf;
-            g = expf((float)(-0.5 * tc * tc * is2));
-            u0 = expf((float)(P.beta[0] * tc * is2));
-            u1 = expf((float)(P.beta[1] * tc * is2));
-            u2 = expf((float)(P.beta[2] * tc * is2));
-        } else {
-            sincos(w * tc, &s, &c);
-            g = exp(-0.5 * tc * tc * is2);
-            u0 = exp(P.beta[0] * tc * is2);
-            u1 = exp(P.beta[1] * tc * is2);
-            u2 = exp(P.beta[2] * tc * is2);
-        }
-        double Er = g * c, Ei = g * s;
-        double v0 = 1.0 / u0, v1 = 1.0 / u1, v2 = 1.0 / u2;
-        double acc = 0.0;
+            const float g = expf((float)(-0.5 * tc * tc * is2));
+            const float Er = g * cf, Ei = g * sf;
+            const float a0 = (float)(P.beta[0] * tc * is2), a1 = (float)(P.beta[1] * tc * is2),
+                        a2 = (float)(P.beta[2] * tc * is2);
+            const float u0 = expf(a0), u1 = expf(a1), u2 = expf(a2);
+            const float v0 = expf(-a0), v1 = expf(-a1), v2 = expf(-a2);
+            const float tcs = (float)(tc / P.sigma);  // tau_c / sigma
+            const float ws = (float)(w * P.sigma);
+            float accf = 0.f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            double f = ((q & 1) ? u0 : v0) * ((q & 2) ? u1 : v1) * ((q & 4) ? u2 : v2);
-            double zr = f * (Er * P.Cre[q] - Ei * P.Cim[q]);
-            double zi = f * (Er * P.Cim[q] + Ei * P.Cre[q]);
-            double tau = tc - P.delta[q];
-            acc += -tau * is2 * zr - w * zi;  // Re[(-tau/sigma^2 + i w)(zr + i zi)]
+            for (int q = 0; q < 8; ++q) {
+                const float f = ((q & 1) ? u0 : v0) * ((q & 2) ? u1 : v1) * ((q & 4) ? u2 : v2);
+                const float cr = (float)P.Cre[q], ci = (float)P.Cim[q];
+                const float zr = f * (Er * cr - Ei * ci);
+                const float zi = f * (Er * ci + Ei * cr);
+                // scaled by sigma: (-tau/sigma^2) sigma = -tau/sigma, w sigma
+                const float tau_s = tcs - P.delta_over_sigma[q];
+                accf += -tau_s * zr - ws * zi;
+            }
+            acc = (double)accf / P.sigma;
+        } else {
+            double s, c;
+            sincos(w * tc, &s, &c);
+            double g = exp(-0.5 * tc * tc * is2);
+            double u0 = exp(P.beta[0] * tc * is2), u1 = exp(P.beta[1] * tc * is2), u2 = exp(P.beta[2] * tc * is2);
+            double v0 = 1.0 / u0, v1 = 1.0 / u1, v2 = 1.0 / u2;
+            double Er = g * c, Ei = g * s;
+            acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                double f = ((q & 1) ? u0 : v0) * ((q & 2) ? u1 : v1) * ((q & 4) ? u2 : v2);
+                double zr = f * (Er * P.Cre[q] - Ei * P.Cim[q]);
+                double zi = f * (Er * P.Cim[q] + Ei * P.Cre[q]);
+                double tau = tc - P.delta[q];
+                acc += -tau * is2 * zr - w * zi;  // Re[(-tau/sigma^2 + i w)(zr + i zi)]
+            }
         }
         inc[i] = (ep - 1.0) * eps0 * amp * 0.125 * acc;
     }

@@ -74,13 +74,16 @@ template <typename T, int S>
 __global__ void __launch_bounds__(512) k_axis(const cplx<T> *__restrict__ in, cplx<T> *__restrict__ out,
                                               FftPlan pl, const cplx<T> *__restrict__ tw_g, int H, int tx,
                                               int Lin, int Lout, int O2, long is1, long is2, long ias,
-                                              long os1, long os2, long oas) {
+                                              long os1, long os2, long oas, const long long *__restrict__ nptr,
+                                              int ell, long slot_stride) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     const int M = pl.M;
     C *a = tw + M;
     C *b = a + M * tx;
+    // graph mode: write into history-ring slot (*nptr mod ell)
+    if (nptr) out += (long)(*nptr % ell) * slot_stride;
     load_twiddles(tw, tw_g, M);
     const int o = blockIdx.y, o1 = o / O2, o2 = o - o1 * O2;
     const int kx0 = blockIdx.x * tx;
@@ -202,6 +205,199 @@ __global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_inverse(const cplx<T> *_
     for (int i = threadIdx.x; i < Ny * Nx; i += blockDim.x) {
         int y = (int)fdiv((unsigned)i, fNx);
         C z = rx[(y >> 1) * Mx + (i - y * Nx)];
+        pe(i, (y & 1) ? z.y : z.x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// xy plane passes specialised for compile-time Mx = RX1*RX2, My = RY1*RY2.
+// Each 1-D FFT is two register stages (R1-point DFTs, twiddle, R2-point DFTs)
+// with one shared-memory exchange.  Shared memory: two buffers of
+// max(ceil(Ny/2)*(Mx+1), H*(My+1)) complex plus the two twiddle tables.
+// ---------------------------------------------------------------------------
+template <typename T, int RX1, int RX2, int RY1, int RY2>
+__host__ __device__ inline size_t xy_r_buf(int Ny) {
+    constexpr int Mx = RX1 * RX2, My = RY1 * RY2, H = Mx / 2 + 1;
+    const int np = (Ny + 1) / 2;
+    const int a = np * (Mx + 1), b = H * (My + 1);
+    return (size_t)(a > b ? a : b);
+}
+template <typename T, int RX1, int RX2, int RY1, int RY2>
+__host__ __device__ inline size_t xy_r_smem_bytes(int Ny) {
+    return (2 * xy_r_buf<T, RX1, RX2, RY1, RY2>(Ny) + RX1 * RX2 + RY1 * RY2) * sizeof(cplx<T>);
+}
+
+template <typename TI, typename T, int RX1, int RX2, int RY1, int RY2>
+__global__ void __launch_bounds__(512) k_xy_forward_r(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
+                                                      int Ny, const cplx<T> *__restrict__ twx_g,
+                                                      const cplx<T> *__restrict__ twy_g) {
+    using C = cplx<T>;
+    constexpr int Mx = RX1 * RX2, My = RY1 * RY2, H = Mx / 2 + 1, PX = Mx + 1, PY = My + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int np = (Ny + 1) / 2;
+    const size_t nb = xy_r_buf<T, RX1, RX2, RY1, RY2>(Ny);
+    C *twx = reinterpret_cast<C *>(smem_raw);
+    C *twy = twx + Mx;
+    C *A = twy + My;  // [np][PX] then [H][PY]
+    C *Bf = A + nb;   // [np][Mx]  then [H][PY]
+    load_twiddles(twx, twx_g, Mx);
+    load_twiddles(twy, twy_g, My);
+    __syncthreads();
+    const long plane = blockIdx.x;
+    const TI *src = x + plane * (long)Ny * Nx;
+    // x stage A: pencil p = rows (2p, 2p+1) as re/im, thread t < RX2 loads e = t + RX2 m
+    for (int task = threadIdx.x; task < np * RX2; task += blockDim.x) {
+        const int p = task / RX2, t = task - p * RX2;
+        C v[RX1];
+        const bool two = 2 * p + 1 < Ny;
+#pragma unroll
+        for (int m = 0; m < RX1; ++m) {
+            const int e = t + RX2 * m;
+            T re = T(0), im = T(0);
+            if (e < Nx) {
+                re = (T)src[(long)(2 * p) * Nx + e];
+                if (two) im = (T)src[(long)(2 * p + 1) * Nx + e];
+            }
+            v[m] = cmake<C>(re, im);
+        }
+        dft_small<RX1, -1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < RX1; ++k1) A[p * PX + k1 * RX2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], twx[t * k1]) : v[k1];
+    }
+    __syncthreads();
+    // x stage B: RX2-point DFTs -> natural order Z[k1 + RX1 k2] in Bf[p][.]
+    for (int task = threadIdx.x; task < np * RX1; task += blockDim.x) {
+        const int p = task / RX1, k1 = task - p * RX1;
+        C u[RX2];
+#pragma unroll
+        for (int t = 0; t < RX2; ++t) u[t] = A[p * PX + k1 * RX2 + t];
+        dft_small<RX2, -1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < RX2; ++k2) Bf[p * Mx + k1 + RX1 * k2] = u[k2];
+    }
+    __syncthreads();
+    // unpack the two real rows of each pencil into the half spectra, stored
+    // transposed for the y pass: A[kx][y]
+    for (int task = threadIdx.x; task < Ny * H; task += blockDim.x) {
+        const int y = task / H, k = task - y * H;
+        const C *row = Bf + (y >> 1) * Mx;
+        C z = row[k], zm = cconj(row[k == 0 ? 0 : Mx - k]);
+        C v;
+        if ((y & 1) == 0) { C s2 = cadd(z, zm); v = cmake<C>(T(0.5) * s2.x, T(0.5) * s2.y); }
+        else { C d2 = csub(z, zm); v = cmake<C>(T(0.5) * d2.y, T(-0.5) * d2.x); }
+        A[k * PY + y] = v;
+    }
+    __syncthreads();
+    // y stage A: pencil kx, thread t < RY2 takes y = t + RY2 m (zero for y >= Ny)
+    for (int task = threadIdx.x; task < H * RY2; task += blockDim.x) {
+        const int kx = task / RY2, t = task - kx * RY2;
+        C v[RY1];
+#pragma unroll
+        for (int m = 0; m < RY1; ++m) {
+            const int y = t + RY2 * m;
+            v[m] = y < Ny ? A[kx * PY + y] : cmake<C>(T(0), T(0));
+        }
+        dft_small<RY1, -1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < RY1; ++k1) Bf[kx * PY + k1 * RY2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], twy[t * k1]) : v[k1];
+    }
+    __syncthreads();
+    // y stage B: RY2-point DFTs, rows ky = k1 + RY1 k2 straight to HBM (kx fastest)
+    C *dst = out + plane * (long)My * H;
+    for (int task = threadIdx.x; task < H * RY1; task += blockDim.x) {
+        const int k1 = task / H, kx = task - k1 * H;
+        C u[RY2];
+#pragma unroll
+        for (int t = 0; t < RY2; ++t) u[t] = Bf[kx * PY + k1 * RY2 + t];
+        dft_small<RY2, -1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < RY2; ++k2) dst[(k1 + RY1 * k2) * H + kx] = u[k2];
+    }
+}
+
+template <typename T, class Epi, int RX1, int RX2, int RY1, int RY2>
+__global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict__ in, int Nx, int Ny, int Nz,
+                                                      const cplx<T> *__restrict__ twx_g,
+                                                      const cplx<T> *__restrict__ twy_g, Epi epi) {
+    using C = cplx<T>;
+    constexpr int Mx = RX1 * RX2, My = RY1 * RY2, H = Mx / 2 + 1, PX = Mx + 1, PY = My + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int np = (Ny + 1) / 2;
+    const size_t nb = xy_r_buf<T, RX1, RX2, RY1, RY2>(Ny);
+    C *twx = reinterpret_cast<C *>(smem_raw);
+    C *twy = twx + Mx;
+    C *A = twy + My;
+    C *Bf = A + nb;
+    load_twiddles(twx, twx_g, Mx);
+    load_twiddles(twy, twy_g, My);
+    __syncthreads();
+    const long plane = blockIdx.x;
+    const C *src = in + plane * (long)My * H;
+    // inverse y stage A: pencil kx, thread t < RY2 loads ky = t + RY2 m from HBM
+    for (int task = threadIdx.x; task < H * RY2; task += blockDim.x) {
+        const int t = task / H, kx = task - t * H;  // kx fastest: coalesced rows
+        C v[RY1];
+#pragma unroll
+        for (int m = 0; m < RY1; ++m) v[m] = src[(t + RY2 * m) * H + kx];
+        dft_small<RY1, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < RY1; ++k1)
+            A[kx * PY + k1 * RY2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(twy[t * k1])) : v[k1];
+    }
+    __syncthreads();
+    // inverse y stage B: rows y = k1 + RY1 k2 < Ny kept, stored Bf[kx][y]
+    for (int task = threadIdx.x; task < H * RY1; task += blockDim.x) {
+        const int kx = task / RY1, k1 = task - kx * RY1;
+        C u[RY2];
+#pragma unroll
+        for (int t = 0; t < RY2; ++t) u[t] = A[kx * PY + k1 * RY2 + t];
+        dft_small<RY2, +1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < RY2; ++k2) {
+            const int y = k1 + RY1 * k2;
+            if (y < Ny) Bf[kx * PY + y] = u[k2];
+        }
+    }
+    __syncthreads();
+    // Hermitian extension of rows (2p, 2p+1) into one complex pencil, inverse x
+    // stage A: thread t < RX2 takes k = t + RX2 m
+    for (int task = threadIdx.x; task < np * RX2; task += blockDim.x) {
+        const int p = task / RX2, t = task - p * RX2;
+        const bool two = 2 * p + 1 < Ny;
+        C v[RX1];
+#pragma unroll
+        for (int m = 0; m < RX1; ++m) {
+            const int k = t + RX2 * m;
+            const int kk = k < H ? k : Mx - k;
+            C a = Bf[kk * PY + 2 * p];
+            C b = two ? Bf[kk * PY + 2 * p + 1] : cmake<C>(T(0), T(0));
+            if (kk == 0 || 2 * kk == Mx) { a.y = T(0); b.y = T(0); }
+            if (k >= H) { a = cconj(a); b = cconj(b); }
+            v[m] = cmake<C>(a.x - b.y, a.y + b.x);
+        }
+        dft_small<RX1, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < RX1; ++k1)
+            A[p * PX + k1 * RX2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(twx[t * k1])) : v[k1];
+    }
+    __syncthreads();
+    // inverse x stage B: natural order e = k1 + RX1 k2 into Bf[p][e]
+    for (int task = threadIdx.x; task < np * RX1; task += blockDim.x) {
+        const int p = task / RX1, k1 = task - p * RX1;
+        C u[RX2];
+#pragma unroll
+        for (int t = 0; t < RX2; ++t) u[t] = A[p * PX + k1 * RX2 + t];
+        dft_small<RX2, +1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < RX2; ++k2) Bf[p * PX + k1 + RX1 * k2] = u[k2];
+    }
+    __syncthreads();
+    // epilogue, x fastest (rows 2p, 2p+1 are the real and imaginary parts)
+    const auto pe = epi.bind(plane, Nz, Ny * Nx);
+    const FastDiv fNx = make_fastdiv((unsigned)Nx);
+    for (int i = threadIdx.x; i < Ny * Nx; i += blockDim.x) {
+        const int y = (int)fdiv((unsigned)i, fNx), e = i - y * Nx;
+        const C z = Bf[(y >> 1) * PX + e];
         pe(i, (y & 1) ? z.y : z.x);
     }
 }
@@ -341,6 +537,122 @@ __global__ void __launch_bounds__(256) k_z_history(const cplx<T> *__restrict__ r
 }
 
 // ---------------------------------------------------------------------------
+// present-time z pass specialised for a compile-time length M = R1 * R2.
+// Columns are consecutive positions col = ky*H + kx of the (ky, kx) plane, so a
+// tile of 32 columns is 32 contiguous complex values in every z row.
+// stage A  (thread = (t, c), t < R2): x[t + R2 m], m < R1, straight from HBM,
+//          R1-point DFT in registers, twiddle W_M^(t k1), to shared memory;
+// stage B  (task = (k1, c)): R2-point DFT over t -> X[k1 + R1 k2], 3x3 Green
+//          multiply, inverse R2-point DFT, twiddle W_M^(-t k1), to shared memory;
+// stage A' (thread = (t, c)): inverse R1-point DFT over k1, rows z < Nz to HBM.
+// grid = (ceil(My*H/32), B); block = 32*R2; smem = M + 3*32*(M+1) complex
+// ---------------------------------------------------------------------------
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(32 * R2) k_z_green_r(cplx<T> *__restrict__ buf, const T *__restrict__ L,
+                                                       const cplx<T> *__restrict__ tw_g, int Nz, int My, int H,
+                                                       Octant oc) {
+    using C = cplx<T>;
+    constexpr int M = R1 * R2, TC = 32, RS = M + 1;  // padded row stride in shared memory
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *S = tw + M;  // [q][c][RS]
+    load_twiddles(tw, tw_g, M);
+    const int ncols = My * H;
+    const int col0 = blockIdx.x * TC;
+    const long plane = ncols;                 // z stride
+    const long comp = (long)Nz * plane;       // component stride
+    C *base = buf + (long)blockIdx.y * 3 * comp;
+    const int c = threadIdx.x % TC, t = threadIdx.x / TC;
+    const bool live = col0 + c < ncols;
+    __syncthreads();
+    // ---- stage A
+#pragma unroll 1
+    for (int q = 0; q < 3; ++q) {
+        C v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int z = t + R2 * m;
+            v[m] = (live && z < Nz) ? base[q * comp + (long)z * plane + col0 + c] : cmake<C>(T(0), T(0));
+        }
+        dft_small<R1, -1>(v);
+        C *row = S + (q * TC + c) * RS;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            C x = v[k1];
+            if (k1 > 0 && t > 0) x = cmul(x, tw[t * k1]);
+            row[k1 * R2 + t] = x;
+        }
+    }
+    __syncthreads();
+    // ---- stage B1: R2-point DFT of every (q, c, k1) row segment, in place
+    for (int task = threadIdx.x; task < 3 * R1 * TC; task += blockDim.x) {
+        const int q = task / (R1 * TC), rem = task - q * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
+        C *seg = S + (q * TC + cc) * RS + k1 * R2;
+        C u[R2];
+#pragma unroll
+        for (int tt = 0; tt < R2; ++tt) u[tt] = seg[tt];
+        dft_small<R2, -1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) seg[k2] = u[k2];
+    }
+    __syncthreads();
+    // ---- stage B2: 3x3 Green multiply at every (kz, c); kz = k1 + R1 k2 sits at k1*R2 + k2
+    const long cs = (long)oc.Kz * oc.Ky * oc.H;
+    const FastDiv fH = make_fastdiv((unsigned)H);
+    for (int task = threadIdx.x; task < M * TC; task += blockDim.x) {
+        const int pos = task / TC, cc = task - pos * TC;  // pos = k1*R2 + k2
+        const int col = col0 + cc;
+        if (col >= ncols) continue;
+        const int k1 = pos / R2, k2 = pos - k1 * R2, kz = k1 + R1 * k2;
+        const int ky = (int)fdiv((unsigned)col, fH), kx = col - ky * H;
+        int fy, fz;
+        float sy, sz;
+        if (2 * ky > My) { fy = My - ky; sy = -1.f; } else { fy = ky; sy = 1.f; }
+        if (2 * kz > M) { fz = M - kz; sz = -1.f; } else { fz = kz; sz = 1.f; }
+        const long idx = ((long)fz * oc.Ky + fy) * oc.H + kx;
+        C in[3], out[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) in[q] = S[(q * TC + cc) * RS + pos];
+        green_mul<T>(L, cs, idx, sz, sy, in, out);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) S[(q * TC + cc) * RS + pos] = out[q];
+    }
+    __syncthreads();
+    // ---- stage B3: inverse R2-point DFT over k2, twiddle W_M^(-t k1)
+    for (int task = threadIdx.x; task < 3 * R1 * TC; task += blockDim.x) {
+        const int q = task / (R1 * TC), rem = task - q * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
+        C *seg = S + (q * TC + cc) * RS + k1 * R2;
+        C u[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) u[k2] = seg[k2];
+        dft_small<R2, +1>(u);
+#pragma unroll
+        for (int tt = 0; tt < R2; ++tt) {
+            C x = u[tt];
+            if (k1 > 0 && tt > 0) x = cmul(x, cconj(tw[tt * k1]));
+            seg[tt] = x;
+        }
+    }
+    __syncthreads();
+    // ---- stage A': inverse R1-point DFT over k1, rows z = t + R2 m < Nz
+#pragma unroll 1
+    for (int q = 0; q < 3; ++q) {
+        C v[R1];
+        const C *row = S + (q * TC + c) * RS;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = row[k1 * R2 + t];
+        dft_small<R1, +1>(v);
+        if (live) {
+#pragma unroll
+            for (int m = 0; m < R1; ++m) {
+                const int z = t + R2 * m;
+                if (z < Nz) base[q * comp + (long)z * plane + col0 + c] = v[m];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // history z pass over the mirrored row pair (ky, My - ky): both rows fold to
 // the same Green-spectrum octant row (odd components change sign), so each
 // Lambda_k value is read once for the two rows.  grid = (ceil(H/tx), B*(My/2+1));
@@ -350,7 +662,12 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_z_history2(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
                                                     cplx<T> *__restrict__ out, FftPlan pl,
                                                     const cplx<T> *__restrict__ tw_g, int Nz, int My, int H, int tx,
-                                                    Octant oc, int nrhs, int ell, long n, int kmax) {
+                                                    Octant oc, int nrhs, int ell, long n, int kmax,
+                                                    const long long *__restrict__ nptr) {
+    if (nptr) {  // graph mode: step index from device memory
+        n = (long)*nptr;
+        kmax = (int)(n < ell ? n : ell);
+    }
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
@@ -381,7 +698,7 @@ __global__ void __launch_bounds__(512) k_z_history2(const cplx<T> *__restrict__ 
             const long r1 = r0 + (long)(ky1 - ky0) * H;
             long s = (n - 1) % ell;
             if (s < 0) s += ell;
-#pragma unroll 2
+#pragma unroll 4
             for (int k = 1; k <= kmax; ++k) {
                 const T *L = Lh + (long)k * 6 * cs + lidx;
                 const T gxx = L[0], gyy = L[cs], gzz = L[2 * cs];

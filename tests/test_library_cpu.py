@@ -60,3 +60,30 @@ def test_synthetic_inputs_are_deterministic():
     assert (p[8:51] == 3.5).sum() == 4 * 448 * 43 and (p[51:72] == 6.0).sum() == 4 * 448 * 21
     # reference splitmix64 first output for seed 0 (published test vector 0xE220A8397B1DCDAF)
     assert synthetic.splitmix64(0, 1)[0] == (0xE220A8397B1DCDAF >> 11) * 2.0**-53
+
+
+def test_ctypes_structs_match_header(tmp_path):
+    """The binding's ctypes structs have the C header's sizes and field offsets."""
+    import ctypes
+    import subprocess
+
+    structs = {"mot_planewave": mot.mot_planewave, "mot_options": mot.mot_options,
+               "mot_problem_info": mot.mot_problem_info, "mot_step_stats": mot.mot_step_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/motjvie.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+    # the binding's defaults follow the header's documented defaults
+    o = mot.default_options()
+    assert (o.maxit, o.inner_tol, o.max_refine, o.delta, o.timing, o.guess, o.graph) == (500, 1e-6, 6, 0.0, 0, 0, 1)
