@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MOT steps/s, Z0 FFT-matvec HBM GB/s (FP32 vs FP64), p50/p99 latency"
 UNIT = "steps/s"
+GRAPH_MODES = {"step": 1, "loop": 0, "none": 2}  # mot_options.graph values
 
 
 def _peaks():
@@ -91,7 +92,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -221,8 +222,9 @@ def native(args, ws, rank, local):
     nv = int(np.prod(N))
     B = len(w["exc"])
     ctx = mot.mot_ctx_create(local, stream.cuda_stream)
+    gopt = mot.default_options(graph=GRAPH_MODES[args.graph_mode])
     t_setup = time.perf_counter()
-    prob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"])
+    prob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"], gopt)
     run = mot.mot_run_create(prob, w["exc"], prec)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
@@ -233,35 +235,31 @@ def native(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     K = args.steps
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    stats = []
+    sts = (mot.mot_step_stats * K)()
     l0 = mot.mot_kernel_launches()
     e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         e_all0.record(stream)
-        for i in range(K):
-            evs[i][0].record(stream)
-            mot.mot_run_step(run, 1, None, st, allow_notconv=True)
-            evs[i][1].record(stream)
-            s = st[0]
-            stats.append((s.iters, s.sweeps, s.relres, s.mvps, s.ms_zhist, s.ms_zgreen, s.ms_history, s.ms_solve,
-                          s.ms_push))
+        # K steps in one call; the library records CUDA events around each step
+        mot.mot_run_step(run, K, None, sts, allow_notconv=True)
         e_all1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     launches = mot.mot_kernel_launches() - l0
+    stats = [(s.iters, s.sweeps, s.relres, s.mvps, s.ms_zhist, s.ms_zgreen, s.ms_history, s.ms_solve, s.ms_push)
+             for s in sts]
     barrier(ws)
     elapsed = e_all0.elapsed_time(e_all1) / 1e3
     elapsed_max = max_over_ranks(ws, elapsed, dev)
-    lat = sorted(a.elapsed_time(b) for a, b in evs)
+    lat = sorted(s[6] + s[7] + s[8] for s in stats)
     clocks = clk.summary()
 
-    # ---- kernel timing region: the same run continued host-driven with CUDA
-    # events around the history z pass and the Z0 spectral z passes (kernels
-    # inside CUDA graphs cannot be bracketed by events)
-    kopt = mot.default_options(timing=1, graph=0)
+    # ---- kernel timing region: the same workload host-driven without CUDA
+    # graphs, with CUDA events around the history z pass and every Z0 spectral
+    # z pass (kernels inside CUDA graphs cannot be bracketed by events)
+    kopt = mot.default_options(timing=1, graph=2)
     kprob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"], kopt)
     krun = mot.mot_run_create(kprob, w["exc"], prec)
     kst = (mot.mot_step_stats * 1)()
@@ -344,7 +342,7 @@ def native(args, ws, rank, local):
     for label, wl, pr_, steps_c in (("fp64", w, mot.MOT_FP64, 8),
                                     ("mixed_batch16", workload("cube64_b16"), mot.MOT_MIXED, 6)):
         try:
-            pb = mot.mot_problem_create(ctx, wl["N"], wl["h"], wl["eps"], wl["alpha"])
+            pb = mot.mot_problem_create(ctx, wl["N"], wl["h"], wl["eps"], wl["alpha"], gopt)
             rb = mot.mot_run_create(pb, wl["exc"], pr_)
             mot.mot_run_step(rb, 3, None, None, allow_notconv=True)
             torch.cuda.synchronize()
@@ -362,7 +360,7 @@ def native(args, ws, rank, local):
             compare[label] = {"error": str(e)[:200]}
 
     # ---- e2e: public API from host buffers, one call per step with a host J_n
-    e2e = end_to_end(mot, ctx, w, prec, K, stream)
+    e2e = end_to_end(mot, ctx, w, prec, K, stream, gopt)
 
     mot.mot_run_destroy(run)
     mot.mot_problem_destroy(prob)
@@ -374,7 +372,7 @@ def native(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": elapsed_max / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == mot.MOT_MIXED else "f64",
         "data": "synthetic (seeded SplitMix64 permittivity blocks, analytic plane-wave pulse)",
-        "config": dict(describe(w, args.precision), l2="inputs larger than L2: each step reads the "
+        "config": dict(describe(w, args.precision), graph_mode=args.graph_mode, l2="inputs larger than L2: each step reads the "
                        f"{ell}-slot history ring ({ell * B * 3 * Mh[2] * Mh[1] * Hh * cs / 1e9:.2f} GB)",
                        parallelism=f"replicas{ws}", ell=ell, M0=M0, Mh=Mh),
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
@@ -428,7 +426,7 @@ def cufft_baseline(mot, prob, w, dev, stream, flush):
     return {"us": statistics.median(ts) * 1e3}
 
 
-def end_to_end(mot, ctx, w, prec, K, stream):
+def end_to_end(mot, ctx, w, prec, K, stream, opt):
     """steps/s through the public C-ABI from host buffers: problem and run
     creation (host eps_r and plane waves copied in) plus K steps, each step
     copying J_n back to pinned host memory."""
@@ -442,7 +440,7 @@ def end_to_end(mot, ctx, w, prec, K, stream):
     Jn = Jh.numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"])
+    prob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"], opt)
     run = mot.mot_run_create(prob, w["exc"], prec)
     t1 = time.perf_counter()
     for _ in range(K):
@@ -484,12 +482,15 @@ def reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cube64_a8")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph-mode", default="step", choices=list(GRAPH_MODES),
+                    help="step: one CUDA graph per MOT step (default); loop: host-driven steps, one graph per TFQMR "
+                         "loop; none: no CUDA graphs (for per-kernel profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -92,8 +92,12 @@ typedef struct {
                          J_{n-2} (linear extrapolation)                            */
     int graph;        /* 1 (default): after the first step each step is one CUDA
                          graph launch whose loops and tests run on the device; 0:
-                         host-driven steps (needed for the timing option's
-                         per-kernel times)                                         */
+                         host-driven steps, each solve's TFQMR loop one graph
+                         launch (the timing option times the products outside
+                         it); 2: no CUDA graphs at all, every kernel launched
+                         from the host and the TFQMR loop tested on the host
+                         after each iteration (slowest; for per-kernel
+                         profilers and the timing option over every product)  */
 } mot_options;
 
 typedef struct {
@@ -116,8 +120,8 @@ typedef struct {
     int32_t mvps;      /* Z0 products applied in the step                        */
     float ms_zhist;    /* history z-pass kernel time (timing option, else 0)     */
     float ms_zgreen;   /* mean time of the step's timed Z0 spectral z passes
-                          (timing option with graph = 0; those outside the
-                          TFQMR loop graph)                                      */
+                          (timing option; graph = 0: those outside the TFQMR
+                          loop graph, graph = 2: all of them)                    */
 } mot_step_stats;
 
 typedef struct mot_ctx mot_ctx;

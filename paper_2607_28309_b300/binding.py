@@ -219,6 +219,8 @@ def mot_run_create(prob, exc, precision: int = MOT_FP64):
 
 
 def mot_run_step(run, nsteps: int, J_out=None, stats=None, allow_notconv: bool = False):
+    if stats is not None and len(stats) < nsteps:
+        raise ValueError(f"stats holds {len(stats)} entries, {nsteps} steps requested")
     st = lib().mot_run_step(run, int(nsteps), _ptr(J_out), ctypes.byref(stats[0]) if stats is not None else None)
     if st == MOT_ENOTCONV and allow_notconv:
         return st

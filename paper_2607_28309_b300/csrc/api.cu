@@ -249,6 +249,7 @@ struct AxisTw {
 
 struct mot_ctx {
     int device = 0;
+    int sms = 148;  // multiprocessors of the device
     cudaStream_t stream = nullptr;
     bool own_stream = false;
 };
@@ -340,7 +341,8 @@ struct mot_run {
     mot_problem *p = nullptr;
     cudaStream_t cap = nullptr;  // capture stream for the solve graphs
     LoopGraph loop64, loop32;
-    DBuf ctl;                    // device loop control: iteration count, cap
+    DBuf ctl;                    // device loop control: iteration count, cap, continue flag
+    DBuf ctr;                    // last-block tickets of the fused TFQMR reduction kernels (0 between launches)
     int B = 1;
     int prec = MOT_FP64;
     long n = 0;  // next step index
@@ -352,6 +354,7 @@ struct mot_run {
     DBuf scal, part1, part2, part3, dots;
     DBuf r32;  // mixed: residual in FP32 / correction
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> sev;  // graph mode: start/end event of each step of a chunk
     // whole-step graph (graph mode)
     cudaStream_t cap2 = nullptr, cap3 = nullptr;
     cudaGraph_t step_graph = nullptr;
@@ -403,7 +406,7 @@ template <typename T> const cplx<T> *twp(AxisTw *t);
 template <> const cplx<double> *twp<double>(AxisTw *t) { return (const double2 *)t->tw64.p; }
 template <> const cplx<float> *twp<float>(AxisTw *t) { return (const float2 *)t->tw32.p; }
 
-const size_t kSmemMax = 200 * 1024;
+constexpr size_t kSmemMax = 200 * 1024;
 // block sizes: the pencil passes are latency-bound at small grids, so they use
 // large CTAs to keep enough warps resident
 constexpr int kZThreads = 512;
@@ -468,13 +471,13 @@ mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw
 }
 
 // specialised plane kernels for the compiled (Mx, My) shapes; false -> generic
-template <typename TI, typename T, int RX1, int RX2, int RY1, int RY2>
-bool xy_forward_r_go(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
+template <class Src, typename T, int RX1, int RX2, int RY1, int RY2>
+bool xy_forward_r_go(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
     const size_t smem = xy_r_smem_bytes<T, RX1, RX2, RY1, RY2>(Ny);
     if (smem > kSmemMax) return false;
-    if (allow_smem<k_xy_forward_r<TI, T, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
+    if (allow_smem<k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
     count_launch();
-    k_xy_forward_r<TI, T, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(x, out, Nx, Ny, twp<T>(tx), twp<T>(ty));
+    k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(x, out, Nx, Ny, twp<T>(tx), twp<T>(ty));
     return true;
 }
 
@@ -494,14 +497,14 @@ inline bool specialised_off() {
     return off;
 }
 
-template <typename TI, typename T>
-bool xy_forward_r(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
+template <class Src, typename T>
+bool xy_forward_r(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
     if (specialised_off() || tx->M != ty->M) return false;
     switch (tx->M) {
-        case 20: return xy_forward_r_go<TI, T, 5, 4, 5, 4>(x, out, planes, Nx, Ny, tx, ty, st);
-        case 32: return xy_forward_r_go<TI, T, 8, 4, 8, 4>(x, out, planes, Nx, Ny, tx, ty, st);
-        case 72: return xy_forward_r_go<TI, T, 9, 8, 9, 8>(x, out, planes, Nx, Ny, tx, ty, st);
-        case 128: return xy_forward_r_go<TI, T, 16, 8, 16, 8>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 20: return xy_forward_r_go<Src, T, 5, 4, 5, 4>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 32: return xy_forward_r_go<Src, T, 8, 4, 8, 4>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 72: return xy_forward_r_go<Src, T, 9, 8, 9, 8>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 128: return xy_forward_r_go<Src, T, 16, 8, 16, 8>(x, out, planes, Nx, Ny, tx, ty, st);
         default: return false;
     }
 }
@@ -518,17 +521,17 @@ bool xy_inverse_r(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw 
     }
 }
 
-template <typename TI, typename T>
-mot_status launch_xy_forward(const TI *x, cplx<T> *out, int planes, int Nx, int Ny, int H, AxisTw *tx, AxisTw *ty,
+template <class Src, typename T>
+mot_status launch_xy_forward(Src x, cplx<T> *out, int planes, int Nx, int Ny, int H, AxisTw *tx, AxisTw *ty,
                              cudaStream_t st) {
-    if (xy_forward_r<TI, T>(x, out, planes, Nx, Ny, tx, ty, st)) {
+    if (xy_forward_r<Src, T>(x, out, planes, Nx, Ny, tx, ty, st)) {
         MOT_CHECK_LAUNCH();
         return MOT_OK;
     }
     size_t smem = xy_smem_bytes<T>(tx->M, ty->M, H, Ny);
-    MOT_TRY(allow_smem<k_xy_forward<TI, T>>());
+    MOT_TRY(allow_smem<k_xy_forward<Src, T>>());
     count_launch();
-    k_xy_forward<TI, T><<<planes, kXYThreadsOf<T>, smem, st>>>(x, out, Nx, Ny, H, planp<T>(tx), planp<T>(ty), twp<T>(tx), twp<T>(ty));
+    k_xy_forward<Src, T><<<planes, kXYThreadsOf<T>, smem, st>>>(x, out, Nx, Ny, H, planp<T>(tx), planp<T>(ty), twp<T>(tx), twp<T>(ty));
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
@@ -552,17 +555,41 @@ template <typename T> const T *L0_of(mot_problem *p);
 
 // specialised z pass when M0z = R1 * R2 is one of the compiled shapes;
 // returns false to fall back to the generic pass
-template <typename T, int R1, int R2> bool z_green_r_go(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
+template <typename T, int R1, int R2, int TC>
+bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
     const int My = p->M0[1], H = p->H0, Nz = p->N[2];
-    const size_t smem = (size_t)(R1 * R2 + 3 * 32 * (R1 * R2 + 1)) * sizeof(cplx<T>);
-    if (allow_smem<k_z_green_r<T, R1, R2>>() != MOT_OK) return false;
+    constexpr size_t smem = z_green_r_smem<T, R1, R2, TC>();
+    if (smem > kSmemMax || allow_smem<k_z_green_r<T, R1, R2, TC>>() != MOT_OK) return false;
     Octant oc = {p->M0[2], My, p->K0[2], p->K0[1], H};
-    dim3 grid((My * H + 31) / 32, (unsigned)nrhs);
+    dim3 grid((My * H + TC - 1) / TC, (unsigned)nrhs);
     if (!p->capturing) p->kt.begin(st, kTimeZGreen);
     count_launch();
-    k_z_green_r<T, R1, R2><<<grid, 32 * R2, smem, st>>>(Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H, oc);
+    k_z_green_r<T, R1, R2, TC><<<grid, 3 * TC * R2, smem, st>>>(Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H, oc);
     if (!p->capturing) p->kt.end(st);
     return true;
+}
+
+// columns per block TC: 8 (measured fastest for one and for sixteen
+// right-hand sides on the 72^3 grid), 16 or 32 where that block would not
+// fit; MOTJVIE_Z_COLS = 8 | 16 | 32 forces one for timing sweeps
+template <typename T, int R1, int R2, int TC> constexpr bool z_tc_ok() {
+    return 3 * TC * R2 <= 1024 && z_green_r_smem<T, R1, R2, TC>() <= kSmemMax;
+}
+
+inline int z_cols_forced() {
+    static const int f = getenv("MOTJVIE_Z_COLS") ? atoi(getenv("MOTJVIE_Z_COLS")) : 0;
+    return f;
+}
+
+template <typename T, int R1, int R2> bool z_green_r_go(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
+    const int f = z_cols_forced();
+    if constexpr (z_tc_ok<T, R1, R2, 32>())
+        if (f == 32) return z_green_r_tc<T, R1, R2, 32>(p, Bf, tz, nrhs, st);
+    if constexpr (z_tc_ok<T, R1, R2, 16>())
+        if (f == 16) return z_green_r_tc<T, R1, R2, 16>(p, Bf, tz, nrhs, st);
+    if constexpr (z_tc_ok<T, R1, R2, 8>()) return z_green_r_tc<T, R1, R2, 8>(p, Bf, tz, nrhs, st);
+    else if constexpr (z_tc_ok<T, R1, R2, 16>()) return z_green_r_tc<T, R1, R2, 16>(p, Bf, tz, nrhs, st);
+    else return false;
 }
 
 template <typename T> bool launch_z_green_r(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
@@ -589,10 +616,19 @@ template <typename T> const T *Lh_of(mot_problem *p);
 template <> const double *Lh_of<double>(mot_problem *p) { return (const double *)p->Lh_64.p; }
 template <> const float *Lh_of<float>(mot_problem *p) { return (const float *)p->Lh_32.p; }
 
-// y = Z0 x (or the residual epilogue) with the FFT in precision T.
+// true if the present-time xy passes run as one plane per block
+template <typename T> bool z0_planes_fit(const mot_problem *p) {
+    return xy_smem_bytes<T>(p->M0[0], p->M0[1], p->H0, p->N[1]) <= kSmemMax;
+}
+
+// y = Z0 x (or the residual epilogue) with the FFT in precision T.  The
+// input comes from src (a stored vector or one formed on the fly); the row
+// passes used when a plane does not fit in shared memory read `plain`, which
+// must then hold the same vector (nullptr: that case is refused).
 // wsA: nrhs*3*Nz*Ny*H0 complex, wsB: nrhs*3*Nz*M0y*H0 complex.
-template <typename TI, typename T, class Epi>
-mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *wsB, Epi epi, cudaStream_t st) {
+template <class Src, typename TI, typename T, class Epi>
+mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, void *wsA, void *wsB, Epi epi,
+                          cudaStream_t st) {
     const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
     const int H = p->H0, My = p->M0[1];
     AxisTw *tx = get_tw(p, p->M0[0]), *ty = get_tw(p, p->M0[1]), *tz = get_tw(p, p->M0[2]);
@@ -601,11 +637,11 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
     C *A = (C *)wsA, *Bf = (C *)wsB;
     const long nrows = (long)nrhs * 3 * Nz * Ny;
     const int planes = nrhs * 3 * Nz;
-    const size_t xy_smem = xy_smem_bytes<T>(p->M0[0], My, H, Ny);
-    const bool fused = xy_smem <= kSmemMax;
-    if (fused) MOT_TRY(launch_xy_forward<TI, T>(x, Bf, planes, Nx, Ny, H, tx, ty, st));
+    const bool fused = z0_planes_fit<T>(p);
+    if (fused) MOT_TRY((launch_xy_forward<Src, T>(src, Bf, planes, Nx, Ny, H, tx, ty, st)));
     else {
-        MOT_TRY(launch_x_forward<TI, T>(x, A, nrows, Nx, H, tx, st));
+        if (!plain) MOT_FAIL(MOT_EUNSUPPORTED, "row-pass product needs a stored input vector");
+        MOT_TRY(launch_x_forward<TI, T>(plain, A, nrows, Nx, H, tx, st));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
     }
     if (launch_z_green_r<T>(p, Bf, tz, nrhs, st)) {
@@ -628,6 +664,11 @@ mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *ws
         MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
     }
     return MOT_OK;
+}
+
+template <typename TI, typename T, class Epi>
+mot_status z0_product(mot_problem *p, const TI *x, int nrhs, void *wsA, void *wsB, Epi epi, cudaStream_t st) {
+    return z0_product_src<SrcPlain<TI>, TI, T, Epi>(p, SrcPlain<TI>{x}, x, nrhs, wsA, wsB, epi, st);
 }
 
 size_t z0_ws_bytes(const mot_problem *p, int nrhs, size_t csize, size_t *a, size_t *b) {
@@ -844,6 +885,7 @@ mot_status mot_ctx_create(int device, void *cuda_stream, mot_ctx **out) {
     MOT_CUDA_TRY(cudaSetDevice(device));
     mot_ctx *c = new mot_ctx();
     c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     // NULL is the CUDA legacy default stream (the stream PyTorch uses by default)
     c->stream = (cudaStream_t)cuda_stream;
     c->own_stream = false;
@@ -908,7 +950,7 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
     if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
-    if (o.graph != 0 && o.graph != 1) MOT_FAIL(MOT_EINVAL, "graph must be 0 or 1");
+    if (o.graph < 0 || o.graph > 2) MOT_FAIL(MOT_EINVAL, "graph must be 0, 1 or 2");
     MOT_CUDA_TRY(cudaSetDevice(ctx->device));
     mot_problem *p = new mot_problem();
     p->ctx = ctx;
@@ -1116,58 +1158,50 @@ template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restri
         w[i] = b[i] - a[i];
 }
 
-// loop control of a graph-captured solve: count the iteration and keep
-// looping while some right-hand side is active and the cap is not reached
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const TfqmrScal *sc, int B, int *ctl) {
-    __shared__ int active;
-    if (threadIdx.x == 0) active = 0;
-    __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x)
-        if (sc[b].conv == 0) active = 1;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int it = ctl[0] + 1;
-        ctl[0] = it;
-        cudaGraphSetConditional(h, (active && it < ctl[1]) ? 1u : 0u);
-    }
-}
-
-// one TFQMR iteration (two half steps, two Z0 products) on stream st
-template <typename V> mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st) {
+// Z0 y1 with y1 = w + beta y2 formed by the forward plane pass (one vector
+// pass fewer); where the planes do not fit, y1 is formed first
+template <typename V> mot_status mvp_y1(mot_run *r, cudaStream_t st) {
     mot_problem *p = r->p;
-    const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     KrylovView<V> k = kview<V>(r);
-    dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    if (!z0_planes_fit<V>(p)) {
+        count_launch();
+        k_tfqmr_y1<V><<<dim3(grid_for(L), r->B), 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
+        MOT_CHECK_LAUNCH();
+        return mvp<V>(r, k.v[kY1], k.v[kAY1], st);
+    }
+    SrcY1<V> src = {k.v[kY1], k.v[kW], k.v[kY2], k.sc, L};
+    EpiZ0<V, V> e = {k.v[kY1], k.v[kAY1], eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0]};
+    return z0_product_src<SrcY1<V>, V, V>(p, src, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, e, st);
+}
+
+// one TFQMR iteration (two half steps, two Z0 products) on stream st, ending
+// with the next alpha and the loop test (graph handle h if use_h, else ctl[2])
+template <typename V>
+mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
+    mot_problem *p = r->p;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    KrylovView<V> k = kview<V>(r);
+    unsigned *ctr = (unsigned *)r->ctr.p;
+    dim3 gr(kRedBlocks, r->B);
     count_launch();
-    k_tfqmr_alpha<<<B, 32, 0, st>>>(k.sc, k.p3);
-    count_launch();
-    k_tfqmr_y2<V><<<gv, 256, 0, st>>>(k.v[kY2], k.v[kY1], k.v[kV], k.sc, L);
-    count_launch();
-    k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY1], k.v[kAY1], k.v[kRS], k.sc, L,
-                                                     k.p1, nullptr);
-    count_launch();
-    k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
+    k_tfqmr_half_a<V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kY1], k.v[kAY1], k.v[kV], k.sc,
+                                                   L, k.p1, ctr);
     MOT_CHECK_LAUNCH();
     MOT_TRY(mvp<V>(r, k.v[kY2], k.v[kAY2], st));
     count_launch();
-    k_tfqmr_half<V, V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L,
-                                                     k.p1, k.p2);
-    count_launch();
-    k_tfqmr_half_fin<<<B, 32, 0, st>>>(k.sc, k.p1);
-    count_launch();
-    k_tfqmr_beta<<<B, 32, 0, st>>>(k.sc, k.p2);
-    count_launch();
-    k_tfqmr_y1<V><<<gv, 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
+    k_tfqmr_half_b<V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L, k.p1,
+                                                   k.p2, ctr + 1);
     MOT_CHECK_LAUNCH();
-    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
+    MOT_TRY(mvp_y1<V>(r, st));
     count_launch();
-    k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3);
+    k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3, ctr + 2,
+                                              (int *)r->ctl.p, h, use_h);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
 
-// build the graph: while (cond) { tfqmr_body; k_loop_cond }
+// build the graph: while (cond) { tfqmr_body }, the body setting cond
 template <typename V> mot_status build_loop_graph(mot_run *r, V *x, LoopGraph &G) {
     mot_problem *p = r->p;
     cudaGraph_t g = nullptr;
@@ -1185,9 +1219,7 @@ template <typename V> mot_status build_loop_graph(mot_run *r, V *x, LoopGraph &G
     const unsigned long long l0 = g_launches.load();
     p->capturing = true;
     MOT_CUDA_TRY(cudaStreamBeginCaptureToGraph(r->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    mot_status s = tfqmr_body<V>(r, x, r->cap);
-    count_launch();
-    k_loop_cond<<<1, 32, 0, r->cap>>>(h, (const TfqmrScal *)r->scal.p, r->B, (int *)r->ctl.p);
+    mot_status s = tfqmr_body<V>(r, x, r->cap, h, 1);
     cudaGraph_t out = nullptr;
     cudaError_t ce = cudaStreamEndCapture(r->cap, &out);
     p->capturing = false;
@@ -1212,27 +1244,24 @@ template <typename V> mot_status build_loop_graph(mot_run *r, V *x, LoopGraph &G
     return MOT_OK;
 }
 
-// TFQMR on Z0 y = rhs for the batch; x holds x0 on entry (x0 = 0 if zero_x0)
-// and the solution on exit.  The iteration loop runs as one graph launch.
-// iters_out: iterations (max over the batch); mvps_out: Z0 products applied.
+// start of a solve on st: r0 = rhs - Z0 x0 into w (x0 = 0 if zero_x0), y1 = r* =
+// w, d = 0, tau and rho, x = 0 where rhs = 0, v = Z0 y1 and the first alpha.
+// *mvps: products applied.
 template <typename V>
-mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
-                 bool *conv_out, int *mvps_out) {
+mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, cudaStream_t st, int *mvps) {
     mot_problem *p = r->p;
-    cudaStream_t st = p->ctx->stream;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     const long n = L * B;
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
-    int mvps = 0;
-    // r0 = rhs - A x0  (into w)
+    *mvps = 1;
     if (zero_x0) {
         MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
         MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
     } else {
         MOT_TRY(mvp<V>(r, x, k.v[kAY1], st));
-        ++mvps;
+        *mvps = 2;
         count_launch();
         k_sub<V><<<grid_for(n), 256, 0, st>>>(k.v[kW], rhs, k.v[kAY1], n);
         MOT_CHECK_LAUNCH();
@@ -1252,18 +1281,47 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     k_tfqmr_zero_done<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B);
     MOT_CHECK_LAUNCH();
     MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
-    ++mvps;
     MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kV], k.v[kAY1], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
     count_launch();
     k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kRS], k.v[kV], L, k.p3);
+    count_launch();
+    k_tfqmr_alpha<<<B, 32, 0, st>>>(k.sc, k.p3);
     MOT_CHECK_LAUNCH();
-    // the iteration loop: one graph launch
-    LoopGraph &G = sizeof(V) == 8 ? r->loop64 : r->loop32;
-    if (G.exec && G.x != (void *)x) MOT_FAIL(MOT_EINVAL, "solve graph bound to another vector");
-    if (!G.exec) MOT_TRY(build_loop_graph<V>(r, x, G));
+    return MOT_OK;
+}
+
+// TFQMR on Z0 y = rhs for the batch; x holds x0 on entry (x0 = 0 if zero_x0)
+// and the solution on exit.  The iteration loop runs as one graph launch
+// (graph option 0) or host-driven (graph option 2).
+// iters_out: iterations (max over the batch); mvps_out: Z0 products applied.
+template <typename V>
+mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
+                 bool *conv_out, int *mvps_out) {
+    mot_problem *p = r->p;
+    cudaStream_t st = p->ctx->stream;
+    const int B = r->B;
+    const long L = 3L * p->N[0] * p->N[1] * p->N[2];
+    KrylovView<V> k = kview<V>(r);
+    dim3 gv(grid_for(L), B);
+    int mvps = 0;
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &mvps));
     int ctl_h[2] = {0, maxit};
     MOT_CUDA_TRY(cudaMemcpyAsync(r->ctl.p, ctl_h, sizeof(ctl_h), cudaMemcpyHostToDevice, st));
-    MOT_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+    if (p->opt.graph == 2) {
+        // no graphs: the same body, its loop test read by the host
+        int ctl_now[3] = {0, maxit, 1};
+        while (ctl_now[2]) {
+            MOT_TRY(tfqmr_body<V>(r, x, st, cudaGraphConditionalHandle{}, 0));
+            MOT_CUDA_TRY(cudaMemcpyAsync(ctl_now, r->ctl.p, sizeof(ctl_now), cudaMemcpyDeviceToHost, st));
+            MOT_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+    } else {
+        // the iteration loop: one graph launch
+        LoopGraph &G = sizeof(V) == 8 ? r->loop64 : r->loop32;
+        if (G.exec && G.x != (void *)x) MOT_FAIL(MOT_EINVAL, "solve graph bound to another vector");
+        if (!G.exec) MOT_TRY(build_loop_graph<V>(r, x, G));
+        MOT_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+    }
     count_launch();
     k_tfqmr_flush<V, V><<<gv, 256, 0, st>>>(x, k.v[kD], k.sc, L, 1);
     count_launch();
@@ -1273,7 +1331,10 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), k.sc, sizeof(TfqmrScal) * B, cudaMemcpyDeviceToHost, st));
     MOT_CUDA_TRY(cudaMemcpyAsync(ctl_h, r->ctl.p, sizeof(ctl_h), cudaMemcpyDeviceToHost, st));
     MOT_CUDA_TRY(cudaStreamSynchronize(st));
-    g_launches.fetch_add((unsigned long long)G.body_kernels * ctl_h[0]);
+    if (p->opt.graph != 2) {
+        const LoopGraph &G = sizeof(V) == 8 ? r->loop64 : r->loop32;
+        g_launches.fetch_add((unsigned long long)G.body_kernels * ctl_h[0]);
+    }
     mvps += 2 * ctl_h[0];
     int mx = 0;
     bool conv = true;
@@ -1304,7 +1365,8 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
     C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
     const long nrows = (long)r->B * 3 * Nz * Ny;
     if (xy_smem_bytes<T>(p->Mh[0], My, H, Ny) <= kSmemMax) {
-        MOT_TRY((launch_xy_forward<double, T>((const double *)r->J.p, Bf, r->B * 3 * Nz, Nx, Ny, H, tx, ty, st)));
+        MOT_TRY((launch_xy_forward<SrcPlain<double>, T>(SrcPlain<double>{(const double *)r->J.p}, Bf, r->B * 3 * Nz, Nx,
+                                                         Ny, H, tx, ty, st)));
     } else {
         MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
@@ -1440,8 +1502,10 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             for (int b = 0; b < r->B; ++b)
                 if (rn[b] > tol * bn[b]) done = false;
             if (done || sweeps == p->opt.max_refine) break;
+            // r->dots holds the squared residual norms (norms above)
+            const dim3 gs(grid_for(L), r->B);
             count_launch();
-            k_convert<float, double><<<grid_for(n), 256, 0, st>>>(r32, (const double *)r->r.p, n);
+            k_convert_scaled<<<gs, 256, 0, st>>>(r32, (const double *)r->r.p, (const double *)r->dots.p, L);
             MOT_CHECK_LAUNCH();
             int it;
             bool c;
@@ -1450,7 +1514,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             mvps += nm;
             iters += it;
             count_launch();
-            k_add_into<double, float><<<grid_for(n), 256, 0, st>>>((double *)r->J.p, c32, n);
+            k_add_scaled<<<gs, 256, 0, st>>>((double *)r->J.p, c32, (const double *)r->dots.p, L);
             MOT_CHECK_LAUNCH();
         }
         conv = true;
@@ -1656,7 +1720,7 @@ mot_status while_insert(cudaStream_t st, cudaStream_t bst, const WhileNode &w, F
     return MOT_OK;
 }
 
-// TFQMR solve captured on st (init kernels, WHILE node with the iteration
+// TFQMR solve captured on st (start kernels, WHILE node with the iteration
 // body captured on bst, flush), solve statistics into the step record
 template <typename V>
 mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, cudaStream_t st,
@@ -1664,49 +1728,17 @@ mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double to
     mot_problem *p = r->p;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
-    const long n = L * B;
     KrylovView<V> k = kview<V>(r);
-    dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
+    dim3 gv(grid_for(L), B);
     int init_mvps = 1;
-    if (zero_x0) {
-        MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
-        MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
-    } else {
-        MOT_TRY(mvp<V>(r, x, k.v[kAY1], st));
-        init_mvps = 2;
-        count_launch();
-        k_sub<V><<<grid_for(n), 256, 0, st>>>(k.v[kW], rhs, k.v[kAY1], n);
-        MOT_CHECK_LAUNCH();
-    }
-    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kY1], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
-    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kRS], k.v[kW], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
-    MOT_CUDA_TRY(cudaMemsetAsync(k.v[kD], 0, sizeof(V) * n, st));
-    count_launch();
-    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kW], k.v[kW], L, k.p1);
-    count_launch();
-    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(rhs, rhs, L, k.p2);
-    count_launch();
-    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol);
-    count_launch();
-    k_tfqmr_zero_rhs<V><<<gv, 256, 0, st>>>(x, k.sc, L);
-    count_launch();
-    k_tfqmr_zero_done<<<(B + 255) / 256, 256, 0, st>>>(k.sc, B);
-    MOT_CHECK_LAUNCH();
-    MOT_TRY(mvp<V>(r, k.v[kY1], k.v[kAY1], st));
-    MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kV], k.v[kAY1], sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
-    count_launch();
-    k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(k.v[kRS], k.v[kV], L, k.p3);
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &init_mvps));
     WhileNode w;
     MOT_TRY(while_handle(st, w, 1));
     count_launch();
     k_cond_set<<<1, 32, 0, st>>>(w.h, (int *)r->ctl.p, maxit);
     MOT_CHECK_LAUNCH();
     MOT_TRY(while_insert(st, bst, w, [&](cudaStream_t cs) -> mot_status {
-        MOT_TRY(tfqmr_body<V>(r, x, cs));
-        count_launch();
-        k_loop_cond<<<1, 32, 0, cs>>>(w.h, (const TfqmrScal *)r->scal.p, r->B, (int *)r->ctl.p);
-        MOT_CHECK_LAUNCH();
-        return MOT_OK;
+        return tfqmr_body<V>(r, x, cs, w.h, 1);
     }, &r->k_inner));
     count_launch();
     k_tfqmr_flush<V, V><<<gv, 256, 0, st>>>(x, k.v[kD], k.sc, L, 1);
@@ -1772,12 +1804,14 @@ mot_status build_step_graph(mot_run *r) {
                                             p->opt.max_refine, sd, 0);
             MOT_CHECK_LAUNCH();
             MOT_TRY(while_insert(st, r->cap2, wo, [&](cudaStream_t cs) -> mot_status {
+                // r->r2 holds the squared residual norms (dev_norms2 before the test)
+                const dim3 gs(grid_for(L), r->B);
                 count_launch();
-                k_convert<float, double><<<grid_for(n), 256, 0, cs>>>(r32, (const double *)r->r.p, n);
+                k_convert_scaled<<<gs, 256, 0, cs>>>(r32, (const double *)r->r.p, (const double *)r->r2.p, L);
                 MOT_CHECK_LAUNCH();
                 MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0));
                 count_launch();
-                k_add_into<double, float><<<grid_for(n), 256, 0, cs>>>((double *)r->J.p, c32, n);
+                k_add_scaled<<<gs, 256, 0, cs>>>((double *)r->J.p, c32, (const double *)r->r2.p, L);
                 MOT_CHECK_LAUNCH();
                 MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, cs)));
                 MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, cs));
@@ -1889,7 +1923,9 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->part2, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->part3, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->dots, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
-    if ((s = dalloc(r->ctl, sizeof(int) * 2)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->ctl, sizeof(int) * 4)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->ctr, sizeof(unsigned) * 4)) != MOT_OK) return fail(s);
+    if (cudaMemset(r->ctr.p, 0, sizeof(unsigned) * 4) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamCreateWithFlags(&r->cap2, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamCreateWithFlags(&r->cap3, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
@@ -1924,8 +1960,8 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     mot_status result = MOT_OK;
     // graph mode (default): after one eager step (which sets every kernel's
     // attributes), each step is one graph launch with its control on the
-    // device; MOTJVIE_EAGER=1 keeps host-driven steps
-    const bool eager_env = r->p->opt.graph == 0;
+    // device; graph = 0 or 2 keeps host-driven steps
+    const bool eager_env = r->p->opt.graph != 1;
     if (!eager_env && r->n >= 1 && nsteps > 0) {
         cudaStream_t st = r->p->ctx->stream;
         if (!r->step_exec) MOT_TRY(build_step_graph(r));
@@ -1936,28 +1972,33 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
         while (done < nsteps) {
             const int chunk = std::min(nsteps - done, r->sstats_cap);
             MOT_CUDA_TRY(cudaMemsetAsync((char *)r->sdev.p + offsetof(StepDev, nstat), 0, sizeof(int), st));
+            // per-step events are read once the chunk is done: no host wait between steps
+            while (stats && (int)r->sev.size() < 2 * chunk) {
+                cudaEvent_t e;
+                MOT_CUDA_TRY(cudaEventCreate(&e));
+                r->sev.push_back(e);
+            }
             for (int i = 0; i < chunk; ++i) {
                 const int sidx = done + i;
-                if (stats) MOT_CUDA_TRY(cudaEventRecord(r->ev[0], st));
+                if (stats) MOT_CUDA_TRY(cudaEventRecord(r->sev[2 * i], st));
                 MOT_CUDA_TRY(cudaGraphLaunch(r->step_exec, st));
                 r->n += 1;
+                if (stats) MOT_CUDA_TRY(cudaEventRecord(r->sev[2 * i + 1], st));
                 if (J_out)
                     MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)sidx * n, r->J.p, sizeof(double) * n,
                                                  cudaMemcpyDeviceToHost, st));
-                if (stats) {
-                    MOT_CUDA_TRY(cudaEventRecord(r->ev[3], st));
-                    MOT_CUDA_TRY(cudaEventSynchronize(r->ev[3]));
-                    mot_step_stats &S = stats[sidx];
-                    memset(&S, 0, sizeof(S));
-                    if (cudaEventElapsedTime(&S.ms_solve, r->ev[0], r->ev[3]) != cudaSuccess) {
-                        S.ms_solve = 0.f;
-                        cudaGetLastError();
-                    }
-                }
             }
             std::vector<StepStatDev> hs(chunk);
             MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), r->sstats.p, sizeof(StepStatDev) * chunk, cudaMemcpyDeviceToHost, st));
             MOT_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int i = 0; stats && i < chunk; ++i) {
+                mot_step_stats &S = stats[done + i];
+                memset(&S, 0, sizeof(S));
+                if (cudaEventElapsedTime(&S.ms_solve, r->sev[2 * i], r->sev[2 * i + 1]) != cudaSuccess) {
+                    S.ms_solve = 0.f;
+                    cudaGetLastError();
+                }
+            }
             for (int i = 0; i < chunk; ++i) {
                 // kernels the step graph executed: fixed part, each refinement
                 // sweep's body, each TFQMR loop iteration
@@ -2037,11 +2078,13 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->dots);
     for (int i = 0; i < 4; ++i)
         if (r->ev[i]) cudaEventDestroy(r->ev[i]);
+    for (cudaEvent_t e : r->sev) cudaEventDestroy(e);
     for (LoopGraph *G : {&r->loop64, &r->loop32}) {
         if (G->exec) cudaGraphExecDestroy(G->exec);
         if (G->graph) cudaGraphDestroy(G->graph);
     }
     dfree(r->ctl);
+    dfree(r->ctr);
     if (r->step_exec) cudaGraphExecDestroy(r->step_exec);
     if (r->step_graph) cudaGraphDestroy(r->step_graph);
     dfree(r->sdev);

@@ -2,9 +2,10 @@
 // kernels, FP64 inner products, and the incident right-hand side (Eq. 7-8).
 //
 // Vectors are [B][L] (L = 3 * Nx * Ny * Nz); every right-hand side b keeps
-// its own scalars in TfqmrScal.  Inner products and norms are accumulated in
-// FP64 whatever the vector type, by a deterministic two-level reduction:
-// fixed block partials, then one warp per right-hand side in fixed order.
+// its own scalars in TfqmrScal.  Inner products and norms use a deterministic
+// two-level reduction: each thread sums its strided elements in the vector
+// precision, block sums and the final sum (one warp per right-hand side, fixed
+// order) are FP64.
 #pragma once
 
 #include <math.h>
@@ -26,6 +27,26 @@ struct TfqmrScal {
 
 constexpr int kRedBlocks = 296;  // 2 x 148 SMs
 constexpr int kRedThreads = 256;
+
+// per-thread accumulator of the element sums: the vector precision (a thread
+// sums about L / (kRedBlocks * kRedThreads) terms), FP64 from the block sums on
+template <typename V> struct AccOf { using type = double; };
+template <> struct AccOf<float> { using type = float; };
+
+// 16-byte packs of vector elements (4 floats, 2 doubles): the fused kernels
+// move whole packs when the per-right-hand-side length L is a multiple of the
+// pack width (then every right-hand side's slice starts 16-byte aligned) and
+// fall back to single elements otherwise
+template <typename V> struct PackW { static constexpr int W = 16 / sizeof(V); };
+template <typename V> __device__ __forceinline__ void ld_pack(V (&r)[PackW<V>::W], const V *p) {
+    const uint4 u = *reinterpret_cast<const uint4 *>(p);
+    memcpy(r, &u, 16);
+}
+template <typename V> __device__ __forceinline__ void st_pack(V *p, const V (&r)[PackW<V>::W]) {
+    uint4 u;
+    memcpy(&u, r, 16);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -54,11 +75,12 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const TA *__restrict__
     const int b = blockIdx.y;
     const TA *pa = a + (long)b * L;
     const TC *pc = c + (long)b * L;
-    double s = 0.0;
+    using A = typename AccOf<TA>::type;
+    A s = A(0);
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
-        s += (double)pa[i] * (double)pc[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = s;
+        s += (A)pa[i] * (A)pc[i];
+    const double bs = block_sum((double)s, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
 }
 
 __device__ __forceinline__ double reduce_parts(const double *part, int b) {
@@ -118,85 +140,195 @@ __global__ void k_tfqmr_alpha(TfqmrScal *sc, const double *part) {
     }
 }
 
-// y2 = y1 - alpha v
-template <typename V>
-__global__ void k_tfqmr_y2(V *__restrict__ y2, const V *__restrict__ y1, const V *__restrict__ v,
-                           const TfqmrScal *__restrict__ sc, long L) {
-    const int b = blockIdx.y;
-    if (sc[b].conv) return;
-    const V al = (V)sc[b].alpha;
-    const long o = (long)b * L;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
-        y2[o + i] = y1[o + i] - al * v[o + i];
+// Fused iteration kernels.  Each reduction kernel ends with its scalar update:
+// the block that finishes last (counted with an atomic ticket after a memory
+// fence) reduces every right-hand side's partials in fixed order, so the
+// result does not depend on which block finished last.
+// true in every thread of the block that finished last; ctr is left at 0 by
+// that block (kernel end), ready for the next launch
+__device__ __forceinline__ bool last_block(unsigned *ctr, unsigned total) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ctr, 1u) == total - 1u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last != 0;
 }
 
-// half step: x += eta_prev d (pending); w -= alpha Ay; d = y + (theta^2 eta/alpha) d;
-// partials of ||w||^2 and (optionally) (r*, w).  grid (kRedBlocks, B)
-template <typename V, typename VX>
-__global__ void __launch_bounds__(kRedThreads) k_tfqmr_half(VX *__restrict__ x, V *__restrict__ w, V *__restrict__ d,
-                                                            const V *__restrict__ y, const V *__restrict__ Ay,
-                                                            const V *__restrict__ rs, const TfqmrScal *__restrict__ sc,
-                                                            long L, double *__restrict__ part_w2,
-                                                            double *__restrict__ part_rw) {
-    __shared__ double sh[32];
-    const int b = blockIdx.y;
-    const TfqmrScal s = sc[b];
-    double w2 = 0.0, rw = 0.0;
-    if (!s.conv) {
-        const V al = (V)s.alpha;
-        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
-        const VX ep = (VX)s.eta_prev;
-        const long o = (long)b * L;
-        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
-            V dold = d[o + i];
-            if (s.pending) x[o + i] += ep * (VX)dold;
-            V wn = w[o + i] - al * Ay[o + i];
-            w[o + i] = wn;
-            d[o + i] = y[o + i] + coef * dold;
-            w2 += (double)wn * (double)wn;
-            if (part_rw) rw += (double)rs[o + i] * (double)wn;
-        }
-    }
-    w2 = block_sum(w2, sh);
-    if (part_rw) rw = block_sum(rw, sh);
-    if (threadIdx.x == 0) {
-        part_w2[b * kRedBlocks + blockIdx.x] = w2;
-        if (part_rw) part_rw[b * kRedBlocks + blockIdx.x] = rw;
-    }
+__device__ __forceinline__ double reduce_parts_lane(const double *part, int b, int lane) {
+    double s = 0.0;
+    for (int i = lane; i < kRedBlocks; i += 32) s += __ldcg(part + b * kRedBlocks + i);
+    return warp_sum(s);
 }
 
 // theta = ||w||/tau, c = 1/sqrt(1+theta^2), tau = tau theta c, eta = c^2 alpha;
-// converged once tau sqrt(m+1) <= tol ||b||.  grid B, block 32
-__global__ void k_tfqmr_half_fin(TfqmrScal *sc, const double *part_w2) {
-    const int b = blockIdx.x;
-    double w2 = reduce_parts(part_w2, b);
-    if (threadIdx.x == 0 && !sc[b].conv) {
-        TfqmrScal s = sc[b];
-        double th = sqrt(w2) / s.tau;
-        double c = 1.0 / sqrt(1.0 + th * th);
-        s.tau = s.tau * th * c;
-        s.theta = th;
-        s.eta = c * c * s.alpha;
-        s.eta_prev = s.eta;
-        s.pending = 1;
-        s.m += 1;
-        if (s.tau * sqrt((double)s.m + 1.0) <= s.tolabs) s.conv = 2;  // 2: pending update still due
-        sc[b] = s;
-    }
+// converged once tau sqrt(m+1) <= tol ||b|| (conv 2: pending update still due)
+__device__ __forceinline__ void half_scalars(TfqmrScal &s, double w2) {
+    double th = sqrt(w2) / s.tau;
+    double c = 1.0 / sqrt(1.0 + th * th);
+    s.tau = s.tau * th * c;
+    s.theta = th;
+    s.eta = c * c * s.alpha;
+    s.eta_prev = s.eta;
+    s.pending = 1;
+    s.m += 1;
+    if (s.tau * sqrt((double)s.m + 1.0) <= s.tolabs) s.conv = 2;
 }
 
-// rho_new = (r*, w): beta = rho_new / rho.  grid B, block 32
-__global__ void k_tfqmr_beta(TfqmrScal *sc, const double *part_rw) {
-    const int b = blockIdx.x;
-    double rn = reduce_parts(part_rw, b);
-    if (threadIdx.x == 0 && !sc[b].conv) {
-        if (sc[b].rho == 0.0) { sc[b].conv = 2; return; }
-        sc[b].beta = rn / sc[b].rho;
-        sc[b].rho = rn;
+// first half step of an iteration, on (y1, Ay1):
+//   x += eta_prev d (pending); w -= alpha Ay1; d = y1 + (theta^2 eta/alpha) d;
+//   y2 = y1 - alpha v;  ||w||^2  ->  theta, tau, eta.   grid (kRedBlocks, B)
+template <typename V>
+__global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_a(V *__restrict__ x, V *__restrict__ w,
+                                                              V *__restrict__ d, V *__restrict__ y2,
+                                                              const V *__restrict__ y1, const V *__restrict__ Ay1,
+                                                              const V *__restrict__ v, TfqmrScal *__restrict__ sc,
+                                                              long L, double *__restrict__ part, unsigned *ctr) {
+    using A = typename AccOf<V>::type;
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const TfqmrScal s = sc[b];
+    A w2 = A(0);
+    if (!s.conv) {
+        const V al = (V)s.alpha;
+        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
+        const V ep = (V)s.eta_prev;
+        const long o = (long)b * L;
+        constexpr int W = PackW<V>::W;
+        const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+        const long np = L % W == 0 ? L / W : 0;
+#pragma unroll 2
+        for (long j = t0; j < np; j += ts) {
+            const long i = o + j * W;
+            V dd[W], yy[W], ww[W], aa[W], vv[W], xx[W];
+            ld_pack(dd, d + i);
+            ld_pack(yy, y1 + i);
+            ld_pack(ww, w + i);
+            ld_pack(aa, Ay1 + i);
+            ld_pack(vv, v + i);
+            if (s.pending) ld_pack(xx, x + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (s.pending) xx[k] += ep * dd[k];
+                ww[k] -= al * aa[k];
+                w2 += ww[k] * ww[k];
+                dd[k] = yy[k] + coef * dd[k];
+                yy[k] -= al * vv[k];
+            }
+            if (s.pending) st_pack(x + i, xx);
+            st_pack(w + i, ww);
+            st_pack(d + i, dd);
+            st_pack(y2 + i, yy);
+        }
+        for (long i = np * W + t0; i < L; i += ts) {
+            const V dold = d[o + i], yv = y1[o + i];
+            if (s.pending) x[o + i] += ep * dold;
+            const V wn = w[o + i] - al * Ay1[o + i];
+            w[o + i] = wn;
+            d[o + i] = yv + coef * dold;
+            y2[o + i] = yv - al * v[o + i];
+            w2 += wn * wn;
+        }
     }
+    const double bs = block_sum((double)w2, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
+    if (!last_block(ctr, gridDim.x * gridDim.y)) return;
+    const int lane = threadIdx.x & 31;
+    for (int bb = threadIdx.x >> 5; bb < (int)gridDim.y; bb += blockDim.x >> 5) {
+        const double t = reduce_parts_lane(part, bb, lane);
+        if (lane == 0 && !sc[bb].conv) {
+            TfqmrScal u = sc[bb];
+            half_scalars(u, t);
+            sc[bb] = u;
+        }
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
 }
 
-// y1 = w + beta y2
+// second half step, on (y2, Ay2): as above without y2, plus rho_new = (r*, w)
+// -> beta = rho_new / rho (breakdown at rho = 0).   grid (kRedBlocks, B)
+template <typename V>
+__global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x, V *__restrict__ w,
+                                                              V *__restrict__ d, const V *__restrict__ y2,
+                                                              const V *__restrict__ Ay2, const V *__restrict__ rs,
+                                                              TfqmrScal *__restrict__ sc, long L,
+                                                              double *__restrict__ part_w2,
+                                                              double *__restrict__ part_rw, unsigned *ctr) {
+    using A = typename AccOf<V>::type;
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const TfqmrScal s = sc[b];
+    A w2 = A(0), rw = A(0);
+    if (!s.conv) {
+        const V al = (V)s.alpha;
+        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
+        const V ep = (V)s.eta_prev;
+        const long o = (long)b * L;
+        constexpr int W = PackW<V>::W;
+        const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+        const long np = L % W == 0 ? L / W : 0;
+#pragma unroll 2
+        for (long j = t0; j < np; j += ts) {
+            const long i = o + j * W;
+            V dd[W], yy[W], ww[W], aa[W], rr[W], xx[W];
+            ld_pack(dd, d + i);
+            ld_pack(yy, y2 + i);
+            ld_pack(ww, w + i);
+            ld_pack(aa, Ay2 + i);
+            ld_pack(rr, rs + i);
+            if (s.pending) ld_pack(xx, x + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (s.pending) xx[k] += ep * dd[k];
+                ww[k] -= al * aa[k];
+                w2 += ww[k] * ww[k];
+                rw += rr[k] * ww[k];
+                dd[k] = yy[k] + coef * dd[k];
+            }
+            if (s.pending) st_pack(x + i, xx);
+            st_pack(w + i, ww);
+            st_pack(d + i, dd);
+        }
+        for (long i = np * W + t0; i < L; i += ts) {
+            const V dold = d[o + i];
+            if (s.pending) x[o + i] += ep * dold;
+            const V wn = w[o + i] - al * Ay2[o + i];
+            w[o + i] = wn;
+            d[o + i] = y2[o + i] + coef * dold;
+            w2 += wn * wn;
+            rw += rs[o + i] * wn;
+        }
+    }
+    const double bw = block_sum((double)w2, sh);
+    const double br = block_sum((double)rw, sh);
+    if (threadIdx.x == 0) {
+        part_w2[b * kRedBlocks + blockIdx.x] = bw;
+        part_rw[b * kRedBlocks + blockIdx.x] = br;
+    }
+    if (!last_block(ctr, gridDim.x * gridDim.y)) return;
+    const int lane = threadIdx.x & 31;
+    for (int bb = threadIdx.x >> 5; bb < (int)gridDim.y; bb += blockDim.x >> 5) {
+        const double t = reduce_parts_lane(part_w2, bb, lane);
+        const double rn = reduce_parts_lane(part_rw, bb, lane);
+        if (lane == 0 && !sc[bb].conv) {
+            TfqmrScal u = sc[bb];
+            half_scalars(u, t);
+            if (!u.conv) {
+                if (u.rho == 0.0) u.conv = 2;
+                else {
+                    u.beta = rn / u.rho;
+                    u.rho = rn;
+                }
+            }
+            sc[bb] = u;
+        }
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+// y1 = w + beta y2 (used where the product cannot form y1 on the fly)
 template <typename V>
 __global__ void k_tfqmr_y1(V *__restrict__ y1, const V *__restrict__ w, const V *__restrict__ y2,
                            const TfqmrScal *__restrict__ sc, long L) {
@@ -208,26 +340,100 @@ __global__ void k_tfqmr_y1(V *__restrict__ y1, const V *__restrict__ w, const V 
         y1[o + i] = w[o + i] + be * y2[o + i];
 }
 
-// v = Ay1 + beta (Ay2 + beta v), with the partials of (r*, v).  grid (kRedBlocks, B)
+// y1 = w + beta y2 formed while a forward plane kernel reads it, and stored
+// (each element is loaded once); unchanged for right-hand sides that stopped
+template <typename V> struct SrcY1 {
+    V *y1;
+    const V *w, *y2;
+    const TfqmrScal *sc;
+    long L;  // vector length of one right-hand side (a multiple of the plane size)
+    struct Plane {
+        V *y1;
+        const V *w, *y2;
+        V beta;
+        int skip;
+        __device__ __forceinline__ V load(long o) const {
+            if (skip) return y1[o];
+            const V v = w[o] + beta * y2[o];
+            y1[o] = v;
+            return v;
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, long plane_size) const {
+        const long off = plane * plane_size;
+        const int b = (int)(off / L);
+        return Plane{y1 + off, w + off, y2 + off, (V)sc[b].beta, sc[b].conv != 0};
+    }
+};
+
+// end of an iteration: v = Ay1 + beta (Ay2 + beta v), sigma = (r*, v) ->
+// alpha = rho / sigma for the next iteration (breakdown at sigma = 0), then the
+// loop test: count the iteration in ctl[0] and continue while some right-hand
+// side is active and ctl[0] < ctl[1] -- through the graph's conditional handle
+// (use_h) or into ctl[2] for a host-driven loop.   grid (kRedBlocks, B)
 template <typename V>
 __global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, const V *__restrict__ Ay1,
                                                          const V *__restrict__ Ay2, const V *__restrict__ rs,
-                                                         const TfqmrScal *__restrict__ sc, long L,
-                                                         double *__restrict__ part) {
+                                                         TfqmrScal *__restrict__ sc, long L, double *__restrict__ part,
+                                                         unsigned *ctr, int *ctl, cudaGraphConditionalHandle h,
+                                                         int use_h) {
+    using A = typename AccOf<V>::type;
     __shared__ double sh[32];
+    __shared__ int active;
     const int b = blockIdx.y;
-    double acc = 0.0;
+    A acc = A(0);
     if (!sc[b].conv) {
         const V be = (V)sc[b].beta;
         const long o = (long)b * L;
-        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
-            V vn = Ay1[o + i] + be * (Ay2[o + i] + be * v[o + i]);
+        constexpr int W = PackW<V>::W;
+        const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+        const long np = L % W == 0 ? L / W : 0;
+#pragma unroll 2
+        for (long j = t0; j < np; j += ts) {
+            const long i = o + j * W;
+            V a1[W], a2[W], vv[W], rr[W];
+            ld_pack(a1, Ay1 + i);
+            ld_pack(a2, Ay2 + i);
+            ld_pack(vv, v + i);
+            ld_pack(rr, rs + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                vv[k] = a1[k] + be * (a2[k] + be * vv[k]);
+                acc += rr[k] * vv[k];
+            }
+            st_pack(v + i, vv);
+        }
+        for (long i = np * W + t0; i < L; i += ts) {
+            const V vn = Ay1[o + i] + be * (Ay2[o + i] + be * v[o + i]);
             v[o + i] = vn;
-            acc += (double)rs[o + i] * (double)vn;
+            acc += rs[o + i] * vn;
         }
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = acc;
+    const double bs = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
+    if (!last_block(ctr, gridDim.x * gridDim.y)) return;
+    if (threadIdx.x == 0) active = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int bb = threadIdx.x >> 5; bb < (int)gridDim.y; bb += blockDim.x >> 5) {
+        const double sigma = reduce_parts_lane(part, bb, lane);
+        if (lane == 0) {
+            if (!sc[bb].conv) {
+                if (sigma == 0.0) sc[bb].conv = 2;
+                else sc[bb].alpha = sc[bb].rho / sigma;
+            }
+            if (sc[bb].conv == 0) active = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int it = ctl[0] + 1;
+        ctl[0] = it;
+        const int cont = (active && it < ctl[1]) ? 1 : 0;
+        if (use_h) cudaGraphSetConditional(h, (unsigned)cont);
+        else ctl[2] = cont;
+        *ctr = 0u;
+    }
 }
 
 // apply the pending x += eta d of right-hand sides that converged (conv == 2)
@@ -259,18 +465,34 @@ __global__ void k_finish_dot(const double *part, double *out) {
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// ---- elementwise helpers ----
-template <typename TD, typename TS>
-__global__ void k_convert(TD *__restrict__ dst, const TS *__restrict__ src, long n) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        dst[i] = (TD)src[i];
+// ---- scaling of the FP32 correction solve ----
+// The residual handed to the FP32 solve is scaled per right-hand side by 2^-e
+// with 2^e ~ its 2-norm (exact: a power of two), so the FP32 vectors and their
+// squared sums stay near 1 whatever the units of the problem; the correction
+// is scaled back by 2^e when it is added to J.  n2 = squared norms ([B]).
+__device__ __forceinline__ int pow2_exponent(double n2) {
+    if (!(n2 > 0.0) || !isfinite(n2)) return 0;
+    return ilogb(n2) / 2;
 }
 
-template <typename TD, typename TS>
-__global__ void k_add_into(TD *__restrict__ dst, const TS *__restrict__ src, long n) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        dst[i] += (TD)src[i];
+__global__ void k_convert_scaled(float *__restrict__ dst, const double *__restrict__ src,
+                                 const double *__restrict__ n2, long L) {
+    const int b = blockIdx.y;
+    const int e = pow2_exponent(n2[b]);
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        dst[o + i] = (float)ldexp(src[o + i], -e);
 }
+
+__global__ void k_add_scaled(double *__restrict__ J, const float *__restrict__ c, const double *__restrict__ n2,
+                             long L) {
+    const int b = blockIdx.y;
+    const int e = pow2_exponent(n2[b]);
+    const long o = (long)b * L;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        J[o + i] += ldexp((double)c[o + i], e);
+}
+
 
 // ---------------------------------------------------------------------------
 // incident right-hand side (Eq. 7-8):

@@ -103,6 +103,20 @@ __global__ void __launch_bounds__(512) k_axis(const cplx<T> *__restrict__ in, cp
 }
 
 // ---------------------------------------------------------------------------
+// input of the plane kernels: bind(plane, plane_size) gives an accessor whose
+// load(o) returns element o of that plane.  SrcPlain reads a stored vector;
+// other sources form the vector while it is read (one load per element).
+// ---------------------------------------------------------------------------
+template <typename TI> struct SrcPlain {
+    const TI *x;
+    struct Plane {
+        const TI *p;
+        __device__ __forceinline__ TI load(long o) const { return p[o]; }
+    };
+    __device__ __forceinline__ Plane bind(long plane, long plane_size) const { return Plane{x + plane * plane_size}; }
+};
+
+// ---------------------------------------------------------------------------
 // fused xy passes over whole planes (used when a plane fits in shared memory):
 // forward: pad + R2C along x (row pairs) and FFT along y in one CTA per plane,
 //   in [P][Ny][Nx] real -> out [P][My][H] complex;
@@ -118,8 +132,8 @@ __host__ __device__ inline size_t xy_smem_bytes(int Mx, int My, int H, int Ny) {
     return (size_t)(Mx + My + 2 * My * H + 2 * ((Ny + 1) / 2) * Mx) * sizeof(cplx<T>);
 }
 
-template <typename TI, typename T>
-__global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
+template <class Src, typename T>
+__global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(Src x, cplx<T> *__restrict__ out, int Nx,
                                                     int Ny, int H, FftPlan px, FftPlan py,
                                                     const cplx<T> *__restrict__ twx_g,
                                                     const cplx<T> *__restrict__ twy_g) {
@@ -135,15 +149,15 @@ __global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(const TI *__rest
     load_twiddles(twx, twx_g, Mx);
     load_twiddles(twy, twy_g, My);
     const long plane = blockIdx.x;
-    const TI *src = x + plane * (long)Ny * Nx;
+    const auto src = x.bind(plane, (long)Ny * Nx);
     const FastDiv fNx = make_fastdiv((unsigned)Nx), fMx = make_fastdiv((unsigned)Mx), fH = make_fastdiv((unsigned)H);
     // rows y and y+1 -> one complex pencil; padded columns and a missing odd row are 0
     for (int i = threadIdx.x; i < np * Mx; i += blockDim.x) {
         int pr = (int)fdiv((unsigned)i, fMx), e = i - pr * Mx;
         T re = T(0), im = T(0);
         if (e < Nx) {
-            re = (T)src[(long)(2 * pr) * Nx + e];
-            if (2 * pr + 1 < Ny) im = (T)src[(long)(2 * pr + 1) * Nx + e];
+            re = (T)src.load((long)(2 * pr) * Nx + e);
+            if (2 * pr + 1 < Ny) im = (T)src.load((long)(2 * pr + 1) * Nx + e);
         }
         A[i] = cmake<C>(re, im);
     }
@@ -227,8 +241,8 @@ __host__ __device__ inline size_t xy_r_smem_bytes(int Ny) {
     return (2 * xy_r_buf<T, RX1, RX2, RY1, RY2>(Ny) + RX1 * RX2 + RY1 * RY2) * sizeof(cplx<T>);
 }
 
-template <typename TI, typename T, int RX1, int RX2, int RY1, int RY2>
-__global__ void __launch_bounds__(512) k_xy_forward_r(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
+template <class Src, typename T, int RX1, int RX2, int RY1, int RY2>
+__global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict__ out, int Nx,
                                                       int Ny, const cplx<T> *__restrict__ twx_g,
                                                       const cplx<T> *__restrict__ twy_g) {
     using C = cplx<T>;
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(const TI *__restrict__ x, 
     load_twiddles(twy, twy_g, My);
     __syncthreads();
     const long plane = blockIdx.x;
-    const TI *src = x + plane * (long)Ny * Nx;
+    const auto src = x.bind(plane, (long)Ny * Nx);
     // x stage A: pencil p = rows (2p, 2p+1) as re/im, thread t < RX2 loads e = t + RX2 m
     for (int task = threadIdx.x; task < np * RX2; task += blockDim.x) {
         const int p = task / RX2, t = task - p * RX2;
@@ -255,8 +269,8 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(const TI *__restrict__ x, 
             const int e = t + RX2 * m;
             T re = T(0), im = T(0);
             if (e < Nx) {
-                re = (T)src[(long)(2 * p) * Nx + e];
-                if (two) im = (T)src[(long)(2 * p + 1) * Nx + e];
+                re = (T)src.load((long)(2 * p) * Nx + e);
+                if (two) im = (T)src.load((long)(2 * p + 1) * Nx + e);
             }
             v[m] = cmake<C>(re, im);
         }
@@ -537,37 +551,74 @@ __global__ void __launch_bounds__(256) k_z_history(const cplx<T> *__restrict__ r
 }
 
 // ---------------------------------------------------------------------------
+// asynchronous global -> shared copy of one element (4 or 8 bytes), waited for
+// with cp_async_wait_all() before the data is read
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // present-time z pass specialised for a compile-time length M = R1 * R2.
 // Columns are consecutive positions col = ky*H + kx of the (ky, kx) plane, so a
-// tile of 32 columns is 32 contiguous complex values in every z row.
-// stage A  (thread = (t, c), t < R2): x[t + R2 m], m < R1, straight from HBM,
-//          R1-point DFT in registers, twiddle W_M^(t k1), to shared memory;
-// stage B  (task = (k1, c)): R2-point DFT over t -> X[k1 + R1 k2], 3x3 Green
-//          multiply, inverse R2-point DFT, twiddle W_M^(-t k1), to shared memory;
-// stage A' (thread = (t, c)): inverse R1-point DFT over k1, rows z < Nz to HBM.
-// grid = (ceil(My*H/32), B); block = 32*R2; smem = M + 3*32*(M+1) complex
+// tile of TC columns is TC contiguous complex values in every z row.  One
+// thread per (component q, offset t < R2, column c): block = 3*TC*R2.
+// slab     the tile's Lambda0 values, [6][Kz][TC] in shared memory, fetched
+//          with asynchronous copies issued first (they overlap stages A, B1);
+// stage A  thread (q, t, c): x_q[t + R2 m], m < R1, straight from HBM, R1-point
+//          DFT in registers, twiddle W_M^(t k1), to shared memory;
+// stage B  (task = (q, k1, c)): R2-point DFT over t -> X[k1 + R1 k2]; 3x3 Green
+//          multiply from the slab per (kz, c); inverse R2-point DFT, twiddle
+//          W_M^(-t k1);
+// stage A' thread (q, t, c): inverse R1-point DFT over k1, rows z < Nz to HBM.
+// grid = (ceil(My*H/TC), B); smem = (M + 3*TC*(M+1)) complex + 6*(M/2+1)*TC real
 // ---------------------------------------------------------------------------
-template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(32 * R2) k_z_green_r(cplx<T> *__restrict__ buf, const T *__restrict__ L,
-                                                       const cplx<T> *__restrict__ tw_g, int Nz, int My, int H,
-                                                       Octant oc) {
+template <typename T, int R1, int R2, int TC>
+__host__ __device__ constexpr size_t z_green_r_smem() {
+    return (size_t)(R1 * R2 + 3 * TC * (R1 * R2 + 1)) * sizeof(cplx<T>) + (size_t)6 * (R1 * R2 / 2 + 1) * TC * sizeof(T);
+}
+
+template <typename T, int R1, int R2, int TC>
+__global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__ buf, const T *__restrict__ L,
+                                                           const cplx<T> *__restrict__ tw_g, int Nz, int My, int H,
+                                                           Octant oc) {
     using C = cplx<T>;
-    constexpr int M = R1 * R2, TC = 32, RS = M + 1;  // padded row stride in shared memory
+    constexpr int M = R1 * R2, RS = M + 1, KZ = M / 2 + 1;  // RS: padded row stride in shared memory
+    constexpr int NT = 3 * TC * R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *S = tw + M;  // [q][c][RS]
-    load_twiddles(tw, tw_g, M);
+    C *S = tw + M;                                   // [q][c][RS]
+    T *sL = reinterpret_cast<T *>(S + 3 * TC * RS);  // [6][KZ][TC]
     const int ncols = My * H;
     const int col0 = blockIdx.x * TC;
     const long plane = ncols;                 // z stride
     const long comp = (long)Nz * plane;       // component stride
     C *base = buf + (long)blockIdx.y * 3 * comp;
-    const int c = threadIdx.x % TC, t = threadIdx.x / TC;
+    const int c = threadIdx.x % TC, qt = threadIdx.x / TC;  // qt = q*R2 + t
+    const int q = qt / R2, t = qt - q * R2;
     const bool live = col0 + c < ncols;
+    // ---- slab: column c, slab rows qt, qt + 3 R2, ... (row = component6 * KZ + fz)
+    const long cs = (long)oc.Kz * oc.Ky * oc.H;
+    if (live) {
+        const int col = col0 + c, ky = col / H, kx = col - ky * H;
+        const int fy = 2 * ky > My ? My - ky : ky;
+        const T *src = L + (long)fy * H + kx;
+        for (int r = qt; r < 6 * KZ; r += 3 * R2) {
+            const int comp6 = r / KZ, fz = r - comp6 * KZ;
+            cp_async_elem(sL + r * TC + c, src + comp6 * cs + (long)fz * oc.Ky * H);
+        }
+    }
+    load_twiddles(tw, tw_g, M);
     __syncthreads();
     // ---- stage A
-#pragma unroll 1
-    for (int q = 0; q < 3; ++q) {
+    {
         C v[R1];
 #pragma unroll
         for (int m = 0; m < R1; ++m) {
@@ -585,9 +636,9 @@ __global__ void __launch_bounds__(32 * R2) k_z_green_r(cplx<T> *__restrict__ buf
     }
     __syncthreads();
     // ---- stage B1: R2-point DFT of every (q, c, k1) row segment, in place
-    for (int task = threadIdx.x; task < 3 * R1 * TC; task += blockDim.x) {
-        const int q = task / (R1 * TC), rem = task - q * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
-        C *seg = S + (q * TC + cc) * RS + k1 * R2;
+    for (int task = threadIdx.x; task < 3 * R1 * TC; task += NT) {
+        const int qq = task / (R1 * TC), rem = task - qq * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
+        C *seg = S + (qq * TC + cc) * RS + k1 * R2;
         C u[R2];
 #pragma unroll
         for (int tt = 0; tt < R2; ++tt) u[tt] = seg[tt];
@@ -595,33 +646,32 @@ __global__ void __launch_bounds__(32 * R2) k_z_green_r(cplx<T> *__restrict__ buf
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) seg[k2] = u[k2];
     }
+    cp_async_wait_all();
     __syncthreads();
     // ---- stage B2: 3x3 Green multiply at every (kz, c); kz = k1 + R1 k2 sits at k1*R2 + k2
-    const long cs = (long)oc.Kz * oc.Ky * oc.H;
     const FastDiv fH = make_fastdiv((unsigned)H);
-    for (int task = threadIdx.x; task < M * TC; task += blockDim.x) {
+    for (int task = threadIdx.x; task < M * TC; task += NT) {
         const int pos = task / TC, cc = task - pos * TC;  // pos = k1*R2 + k2
         const int col = col0 + cc;
         if (col >= ncols) continue;
         const int k1 = pos / R2, k2 = pos - k1 * R2, kz = k1 + R1 * k2;
-        const int ky = (int)fdiv((unsigned)col, fH), kx = col - ky * H;
-        int fy, fz;
-        float sy, sz;
-        if (2 * ky > My) { fy = My - ky; sy = -1.f; } else { fy = ky; sy = 1.f; }
+        const int ky = (int)fdiv((unsigned)col, fH);
+        const float sy = 2 * ky > My ? -1.f : 1.f;
+        int fz;
+        float sz;
         if (2 * kz > M) { fz = M - kz; sz = -1.f; } else { fz = kz; sz = 1.f; }
-        const long idx = ((long)fz * oc.Ky + fy) * oc.H + kx;
         C in[3], out[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) in[q] = S[(q * TC + cc) * RS + pos];
-        green_mul<T>(L, cs, idx, sz, sy, in, out);
+        for (int qq = 0; qq < 3; ++qq) in[qq] = S[(qq * TC + cc) * RS + pos];
+        green_mul<T>(sL, (long)KZ * TC, (long)fz * TC + cc, sz, sy, in, out);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) S[(q * TC + cc) * RS + pos] = out[q];
+        for (int qq = 0; qq < 3; ++qq) S[(qq * TC + cc) * RS + pos] = out[qq];
     }
     __syncthreads();
     // ---- stage B3: inverse R2-point DFT over k2, twiddle W_M^(-t k1)
-    for (int task = threadIdx.x; task < 3 * R1 * TC; task += blockDim.x) {
-        const int q = task / (R1 * TC), rem = task - q * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
-        C *seg = S + (q * TC + cc) * RS + k1 * R2;
+    for (int task = threadIdx.x; task < 3 * R1 * TC; task += NT) {
+        const int qq = task / (R1 * TC), rem = task - qq * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
+        C *seg = S + (qq * TC + cc) * RS + k1 * R2;
         C u[R2];
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) u[k2] = seg[k2];
@@ -635,8 +685,7 @@ __global__ void __launch_bounds__(32 * R2) k_z_green_r(cplx<T> *__restrict__ buf
     }
     __syncthreads();
     // ---- stage A': inverse R1-point DFT over k1, rows z = t + R2 m < Nz
-#pragma unroll 1
-    for (int q = 0; q < 3; ++q) {
+    {
         C v[R1];
         const C *row = S + (q * TC + c) * RS;
 #pragma unroll

@@ -79,8 +79,8 @@ def test_z0_fft_product_matches_direct(ctx, orc, N, alpha):
         mot.mot_problem_destroy(prob)
 
 
-def _march_pair(ctx, orc, N, eps, alpha, exc, steps, precision):
-    prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+def _march_pair(ctx, orc, N, eps, alpha, exc, steps, precision, opt=None):
+    prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha, opt)
     try:
         run = mot.mot_run_create(prob, exc, precision)
         try:
@@ -123,6 +123,24 @@ def test_mot_oblique_batch(ctx, orc):
     Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
     e64 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64), Jo)
     assert e64.max() <= 1e-9, e64.max()
+
+
+def test_step_drivers_agree(ctx, orc):
+    """The three step drivers (one CUDA graph per step, host-driven steps with a
+    graph per TFQMR loop, no graphs at all) run the same kernels on the same
+    data and take the same convergence decisions."""
+    N = (9, 7, 8)
+    eps = synthetic.block_eps(N, 3, 2.0, 5.0, 8)
+    alpha, steps = 8.0, 14
+    exc = [synthetic.pulse(steps, alpha)]
+    Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
+    for precision, tol in ((mot.MOT_FP64, 1e-9), (mot.MOT_MIXED, 1e-5)):
+        J = {g: _march_pair(ctx, orc, N, eps, alpha, exc, steps, precision, mot.default_options(graph=g))
+             for g in (0, 1, 2)}
+        for g in (0, 1, 2):
+            assert _mot_errors(J[g], Jo).max() <= tol, (precision, g)
+        assert np.array_equal(J[0], J[2]), precision
+        assert _mot_errors(J[1], J[0]).max() <= 1e-12, precision
 
 
 def test_zero_contrast_gives_zero_current(ctx):
