@@ -151,9 +151,10 @@ void mot_problem_destroy(mot_problem *p);
 /* y = Z0 x for nrhs current vectors (Eq. 12: Z0 x = D x - X (G x), with
  * (G x) from Eq. 11 through zero-padded FFTs on the M0 grid).  x_dev, y_dev:
  * device arrays of nrhs*3*Nz*Ny*Nx elements of `dtype` (MOT_F64 computes in
- * FP64, MOT_F32 in FP32), x fastest; x and y must not overlap.  Asynchronous on
- * the context stream.  Errors: MOT_EINVAL (null, nrhs < 1, dtype), MOT_ENOMEM
- * (workspace), MOT_ECUDA.                                                     */
+ * FP64, MOT_F32 in FP32), x fastest; x and y must not overlap and must be
+ * 16-byte aligned (the kernels move 16-byte packs).  Asynchronous on the
+ * context stream.  Errors: MOT_EINVAL (null, nrhs < 1, dtype, alignment),
+ * MOT_ENOMEM (workspace), MOT_ECUDA.                                          */
 mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
 
 /* Byte size of the scratch array behind mot_apply_Z0_static (64 MiB).        */

@@ -639,7 +639,9 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
     const int planes = nrhs * 3 * Nz;
     const bool fused = z0_planes_fit<T>(p);
     if (fused) MOT_TRY((launch_xy_forward<Src, T>(src, Bf, planes, Nx, Ny, H, tx, ty, st)));
-    else {
+    else if constexpr (Epi::kPlaneOnly) {
+        MOT_FAIL(MOT_EUNSUPPORTED, "fused solver epilogue needs the plane passes");
+    } else {
         if (!plain) MOT_FAIL(MOT_EUNSUPPORTED, "row-pass product needs a stored input vector");
         MOT_TRY(launch_x_forward<TI, T>(plain, A, nrows, Nx, H, tx, st));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
@@ -659,7 +661,7 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_CHECK_LAUNCH();
     }
     if (fused) MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
-    else {
+    else if constexpr (!Epi::kPlaneOnly) {
         MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
         MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
     }
@@ -1048,6 +1050,8 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
     if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
     if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
     if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
+    if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15u)
+        MOT_FAIL(MOT_EINVAL, "x and y must be 16-byte aligned");
     MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
     size_t a, b;
     z0_ws_bytes(p, nrhs, dtype == MOT_F64 ? sizeof(double2) : sizeof(float2), &a, &b);
@@ -1176,7 +1180,9 @@ template <typename V> mot_status mvp_y1(mot_run *r, cudaStream_t st) {
 }
 
 // one TFQMR iteration (two half steps, two Z0 products) on stream st, ending
-// with the next alpha and the loop test (graph handle h if use_h, else ctl[2])
+// with the next alpha and the loop test (graph handle h if use_h, else ctl[2]).
+// Where the product runs as plane passes the vector updates ride in them
+// (six kernels); otherwise separate vector kernels (nine or ten).
 template <typename V>
 mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
     mot_problem *p = r->p;
@@ -1184,6 +1190,18 @@ mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st, cudaGraphConditionalHan
     KrylovView<V> k = kview<V>(r);
     unsigned *ctr = (unsigned *)r->ctr.p;
     dim3 gr(kRedBlocks, r->B);
+    if (z0_planes_fit<V>(p)) {
+        const int P = 3 * p->N[2];
+        const V *eps = eps_of<V>(p);
+        SrcHalfA<V> sa = {x, k.v[kW], k.v[kD], k.v[kY2], k.v[kY1], k.v[kAY1], k.v[kV], k.sc, L, k.p1, P, ctr};
+        EpiHalfB<V> eb = {k.v[kY2], k.v[kAY2], eps, x, k.v[kW], k.v[kD], k.v[kRS], k.sc, k.p1, k.p2, P, ctr + 1};
+        MOT_TRY((z0_product_src<SrcHalfA<V>, V, V>(p, sa, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, eb, st)));
+        SrcY1<V> s1 = {k.v[kY1], k.v[kW], k.v[kY2], k.sc, L};
+        EpiV<V> ev = {k.v[kY1], k.v[kAY1], eps, k.v[kV], k.v[kAY2], k.v[kRS], k.sc, k.p3, P, ctr + 2,
+                      (int *)r->ctl.p, h, use_h};
+        MOT_TRY((z0_product_src<SrcY1<V>, V, V>(p, s1, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, ev, st)));
+        return MOT_OK;
+    }
     count_launch();
     k_tfqmr_half_a<V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kY1], k.v[kAY1], k.v[kV], k.sc,
                                                    L, k.p1, ctr);
@@ -1919,9 +1937,11 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
         if ((s = dalloc(r->kv[i], vs * n)) != MOT_OK) return fail(s);
     if (mixed && (s = dalloc(r->r32, sizeof(float) * 2 * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->scal, sizeof(TfqmrScal) * nrhs)) != MOT_OK) return fail(s);
-    if ((s = dalloc(r->part1, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
-    if ((s = dalloc(r->part2, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
-    if ((s = dalloc(r->part3, sizeof(double) * kRedBlocks * nrhs)) != MOT_OK) return fail(s);
+    // partial sums per right-hand side: kRedBlocks blocks or one per (component, z) plane
+    const long nparts = std::max<long>(kRedBlocks, 3L * p->N[2]);
+    if ((s = dalloc(r->part1, sizeof(double) * nparts * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->part2, sizeof(double) * nparts * nrhs)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->part3, sizeof(double) * nparts * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->dots, sizeof(double) * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->ctl, sizeof(int) * 4)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->ctr, sizeof(unsigned) * 4)) != MOT_OK) return fail(s);
@@ -2116,6 +2136,8 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
     if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
     if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
     if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
+    if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15u)
+        MOT_FAIL(MOT_EINVAL, "x and y must be 16-byte aligned");
     const int dev = p->ctx->device;
     if (dev < 0 || dev >= kMaxDevices) MOT_FAIL(MOT_EINVAL, "device index beyond the static-scratch table");
     size_t a, b;

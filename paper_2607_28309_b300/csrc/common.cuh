@@ -27,6 +27,26 @@ template <typename C> MOT_HD inline C cconj(C a) { return cmake<C>(a.x, -a.y); }
 // multiply by i (sign +1) or -i (sign -1)
 template <int S, typename C> MOT_HD inline C cmuli(C a) { return S > 0 ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x); }
 
+// W consecutive elements moved with 16-byte accesses; p must be 16-byte
+// aligned and W * sizeof(E) a multiple of 16
+template <int W, typename E> __device__ __forceinline__ void ldv(E (&r)[W], const E *p) {
+    static_assert((W * sizeof(E)) % 16 == 0, "whole 16-byte accesses");
+#pragma unroll
+    for (int k = 0; k < (int)(W * sizeof(E) / 16); ++k) {
+        const uint4 u = reinterpret_cast<const uint4 *>(p)[k];
+        memcpy(reinterpret_cast<char *>(r) + 16 * k, &u, 16);
+    }
+}
+template <int W, typename E> __device__ __forceinline__ void stv(E *p, const E (&r)[W]) {
+    static_assert((W * sizeof(E)) % 16 == 0, "whole 16-byte accesses");
+#pragma unroll
+    for (int k = 0; k < (int)(W * sizeof(E) / 16); ++k) {
+        uint4 u;
+        memcpy(&u, reinterpret_cast<const char *>(r) + 16 * k, 16);
+        reinterpret_cast<uint4 *>(p)[k] = u;
+    }
+}
+
 // thread-local error message + status helpers (host side)
 void set_error(const std::string &msg);
 const char *get_error();

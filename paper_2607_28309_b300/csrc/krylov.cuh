@@ -38,15 +38,6 @@ template <> struct AccOf<float> { using type = float; };
 // pack width (then every right-hand side's slice starts 16-byte aligned) and
 // fall back to single elements otherwise
 template <typename V> struct PackW { static constexpr int W = 16 / sizeof(V); };
-template <typename V> __device__ __forceinline__ void ld_pack(V (&r)[PackW<V>::W], const V *p) {
-    const uint4 u = *reinterpret_cast<const uint4 *>(p);
-    memcpy(r, &u, 16);
-}
-template <typename V> __device__ __forceinline__ void st_pack(V *p, const V (&r)[PackW<V>::W]) {
-    uint4 u;
-    memcpy(&u, r, 16);
-    *reinterpret_cast<uint4 *>(p) = u;
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -203,12 +194,12 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_a(V *__restrict__ x,
         for (long j = t0; j < np; j += ts) {
             const long i = o + j * W;
             V dd[W], yy[W], ww[W], aa[W], vv[W], xx[W];
-            ld_pack(dd, d + i);
-            ld_pack(yy, y1 + i);
-            ld_pack(ww, w + i);
-            ld_pack(aa, Ay1 + i);
-            ld_pack(vv, v + i);
-            if (s.pending) ld_pack(xx, x + i);
+            ldv<W>(dd, d + i);
+            ldv<W>(yy, y1 + i);
+            ldv<W>(ww, w + i);
+            ldv<W>(aa, Ay1 + i);
+            ldv<W>(vv, v + i);
+            if (s.pending) ldv<W>(xx, x + i);
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 if (s.pending) xx[k] += ep * dd[k];
@@ -217,10 +208,10 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_a(V *__restrict__ x,
                 dd[k] = yy[k] + coef * dd[k];
                 yy[k] -= al * vv[k];
             }
-            if (s.pending) st_pack(x + i, xx);
-            st_pack(w + i, ww);
-            st_pack(d + i, dd);
-            st_pack(y2 + i, yy);
+            if (s.pending) stv<W>(x + i, xx);
+            stv<W>(w + i, ww);
+            stv<W>(d + i, dd);
+            stv<W>(y2 + i, yy);
         }
         for (long i = np * W + t0; i < L; i += ts) {
             const V dold = d[o + i], yv = y1[o + i];
@@ -273,12 +264,12 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x,
         for (long j = t0; j < np; j += ts) {
             const long i = o + j * W;
             V dd[W], yy[W], ww[W], aa[W], rr[W], xx[W];
-            ld_pack(dd, d + i);
-            ld_pack(yy, y2 + i);
-            ld_pack(ww, w + i);
-            ld_pack(aa, Ay2 + i);
-            ld_pack(rr, rs + i);
-            if (s.pending) ld_pack(xx, x + i);
+            ldv<W>(dd, d + i);
+            ldv<W>(yy, y2 + i);
+            ldv<W>(ww, w + i);
+            ldv<W>(aa, Ay2 + i);
+            ldv<W>(rr, rs + i);
+            if (s.pending) ldv<W>(xx, x + i);
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 if (s.pending) xx[k] += ep * dd[k];
@@ -287,9 +278,9 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x,
                 rw += rr[k] * ww[k];
                 dd[k] = yy[k] + coef * dd[k];
             }
-            if (s.pending) st_pack(x + i, xx);
-            st_pack(w + i, ww);
-            st_pack(d + i, dd);
+            if (s.pending) stv<W>(x + i, xx);
+            stv<W>(w + i, ww);
+            stv<W>(d + i, dd);
         }
         for (long i = np * W + t0; i < L; i += ts) {
             const V dold = d[o + i];
@@ -340,8 +331,8 @@ __global__ void k_tfqmr_y1(V *__restrict__ y1, const V *__restrict__ w, const V 
         y1[o + i] = w[o + i] + be * y2[o + i];
 }
 
-// y1 = w + beta y2 formed while a forward plane kernel reads it, and stored
-// (each element is loaded once); unchanged for right-hand sides that stopped
+// y1 = w + beta y2 formed while a forward plane kernel stages it, and stored;
+// unchanged for right-hand sides that stopped
 template <typename V> struct SrcY1 {
     V *y1;
     const V *w, *y2;
@@ -352,17 +343,354 @@ template <typename V> struct SrcY1 {
         const V *w, *y2;
         V beta;
         int skip;
-        __device__ __forceinline__ V load(long o) const {
-            if (skip) return y1[o];
-            const V v = w[o] + beta * y2[o];
-            y1[o] = v;
-            return v;
+        __device__ __forceinline__ void stage(V *sm, int n) const {
+            constexpr int W = PackW<V>::W;
+            if (n % W == 0) {
+                for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+                    V a[W], c[W];
+                    if (skip) ldv<W>(a, y1 + j * W);
+                    else {
+                        ldv<W>(a, w + j * W);
+                        ldv<W>(c, y2 + j * W);
+#pragma unroll
+                        for (int k = 0; k < W; ++k) a[k] += beta * c[k];
+                        stv<W>(y1 + j * W, a);
+                    }
+#pragma unroll
+                    for (int k = 0; k < W; ++k) sm[j * W + k] = a[k];
+                }
+            } else {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    V a;
+                    if (skip) a = y1[i];
+                    else {
+                        a = w[i] + beta * y2[i];
+                        y1[i] = a;
+                    }
+                    sm[i] = a;
+                }
+            }
         }
     };
     __device__ __forceinline__ Plane bind(long plane, long plane_size) const {
         const long off = plane * plane_size;
         const int b = (int)(off / L);
         return Plane{y1 + off, w + off, y2 + off, (V)sc[b].beta, sc[b].conv != 0};
+    }
+    __device__ __forceinline__ void finish(const Plane &, long, long) const {}
+};
+
+// ---------------------------------------------------------------------------
+// TFQMR vector updates fused into the Z0 product's plane kernels.  The plane
+// kernels load (forward) and store (inverse) every element of every
+// right-hand side exactly once, one (b, component, z) plane per block, so an
+// element-wise update can ride along: SrcHalfA forms y2 (and the first half
+// step's w, d, x updates) while the forward pass reads it, EpiHalfB applies
+// the second half step to Ay2 as the inverse pass writes it, EpiV the v
+// update to Ay1.  Each block leaves its partial sums at part[b*P + j]
+// (P = 3 Nz planes per right-hand side, j the block's plane within it) and
+// the last block to finish does the scalar update, as the kernels above do.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double reduce_parts_n(const double *part, int b, int lane, int P) {
+    double s = 0.0;
+    for (int i = lane; i < P; i += 32) s += __ldcg(part + (long)b * P + i);
+    return warp_sum(s);
+}
+
+// block sums of NV thread values into part[k][slot]; true in the last block
+template <int NV>
+__device__ __forceinline__ bool plane_block_done(const double (&v)[NV], double *const (&part)[NV], long slot,
+                                                 unsigned *ctr) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double t = block_sum(v[k], sh);
+        if (threadIdx.x == 0) part[k][slot] = t;
+    }
+    return last_block(ctr, gridDim.x * gridDim.y);
+}
+
+// first half step (see k_tfqmr_half_a) formed while the forward pass loads y2
+template <typename V> struct SrcHalfA {
+    V *x, *w, *d, *y2;
+    const V *y1, *Ay1, *v;
+    TfqmrScal *sc;
+    long L;          // vector length of one right-hand side
+    double *part;    // ||w||^2 partials [B][P]
+    int P;           // planes per right-hand side
+    unsigned *ctr;
+    struct Plane {
+        V *x, *w, *d, *y2;
+        const V *y1, *Ay1, *v;
+        V al, coef, ep;
+        int pending, skip;
+        typename AccOf<V>::type w2;
+        __device__ __forceinline__ void stage(V *sm, int n) {
+            constexpr int W = PackW<V>::W;
+            if (n % W == 0) {
+                for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+                    const long o = (long)j * W;
+                    V yy[W];
+                    if (skip) {
+                        ldv<W>(yy, y2 + o);
+                    } else {
+                        V dd[W], ww[W], aa[W], vv[W], xx[W];
+                        ldv<W>(dd, d + o);
+                        ldv<W>(yy, y1 + o);
+                        ldv<W>(ww, w + o);
+                        ldv<W>(aa, Ay1 + o);
+                        ldv<W>(vv, v + o);
+                        if (pending) ldv<W>(xx, x + o);
+#pragma unroll
+                        for (int k = 0; k < W; ++k) {
+                            if (pending) xx[k] += ep * dd[k];
+                            ww[k] -= al * aa[k];
+                            w2 += ww[k] * ww[k];
+                            dd[k] = yy[k] + coef * dd[k];
+                            yy[k] -= al * vv[k];
+                        }
+                        if (pending) stv<W>(x + o, xx);
+                        stv<W>(w + o, ww);
+                        stv<W>(d + o, dd);
+                        stv<W>(y2 + o, yy);
+                    }
+#pragma unroll
+                    for (int k = 0; k < W; ++k) sm[o + k] = yy[k];
+                }
+            } else {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    if (skip) {
+                        sm[i] = y2[i];
+                        continue;
+                    }
+                    const V dold = d[i], yv = y1[i];
+                    if (pending) x[i] += ep * dold;
+                    const V wn = w[i] - al * Ay1[i];
+                    w[i] = wn;
+                    w2 += wn * wn;
+                    d[i] = yv + coef * dold;
+                    const V y = yv - al * v[i];
+                    y2[i] = y;
+                    sm[i] = y;
+                }
+            }
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, long plane_size) const {
+        const long off = plane * plane_size;
+        const TfqmrScal s = sc[(int)(off / L)];
+        Plane p{x + off, w + off, d + off, y2 + off, y1 + off, Ay1 + off, v + off, V(0), V(0), V(0),
+                s.pending, s.conv != 0, 0};
+        if (!p.skip) {
+            p.al = (V)s.alpha;
+            p.coef = (V)(s.theta * s.theta * s.eta / s.alpha);
+            p.ep = (V)s.eta_prev;
+        }
+        return p;
+    }
+    __device__ __forceinline__ void finish(const Plane &pl, long plane, long plane_size) const {
+        const int b = (int)(plane * plane_size / L);
+        const double vals[1] = {(double)pl.w2};
+        double *const parts[1] = {part};
+        if (!plane_block_done<1>(vals, parts, (long)b * P + (plane - (long)b * P), ctr)) return;
+        const int lane = threadIdx.x & 31, B = (int)(gridDim.x / P);
+        for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
+            const double t = reduce_parts_n(part, bb, lane, P);
+            if (lane == 0 && !sc[bb].conv) {
+                TfqmrScal u = sc[bb];
+                half_scalars(u, t);
+                sc[bb] = u;
+            }
+        }
+        if (threadIdx.x == 0) *ctr = 0u;
+    }
+};
+
+// Ay2 = Z0 y2 (Eq. 12) and the second half step (see k_tfqmr_half_b)
+template <typename V> struct EpiHalfB {
+    static constexpr bool kPlaneOnly = true;
+    const V *y2;
+    V *Ay2;
+    const V *eps;
+    V *x, *w, *d;
+    const V *rs;
+    TfqmrScal *sc;
+    double *part_w2, *part_rw;  // [B][P]
+    int P;
+    unsigned *ctr;
+    struct Plane {
+        const V *y2;
+        V *Ay2;
+        const V *eps;
+        V *x, *w, *d;
+        const V *rs;
+        V al, coef, ep;
+        int pending, skip;
+        typename AccOf<V>::type w2, rw;
+        __device__ __forceinline__ void operator()(int i, V g) {
+            const V e = eps[i], yv = y2[i];
+            const V ay = e * V(0.5) * yv - (e - V(1)) * g;
+            Ay2[i] = ay;
+            if (skip) return;
+            const V dold = d[i];
+            if (pending) x[i] += ep * dold;
+            const V wn = w[i] - al * ay;
+            w[i] = wn;
+            d[i] = yv + coef * dold;
+            w2 += wn * wn;
+            rw += rs[i] * wn;
+        }
+        template <int W> __device__ __forceinline__ void pack(int i, const V (&g)[W]) {
+            V e[W], yv[W], ay[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(yv, y2 + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) ay[k] = e[k] * V(0.5) * yv[k] - (e[k] - V(1)) * g[k];
+            stv<W>(Ay2 + i, ay);
+            if (skip) return;
+            V dd[W], ww[W], rr[W], xx[W];
+            ldv<W>(dd, d + i);
+            ldv<W>(ww, w + i);
+            ldv<W>(rr, rs + i);
+            if (pending) ldv<W>(xx, x + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (pending) xx[k] += ep * dd[k];
+                ww[k] -= al * ay[k];
+                w2 += ww[k] * ww[k];
+                rw += rr[k] * ww[k];
+                dd[k] = yv[k] + coef * dd[k];
+            }
+            if (pending) stv<W>(x + i, xx);
+            stv<W>(w + i, ww);
+            stv<W>(d + i, dd);
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
+        const TfqmrScal s = sc[(int)(plane / P)];
+        Plane p{y2 + off, Ay2 + off, eps + zoff, x + off, w + off, d + off, rs + off, V(0), V(0), V(0),
+                s.pending, s.conv != 0, 0, 0};
+        if (!p.skip) {
+            p.al = (V)s.alpha;
+            p.coef = (V)(s.theta * s.theta * s.eta / s.alpha);
+            p.ep = (V)s.eta_prev;
+        }
+        return p;
+    }
+    __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
+        const int b = (int)(plane / P);
+        const double vals[2] = {(double)pl.w2, (double)pl.rw};
+        double *const parts[2] = {part_w2, part_rw};
+        if (!plane_block_done<2>(vals, parts, plane, ctr)) return;
+        const int lane = threadIdx.x & 31, B = (int)(gridDim.x / P);
+        (void)b;
+        for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
+            const double t = reduce_parts_n(part_w2, bb, lane, P);
+            const double rn = reduce_parts_n(part_rw, bb, lane, P);
+            if (lane == 0 && !sc[bb].conv) {
+                TfqmrScal u = sc[bb];
+                half_scalars(u, t);
+                if (!u.conv) {
+                    if (u.rho == 0.0) u.conv = 2;
+                    else {
+                        u.beta = rn / u.rho;
+                        u.rho = rn;
+                    }
+                }
+                sc[bb] = u;
+            }
+        }
+        if (threadIdx.x == 0) *ctr = 0u;
+    }
+};
+
+// Ay1 = Z0 y1 (Eq. 12) and v = Ay1 + beta (Ay2 + beta v), then alpha and the
+// loop test (see k_tfqmr_v)
+template <typename V> struct EpiV {
+    static constexpr bool kPlaneOnly = true;
+    const V *y1;
+    V *Ay1;
+    const V *eps;
+    V *v;
+    const V *Ay2, *rs;
+    TfqmrScal *sc;
+    double *part;  // [B][P]
+    int P;
+    unsigned *ctr;
+    int *ctl;
+    cudaGraphConditionalHandle h;
+    int use_h;
+    struct Plane {
+        const V *y1;
+        V *Ay1;
+        const V *eps;
+        V *v;
+        const V *Ay2, *rs;
+        V be;
+        int skip;
+        typename AccOf<V>::type acc;
+        __device__ __forceinline__ void operator()(int i, V g) {
+            const V e = eps[i];
+            const V ay = e * V(0.5) * y1[i] - (e - V(1)) * g;
+            Ay1[i] = ay;
+            if (skip) return;
+            const V vn = ay + be * (Ay2[i] + be * v[i]);
+            v[i] = vn;
+            acc += rs[i] * vn;
+        }
+        template <int W> __device__ __forceinline__ void pack(int i, const V (&g)[W]) {
+            V e[W], yv[W], ay[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(yv, y1 + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) ay[k] = e[k] * V(0.5) * yv[k] - (e[k] - V(1)) * g[k];
+            stv<W>(Ay1 + i, ay);
+            if (skip) return;
+            V a2[W], vv[W], rr[W];
+            ldv<W>(a2, Ay2 + i);
+            ldv<W>(vv, v + i);
+            ldv<W>(rr, rs + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                vv[k] = ay[k] + be * (a2[k] + be * vv[k]);
+                acc += rr[k] * vv[k];
+            }
+            stv<W>(v + i, vv);
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
+        const TfqmrScal s = sc[(int)(plane / P)];
+        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, (V)s.beta, s.conv != 0, 0};
+    }
+    __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
+        __shared__ int active;
+        const double vals[1] = {(double)pl.acc};
+        double *const parts[1] = {part};
+        if (!plane_block_done<1>(vals, parts, plane, ctr)) return;
+        if (threadIdx.x == 0) active = 0;
+        __syncthreads();
+        const int lane = threadIdx.x & 31, B = (int)(gridDim.x / P);
+        for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
+            const double sigma = reduce_parts_n(part, bb, lane, P);
+            if (lane == 0) {
+                if (!sc[bb].conv) {
+                    if (sigma == 0.0) sc[bb].conv = 2;
+                    else sc[bb].alpha = sc[bb].rho / sigma;
+                }
+                if (sc[bb].conv == 0) active = 1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int it = ctl[0] + 1;
+            ctl[0] = it;
+            const int cont = (active && it < ctl[1]) ? 1 : 0;
+            if (use_h) cudaGraphSetConditional(h, (unsigned)cont);
+            else ctl[2] = cont;
+            *ctr = 0u;
+        }
     }
 };
 
@@ -392,16 +720,16 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, cons
         for (long j = t0; j < np; j += ts) {
             const long i = o + j * W;
             V a1[W], a2[W], vv[W], rr[W];
-            ld_pack(a1, Ay1 + i);
-            ld_pack(a2, Ay2 + i);
-            ld_pack(vv, v + i);
-            ld_pack(rr, rs + i);
+            ldv<W>(a1, Ay1 + i);
+            ldv<W>(a2, Ay2 + i);
+            ldv<W>(vv, v + i);
+            ldv<W>(rr, rs + i);
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 vv[k] = a1[k] + be * (a2[k] + be * vv[k]);
                 acc += rr[k] * vv[k];
             }
-            st_pack(v + i, vv);
+            stv<W>(v + i, vv);
         }
         for (long i = np * W + t0; i < L; i += ts) {
             const V vn = Ay1[o + i] + be * (Ay2[o + i] + be * v[o + i]);

@@ -103,18 +103,51 @@ __global__ void __launch_bounds__(512) k_axis(const cplx<T> *__restrict__ in, cp
 }
 
 // ---------------------------------------------------------------------------
-// input of the plane kernels: bind(plane, plane_size) gives an accessor whose
-// load(o) returns element o of that plane.  SrcPlain reads a stored vector;
-// other sources form the vector while it is read (one load per element).
+// input of the plane kernels: bind(plane, plane_size) gives a per-block view
+// whose stage(sm, n) writes the plane's n elements, in the FFT precision, to
+// shared memory (all threads of the block take part; 16-byte accesses when n
+// is a multiple of the pack width, which also makes every plane 16-byte
+// aligned).  SrcPlain reads a stored vector; other sources form the vector
+// while staging it (and store it).  finish() runs at the end of the block.
 // ---------------------------------------------------------------------------
 template <typename TI> struct SrcPlain {
     const TI *x;
     struct Plane {
         const TI *p;
-        __device__ __forceinline__ TI load(long o) const { return p[o]; }
+        template <typename T> __device__ __forceinline__ void stage(T *sm, int n) const {
+            constexpr int W = 16 / sizeof(T);
+            if (n % W == 0) {
+                for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+                    TI v[W];
+                    ldv<W>(v, p + (long)j * W);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) sm[j * W + k] = (T)v[k];
+                }
+            } else {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = (T)p[i];
+            }
+        }
     };
     __device__ __forceinline__ Plane bind(long plane, long plane_size) const { return Plane{x + plane * plane_size}; }
+    __device__ __forceinline__ void finish(const Plane &, long, long) const {}  // end-of-block hook
 };
+
+// epilogue driver of the inverse plane kernels: g(i) is element i of the
+// plane's result; packs of W elements go to pe.pack when n allows it
+template <typename T, class PE, class G>
+__device__ __forceinline__ void run_epilogue(PE &pe, int n, G g) {
+    constexpr int W = 16 / sizeof(T);
+    if (n % W == 0) {
+        for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+            T v[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) v[k] = g(j * W + k);
+            pe.template pack<W>(j * W, v);
+        }
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pe(i, g(i));
+    }
+}
 
 // ---------------------------------------------------------------------------
 // fused xy passes over whole planes (used when a plane fits in shared memory):
@@ -149,15 +182,19 @@ __global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(Src x, cplx<T> *
     load_twiddles(twx, twx_g, Mx);
     load_twiddles(twy, twy_g, My);
     const long plane = blockIdx.x;
-    const auto src = x.bind(plane, (long)Ny * Nx);
+    auto src = x.bind(plane, (long)Ny * Nx);
     const FastDiv fNx = make_fastdiv((unsigned)Nx), fMx = make_fastdiv((unsigned)Mx), fH = make_fastdiv((unsigned)H);
+    T *stg = reinterpret_cast<T *>(Pl);  // the plane's Ny*Nx inputs (Pl is free until the y pass)
+    __syncthreads();
+    src.stage(stg, Ny * Nx);
+    __syncthreads();
     // rows y and y+1 -> one complex pencil; padded columns and a missing odd row are 0
     for (int i = threadIdx.x; i < np * Mx; i += blockDim.x) {
         int pr = (int)fdiv((unsigned)i, fMx), e = i - pr * Mx;
         T re = T(0), im = T(0);
         if (e < Nx) {
-            re = (T)src.load((long)(2 * pr) * Nx + e);
-            if (2 * pr + 1 < Ny) im = (T)src.load((long)(2 * pr + 1) * Nx + e);
+            re = stg[(2 * pr) * Nx + e];
+            if (2 * pr + 1 < Ny) im = stg[(2 * pr + 1) * Nx + e];
         }
         A[i] = cmake<C>(re, im);
     }
@@ -178,6 +215,7 @@ __global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_forward(Src x, cplx<T> *
     C *ry = block_fft<-1>(Pl, Q, py, H, 1, H, twy, true);
     C *dst = out + plane * (long)My * H;
     for (int i = threadIdx.x; i < My * H; i += blockDim.x) dst[i] = ry[i];
+    x.finish(src, plane, (long)Ny * Nx);
     (void)fNx;
 }
 
@@ -215,12 +253,13 @@ __global__ void __launch_bounds__(kXYThreadsOf<T>) k_xy_inverse(const cplx<T> *_
     }
     __syncthreads();
     C *rx = block_fft<+1>(A, Bb, px, np, Mx, 1, twx, false);
-    const auto pe = epi.bind(plane, Nz, Ny * Nx);
-    for (int i = threadIdx.x; i < Ny * Nx; i += blockDim.x) {
-        int y = (int)fdiv((unsigned)i, fNx);
-        C z = rx[(y >> 1) * Mx + (i - y * Nx)];
-        pe(i, (y & 1) ? z.y : z.x);
-    }
+    auto pe = epi.bind(plane, Nz, Ny * Nx);
+    run_epilogue<T>(pe, Ny * Nx, [&](int i) {
+        const int y = (int)fdiv((unsigned)i, fNx);
+        const C z = rx[(y >> 1) * Mx + (i - y * Nx)];
+        return (y & 1) ? z.y : z.x;
+    });
+    epi.finish(pe, plane);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,8 +297,11 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
     load_twiddles(twy, twy_g, My);
     __syncthreads();
     const long plane = blockIdx.x;
-    const auto src = x.bind(plane, (long)Ny * Nx);
-    // x stage A: pencil p = rows (2p, 2p+1) as re/im, thread t < RX2 loads e = t + RX2 m
+    auto src = x.bind(plane, (long)Ny * Nx);
+    T *stg = reinterpret_cast<T *>(Bf);  // the plane's Ny*Nx inputs (Bf is free until x stage B)
+    src.stage(stg, Ny * Nx);
+    __syncthreads();
+    // x stage A: pencil p = rows (2p, 2p+1) as re/im, thread t < RX2 takes e = t + RX2 m
     for (int task = threadIdx.x; task < np * RX2; task += blockDim.x) {
         const int p = task / RX2, t = task - p * RX2;
         C v[RX1];
@@ -269,8 +311,8 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
             const int e = t + RX2 * m;
             T re = T(0), im = T(0);
             if (e < Nx) {
-                re = (T)src.load((long)(2 * p) * Nx + e);
-                if (two) im = (T)src.load((long)(2 * p + 1) * Nx + e);
+                re = stg[(2 * p) * Nx + e];
+                if (two) im = stg[(2 * p + 1) * Nx + e];
             }
             v[m] = cmake<C>(re, im);
         }
@@ -327,6 +369,7 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
 #pragma unroll
         for (int k2 = 0; k2 < RY2; ++k2) dst[(k1 + RY1 * k2) * H + kx] = u[k2];
     }
+    x.finish(src, plane, (long)Ny * Nx);
 }
 
 template <typename T, class Epi, int RX1, int RX2, int RY1, int RY2>
@@ -407,13 +450,14 @@ __global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict_
     }
     __syncthreads();
     // epilogue, x fastest (rows 2p, 2p+1 are the real and imaginary parts)
-    const auto pe = epi.bind(plane, Nz, Ny * Nx);
+    auto pe = epi.bind(plane, Nz, Ny * Nx);
     const FastDiv fNx = make_fastdiv((unsigned)Nx);
-    for (int i = threadIdx.x; i < Ny * Nx; i += blockDim.x) {
+    run_epilogue<T>(pe, Ny * Nx, [&](int i) {
         const int y = (int)fdiv((unsigned)i, fNx), e = i - y * Nx;
         const C z = Bf[(y >> 1) * PX + e];
-        pe(i, (y & 1) ? z.y : z.x);
-    }
+        return (y & 1) ? z.y : z.x;
+    });
+    epi.finish(pe, plane);
 }
 
 // Green-spectrum lookup: octant value with the parity signs of each component.
@@ -843,6 +887,7 @@ __global__ void __launch_bounds__(256) k_x_inverse(const cplx<T> *__restrict__ i
 // (eps given in that precision too)
 template <typename TX, typename TY>
 struct EpiZ0 {
+    static constexpr bool kPlaneOnly = false;  // also usable by the row pass
     const TX *x;
     TY *y;
     const TY *eps;
@@ -862,6 +907,15 @@ struct EpiZ0 {
             TY ep = eps[i];
             y[i] = ep * TY(0.5) * (TY)x[i] - (ep - TY(1)) * g;
         }
+        template <int W> __device__ __forceinline__ void pack(int i, const TY (&g)[W]) const {
+            TY e[W], r[W];
+            TX xv[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(xv, x + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) r[k] = e[k] * TY(0.5) * (TY)xv[k] - (e[k] - TY(1)) * g[k];
+            stv<W>(y + i, r);
+        }
     };
     // plane = (b*3 + p)*Nz + z; Ny*Nx = plane_rows/Nz*Nx is recovered from Nz
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
@@ -869,10 +923,12 @@ struct EpiZ0 {
         long zoff = (plane % Nz) * (long)NyNx;
         return Plane{x + off, y + off, eps + zoff};
     }
+    __device__ __forceinline__ void finish(const Plane &, long) const {}  // end-of-block hook
 };
 
 // refinement residual: r = b - (eps T(0) x - (eps - 1) G), all FP64
 struct EpiResidual {
+    static constexpr bool kPlaneOnly = false;
     const double *x, *b;
     double *r;
     const double *eps;
@@ -892,18 +948,29 @@ struct EpiResidual {
             double ep = eps[i];
             r[i] = b[i] - (ep * 0.5 * x[i] - (ep - 1.0) * g);
         }
+        template <int W, typename G> __device__ __forceinline__ void pack(int i, const G (&g)[W]) const {
+            double e[W], xv[W], bv[W], rv[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(xv, x + i);
+            ldv<W>(bv, b + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) rv[k] = bv[k] - (e[k] * 0.5 * xv[k] - (e[k] - 1.0) * (double)g[k]);
+            stv<W>(r + i, rv);
+        }
     };
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         long off = plane * (long)NyNx;
         long zoff = (plane % Nz) * (long)NyNx;
         return Plane{x + off, b + off, r + off, eps + zoff};
     }
+    __device__ __forceinline__ void finish(const Plane &, long) const {}
 };
 
 // right-hand side (Eq. 3): b_n = E^i_n - eps T(dt) J_{n-1} + (eps - 1) sum_k G_k J_{n-k}
 // (T(k dt) = 0 for k >= 2, so only lag 1 carries the constitutive term);
 // E^i_n[b][p][m] = inc[b][m] * pol[b][p]
 struct EpiHistory {
+    static constexpr bool kPlaneOnly = false;
     const double *inc;    // [B][n]: (eps - 1) eps0 <dE/dt>/|pol| scalar per voxel
     const double *pol;    // [B][3]
     const double *Jprev;  // [B][3][n] (null at n = 0)
@@ -934,6 +1001,18 @@ struct EpiHistory {
             if (Jprev) v -= ep * 0.5 * Jprev[i];
             out[i] = v;
         }
+        template <int W, typename G> __device__ __forceinline__ void pack(int i, const G (&g)[W]) const {
+            double e[W], in[W], jp[W], v[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(in, inc + i);
+            if (Jprev) ldv<W>(jp, Jprev + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                v[k] = in[k] * pol + (e[k] - 1.0) * (double)g[k];
+                if (Jprev) v[k] -= e[k] * 0.5 * jp[k];
+            }
+            stv<W>(out + i, v);
+        }
     };
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         long off = plane * (long)NyNx;
@@ -943,6 +1022,7 @@ struct EpiHistory {
         long zoff = z * (long)NyNx;
         return Plane{inc + bb * nvox + zoff, Jprev ? Jprev + off : nullptr, eps + zoff, out + off, pol[bb * 3 + p]};
     }
+    __device__ __forceinline__ void finish(const Plane &, long) const {}
 };
 
 }  // namespace mot

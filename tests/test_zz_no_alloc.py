@@ -49,6 +49,13 @@ def test_static_scratch_product_matches_allocating_product():
                         torch.cuda.synchronize()
                         assert torch.isfinite(y).all()
                         assert _rel(y, ref) <= tol
+            # pointers off the 16-byte grid are refused before any device work
+            x = torch.zeros(3 * nv + 1, device="cuda", dtype=torch.float32)
+            y = torch.zeros_like(x)
+            for f in (mot.mot_apply_Z0, mot.mot_apply_Z0_static):
+                with pytest.raises(mot.MotError) as e:
+                    f(prob, x[1:].data_ptr(), y[1:].data_ptr(), 1, mot.MOT_F32)
+                assert e.value.status == mot.MOT_EINVAL
             # a request beyond the static array is refused with MOT_EINVAL
             big = 1 + mot.MOT_STATIC_SCRATCH_BYTES // (3 * N[2] * N[1] * 16 * 16)
             x = torch.zeros(big, 3, nv, device="cuda", dtype=torch.float64)
