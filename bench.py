@@ -204,6 +204,84 @@ def oracle_sample(w, mvps_per_step: float, rows: int = 2048, seed: int = 0):
             "entries_per_s": entries_per_s, "step_entries": step_entries, "cores": os.cpu_count()}
 
 
+# ---------------------------------------------------------------- roofline bookkeeping
+KERNEL_NAMES = {
+    "z_green": "k_z_green_r (present-time z pass)",
+    "z_history": "k_z_history2 (history z pass)",
+    "fwd_half": "k_xy_forward_r<SrcHalfA> (forward xy pass of Z0 y2 + first TFQMR half step)",
+    "fwd_y1": "k_xy_forward_r<SrcY1> (forward xy pass of Z0 y1)",
+    "fwd_plain": "k_xy_forward_r<SrcPlain> (forward xy pass, stored input)",
+    "fwd_ring": "k_xy_forward_r<SrcPlain<double>> (ring push, Mh grid)",
+    "inv_half": "k_xy_inverse_r<EpiHalfB> (inverse xy pass of Z0 y2 + second TFQMR half step)",
+    "inv_v": "k_xy_inverse_r<EpiV> (inverse xy pass of Z0 y1 + v update)",
+    "inv_z0": "k_xy_inverse_r<EpiZ0> (inverse xy pass, Z0 epilogue)",
+    "inv_residual": "k_xy_inverse_r<EpiResidual> (inverse xy pass, FP64 residual)",
+    "inv_history": "k_xy_inverse_r<EpiHistory> (inverse xy pass of the history sum, Mh grid)",
+}
+
+
+def kernel_bytes(info, N, B, prec, lags):
+    """Algorithmic bytes of one launch of each timed kernel class: every array
+    the kernel must read or write once, nothing for re-reads.  lags: the
+    history lag count of each timed step (for the history z pass)."""
+    nv = N[0] * N[1] * N[2]
+    cs = 8 if prec == 1 else 16          # complex element of the FFT precision (MOT_MIXED = 1)
+    rs = cs // 2                         # real element of the solve precision
+    M0, Mh = list(info.M0), list(info.Mh)
+    H0, Hh = M0[0] // 2 + 1, Mh[0] // 2 + 1
+    K0 = [m // 2 + 1 for m in M0]
+    Kh = [m // 2 + 1 for m in Mh]
+    vec = B * 3 * nv * rs                # one solver vector
+    vec64 = B * 3 * nv * 8               # one FP64 vector (J, b, residual)
+    pl0 = B * 3 * N[2] * M0[1] * H0 * cs  # the product's (z, ky, kx) planes
+    plh = B * 3 * N[2] * Mh[1] * Hh * cs
+    eps = nv * rs
+    slot = B * 3 * Mh[2] * Mh[1] * Hh * cs
+    lam_h = 6 * Kh[2] * Kh[1] * Hh * rs
+    zh = sum(L * (slot + lam_h) + plh for L in lags) / max(len(lags), 1)
+    return {
+        "z_green": 2 * pl0 + 6 * K0[2] * K0[1] * H0 * rs,
+        "z_history": zh,
+        "fwd_half": 10 * vec + pl0,      # read d, y1, w, Ay1, v, x; write x, w, d, y2; write planes
+        "fwd_y1": 3 * vec + pl0,         # read w, y2; write y1; write planes
+        "fwd_plain": vec64 + pl0,        # the FP64 J of the residual product
+        "fwd_ring": vec64 + plh,
+        "inv_half": pl0 + eps + 9 * vec,  # read planes, eps, y2, d, w, r*, x; write Ay2, w, d, x
+        "inv_v": pl0 + eps + 6 * vec,     # read planes, eps, y1, Ay2, v, r*; write Ay1, v
+        "inv_z0": pl0 + eps + 2 * vec,
+        "inv_residual": pl0 + nv * 8 + 3 * vec64,
+        "inv_history": plh + nv * 8 + B * nv * 8 + 2 * vec64,
+    }
+
+
+def profiled_traffic(cls):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, if one exists and was taken from the current kernel sources
+    (its digest of csrc/*.cuh matches); else None."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2607_28309_b300", "csrc", "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"{cls}_cube64_a8.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("csrc digest") != digest:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------- native arm
 def native(args, ws, rank, local):
     import numpy as np
@@ -266,49 +344,46 @@ def native(args, ws, rank, local):
     for _ in range(args.warmup):
         mot.mot_run_step(krun, 1, None, kst, allow_notconv=True)
     kstats = []
+    ktimes = {}  # class -> [launches, total ms] over the timed steps
     for _ in range(max(5, min(K, 10))):
         mot.mot_run_step(krun, 1, None, kst, allow_notconv=True)
         s = kst[0]
         kstats.append((s.iters, s.sweeps, s.relres, s.mvps, s.ms_zhist, s.ms_zgreen, s.ms_history, s.ms_solve, s.ms_push))
+        for name, (n, ms) in mot.mot_run_kernel_times(krun).items():
+            acc = ktimes.setdefault(name, [0, 0.0])
+            acc[0] += n
+            acc[1] += n * ms
     k_n0 = mot.mot_run_step_index(krun) - len(kstats)
     mot.mot_run_destroy(krun)
     mot.mot_problem_destroy(kprob)
 
-    # ---- roofline of the dominant kernels (algorithmic bytes / event time)
-    # stats: (iters, sweeps, relres, mvps, ms_zhist, ms_zgreen, ms_history, ms_solve, ms_push)
-    cs = 8 if prec == mot.MOT_MIXED else 16       # complex element size
-    rs = 4 if prec == mot.MOT_MIXED else 8        # real element size
-    Mh, M0 = list(info.Mh), list(info.M0)
-    Hh, H0 = Mh[0] // 2 + 1, M0[0] // 2 + 1
-    Kh = [m // 2 + 1 for m in Mh]
+    # ---- roofline of the dominant kernel (algorithmic bytes / event time)
+    peak, peak_kind = _peaks()
+    nsteps_k = len(kstats)
+    kb = kernel_bytes(info, N, B, prec, [min(n, info.ell) for n in range(k_n0, k_n0 + nsteps_k)])
+    per_kernel = {}
+    for name, (n, tot) in ktimes.items():
+        if n == 0:
+            continue
+        mean_ms = tot / n
+        alg = kb[name]
+        per_kernel[name] = {"launches_per_step": n / nsteps_k, "ms_per_launch": mean_ms,
+                            "ms_per_step": tot / nsteps_k, "alg_bytes_per_launch": alg,
+                            "GBps": alg / (mean_ms / 1e3) / 1e9, "frac": alg / (mean_ms / 1e3) / 1e9 / peak}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
+    d = per_kernel[dom]
+    roofline = {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": d["GBps"], "peak": peak, "unit": "GB/s",
+                "frac": d["frac"], "traffic": profiled_traffic(dom), "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "launch_ms": d["ms_per_launch"], "kernel_ms_per_step": d["ms_per_step"],
+                "alg_bytes_per_launch": d["alg_bytes_per_launch"],
+                "timing": "CUDA events around every launch in a host-driven (no-graph) run of the same workload",
+                "kernels": per_kernel}
+    mvps = sum(s[3] for s in stats)
+    cs = 8 if prec == mot.MOT_MIXED else 16  # complex element of the FFT precision
+    M0, Mh = list(info.M0), list(info.Mh)
+    Hh = Mh[0] // 2 + 1
     K0 = [m // 2 + 1 for m in M0]
     ell = info.ell
-    lags = [min(n, ell) for n in range(k_n0, k_n0 + len(kstats))]
-    # history z pass: ring slots of kmax lags + each Lambda_k octant once + output planes
-    zh_bytes = sum(L * (B * 3 * Mh[2] * Mh[1] * Hh * cs + 6 * Kh[2] * Kh[1] * Hh * rs) + B * 3 * N[2] * Mh[1] * Hh * cs
-                   for L in lags)
-    zh_ms = sum(s[4] for s in kstats)
-    mvps = sum(s[3] for s in stats)
-    # Z0 spectral z pass: read + write the B*3*Nz*M0y*H0 planes, Lambda0 octant once
-    # (the step's first one runs in FP32 in the mixed path, FP64 in the FP64 path)
-    zg_bytes_one = 2 * B * 3 * N[2] * M0[1] * H0 * cs + 6 * K0[2] * K0[1] * H0 * rs
-    zg_ms_one = statistics.mean(s[5] for s in kstats)  # mean per timed launch
-    peak, peak_kind = _peaks()
-    zh_gbs = zh_bytes / (zh_ms / 1e3) / 1e9 if zh_ms > 0 else None
-    zg_gbs = zg_bytes_one / (zg_ms_one / 1e3) / 1e9 if zg_ms_one > 0 else None
-    share_zh = zh_ms / len(kstats)             # ms per step
-    share_zg = zg_ms_one * (mvps / K)          # ms per step over all products of the step
-    dominant = "k_z_history2" if share_zh >= share_zg else "k_z_green"
-    ach = zh_gbs if dominant == "k_z_history2" else zg_gbs
-    roofline = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": (ach / peak) if ach else None, "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                "kernel_ms_per_step": share_zh if dominant == "k_z_history2" else share_zg,
-                "launch_ms": share_zh if dominant == "k_z_history2" else zg_ms_one,
-                "alg_bytes_per_launch": (zh_bytes / len(kstats)) if dominant == "k_z_history2" else zg_bytes_one,
-                "timing": "CUDA events around each launch in a host-driven timed region of the same workload",
-                "other": {"k_z_green_GBps": zg_gbs, "k_z_green_ms_per_step": share_zg,
-                          "k_z_history2_GBps": zh_gbs, "k_z_history2_ms_per_step": share_zh}}
 
     # ---- Z0 product alone (FP32 and FP64), L2 flushed between calls
     mvp = {}

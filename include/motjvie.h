@@ -224,6 +224,31 @@ mot_status mot_kernel_launches(uint64_t *count);
 
 /* Index of the next step to be computed.                                       */
 mot_status mot_run_step_index(const mot_run *r, int64_t *n);
+
+/* Kernel classes timed by the timing option (mot_options.timing = 1 with
+ * graph = 0 or 2): CUDA events around every launch of these kernels during a
+ * step (kernels inside CUDA graphs cannot be bracketed).  Instrumentation; no
+ * counterpart in the paper.                                                    */
+typedef enum {
+    MOT_K_Z_GREEN = 0,      /* present-time z pass: FFT z, Lambda0 multiply, IFFT z (Eq. 11) */
+    MOT_K_Z_HISTORY = 1,    /* history z pass: sum_k Lambda_k Jhat_{n-k} and IFFT z (Eq. 3)  */
+    MOT_K_FWD_HALF = 2,     /* forward xy pass of Z0 y2 with the first TFQMR half step     */
+    MOT_K_FWD_Y1 = 3,       /* forward xy pass of Z0 y1 forming y1 = w + beta y2           */
+    MOT_K_FWD_PLAIN = 4,    /* forward xy pass of a stored vector (other Z0 products)     */
+    MOT_K_FWD_RING = 5,     /* forward xy pass of J_n into the history ring (Mh grid)      */
+    MOT_K_INV_HALF = 6,     /* inverse xy pass of Z0 y2 with the second TFQMR half step    */
+    MOT_K_INV_V = 7,        /* inverse xy pass of Z0 y1 with the v update                  */
+    MOT_K_INV_Z0 = 8,       /* inverse xy pass with the plain Z0 epilogue (Eq. 12)         */
+    MOT_K_INV_RESIDUAL = 9, /* inverse xy pass with the FP64 residual b - Z0 J            */
+    MOT_K_INV_HISTORY = 10, /* inverse xy pass of the history sum forming b_n (Eq. 3)     */
+    MOT_K_CLASSES = 11
+} mot_kernel_class;
+
+/* Timing-option results of the latest step of run r: the number of launches
+ * of class cls and their mean device time in ms (0 and 0 when none was timed).
+ * Synchronises the context stream.
+ * Errors: MOT_EINVAL (null argument, cls out of range), MOT_ECUDA.           */
+mot_status mot_run_kernel_times(mot_run *r, int cls, int32_t *launches, float *mean_ms);
 void mot_run_destroy(mot_run *r);
 
 #ifdef __cplusplus

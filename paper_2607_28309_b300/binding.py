@@ -34,7 +34,7 @@ __all__ = [
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
     "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
-    "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES",
+    "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
 ]
 
 # every symbol include/motjvie.h declares
@@ -42,8 +42,12 @@ EXPORTED = [
     "mot_last_error", "mot_ctx_create", "mot_ctx_destroy", "mot_problem_create", "mot_problem_info_get",
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
-    "mot_kernel_launches", "mot_apply_Z0_static",
+    "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times",
 ]
+
+# mot_kernel_class values, in order
+KERNEL_CLASSES = ["z_green", "z_history", "fwd_half", "fwd_y1", "fwd_plain", "fwd_ring", "inv_half", "inv_v",
+                  "inv_z0", "inv_residual", "inv_history"]
 
 
 class MotError(RuntimeError):
@@ -104,6 +108,7 @@ def lib():
         L.mot_run_current_device.argtypes = [P, PP]
         L.mot_run_step_index.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.mot_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.mot_run_kernel_times.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
         L.mot_run_destroy.argtypes = [P]
         L.mot_run_destroy.restype = None
         for name in EXPORTED:
@@ -238,6 +243,16 @@ def mot_run_step_index(run) -> int:
     n = ctypes.c_int64()
     _check(lib().mot_run_step_index(run, ctypes.byref(n)))
     return n.value
+
+
+def mot_run_kernel_times(run) -> dict:
+    """{class name: (launches, mean ms)} of the latest step (timing option)."""
+    out = {}
+    for i, name in enumerate(KERNEL_CLASSES):
+        n, ms = ctypes.c_int32(), ctypes.c_float()
+        _check(lib().mot_run_kernel_times(run, i, ctypes.byref(n), ctypes.byref(ms)))
+        out[name] = (n.value, ms.value)
+    return out
 
 
 def mot_kernel_launches() -> int:

@@ -305,7 +305,6 @@ struct KTimer {
         for (auto e : ev) cudaEventDestroy(e);
     }
 };
-enum { kTimeZGreen = 0, kTimeZHist = 1 };
 
 struct mot_problem {
     mot_ctx *ctx = nullptr;
@@ -343,6 +342,7 @@ struct mot_run {
     LoopGraph loop64, loop32;
     DBuf ctl;                    // device loop control: iteration count, cap, continue flag
     DBuf ctr;                    // last-block tickets of the fused TFQMR reduction kernels (0 between launches)
+    DBuf inctab;                 // axis tables of the fast incident path
     int B = 1;
     int prec = MOT_FP64;
     long n = 0;  // next step index
@@ -562,7 +562,7 @@ bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_
     if (smem > kSmemMax || allow_smem<k_z_green_r<T, R1, R2, TC>>() != MOT_OK) return false;
     Octant oc = {p->M0[2], My, p->K0[2], p->K0[1], H};
     dim3 grid((My * H + TC - 1) / TC, (unsigned)nrhs);
-    if (!p->capturing) p->kt.begin(st, kTimeZGreen);
+    if (!p->capturing) p->kt.begin(st, MOT_K_Z_GREEN);
     count_launch();
     k_z_green_r<T, R1, R2, TC><<<grid, 3 * TC * R2, smem, st>>>(Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H, oc);
     if (!p->capturing) p->kt.end(st);
@@ -616,6 +616,15 @@ template <typename T> const T *Lh_of(mot_problem *p);
 template <> const double *Lh_of<double>(mot_problem *p) { return (const double *)p->Lh_64.p; }
 template <> const float *Lh_of<float>(mot_problem *p) { return (const float *)p->Lh_32.p; }
 
+// timing-option class of a forward source / inverse epilogue
+template <class S> struct FwdClass { static constexpr int v = MOT_K_FWD_PLAIN; };
+template <typename V> struct FwdClass<SrcHalfA<V>> { static constexpr int v = MOT_K_FWD_HALF; };
+template <typename V> struct FwdClass<SrcY1<V>> { static constexpr int v = MOT_K_FWD_Y1; };
+template <class E> struct InvClass { static constexpr int v = MOT_K_INV_Z0; };
+template <typename V> struct InvClass<EpiHalfB<V>> { static constexpr int v = MOT_K_INV_HALF; };
+template <typename V> struct InvClass<EpiV<V>> { static constexpr int v = MOT_K_INV_V; };
+template <> struct InvClass<EpiResidual> { static constexpr int v = MOT_K_INV_RESIDUAL; };
+
 // true if the present-time xy passes run as one plane per block
 template <typename T> bool z0_planes_fit(const mot_problem *p) {
     return xy_smem_bytes<T>(p->M0[0], p->M0[1], p->H0, p->N[1]) <= kSmemMax;
@@ -638,7 +647,12 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
     const long nrows = (long)nrhs * 3 * Nz * Ny;
     const int planes = nrhs * 3 * Nz;
     const bool fused = z0_planes_fit<T>(p);
-    if (fused) MOT_TRY((launch_xy_forward<Src, T>(src, Bf, planes, Nx, Ny, H, tx, ty, st)));
+    const bool timed = !p->capturing;
+    if (fused) {
+        if (timed) p->kt.begin(st, FwdClass<Src>::v);
+        MOT_TRY((launch_xy_forward<Src, T>(src, Bf, planes, Nx, Ny, H, tx, ty, st)));
+        if (timed) p->kt.end(st);
+    }
     else if constexpr (Epi::kPlaneOnly) {
         MOT_FAIL(MOT_EUNSUPPORTED, "fused solver epilogue needs the plane passes");
     } else {
@@ -654,14 +668,17 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_TRY(allow_smem<k_z_green<T>>());
         Octant oc = {p->M0[2], p->M0[1], p->K0[2], p->K0[1], H};
         dim3 grid((H + tw - 1) / tw, (unsigned)(nrhs * My));
-        if (!p->capturing) p->kt.begin(st, kTimeZGreen);
+        if (!p->capturing) p->kt.begin(st, MOT_K_Z_GREEN);
         count_launch();
         k_z_green<T><<<grid, kZThreads, smem, st>>>(Bf, L0_of<T>(p), planp<T>(tz), twp<T>(tz), Nz, My, H, tw, oc);
         if (!p->capturing) p->kt.end(st);
         MOT_CHECK_LAUNCH();
     }
-    if (fused) MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
-    else if constexpr (!Epi::kPlaneOnly) {
+    if (fused) {
+        if (timed) p->kt.begin(st, InvClass<Epi>::v);
+        MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
+        if (timed) p->kt.end(st);
+    } else if constexpr (!Epi::kPlaneOnly) {
         MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
         MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
     }
@@ -1383,8 +1400,10 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
     C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
     const long nrows = (long)r->B * 3 * Nz * Ny;
     if (xy_smem_bytes<T>(p->Mh[0], My, H, Ny) <= kSmemMax) {
+        if (!p->capturing) p->kt.begin(st, MOT_K_FWD_RING);
         MOT_TRY((launch_xy_forward<SrcPlain<double>, T>(SrcPlain<double>{(const double *)r->J.p}, Bf, r->B * 3 * Nz, Nx,
                                                          Ny, H, tx, ty, st)));
+        if (!p->capturing) p->kt.end(st);
     } else {
         MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
@@ -1407,12 +1426,18 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
     C *A = (C *)r->wsAh.p, *Bf = (C *)r->wsBh.p;
     const double t = (double)r->n * p->dt;
     count_launch();
-    if (sizeof(T) == 4)
-        k_incident<true><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
-                                                             (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B,
-                                                             nptr, p->dt);
-    else
-        k_incident<false><<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
+    if (sizeof(T) == 4) {
+        const long S = (long)Nx + Ny + Nz;
+        const double *ts = (const double *)r->inctab.p;
+        const float2 *ph = (const float2 *)(ts + S * r->B);
+        const float *tsf = (const float *)(ph + S * r->B);
+        const dim3 grid((unsigned)std::min<long>((long)Ny * Nz, 8L * p->ctx->sms), (unsigned)r->B);
+        const int threads = std::min(256, (Nx + 31) / 32 * 32);
+        k_incident_rows<<<grid, threads, 0, st>>>((double *)r->inc.p, (const float *)p->eps32.p,
+                                                  (const PlaneWaveDev *)r->pw.p, ts, tsf, ph, Nx, Ny, Nz, t, nptr,
+                                                  p->dt);
+    } else
+        k_incident<<<grid_for(nv * r->B), 256, 0, st>>>((double *)r->inc.p, (const double *)p->eps.p,
                                                               (const PlaneWaveDev *)r->pw.p, Nx, Ny, Nz, p->h, t, r->B,
                                                               nptr, p->dt);
     MOT_CHECK_LAUNCH();
@@ -1425,7 +1450,7 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
         MOT_TRY(allow_smem<k_z_history2<T>>());
         Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
         dim3 grid((H + tw - 1) / tw, (unsigned)(r->B * (My / 2 + 1)));
-        if (!p->capturing) p->kt.begin(st, kTimeZHist);
+        if (!p->capturing) p->kt.begin(st, MOT_K_Z_HISTORY);
         count_launch();
         k_z_history2<T><<<grid, kZThreads, smem, st>>>((const C *)r->ring.p, Lh_of<T>(p), Bf, planp<T>(tz), twp<T>(tz), Nz, My,
                                                  H, tw, oc, r->B, p->ell, r->n, kmax, nptr);
@@ -1443,7 +1468,9 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
     e.nvox = nv;
     e.pol = (const double *)((const char *)r->pw.p + r->B * sizeof(PlaneWaveDev));
     if (xy_smem_bytes<T>(p->Mh[0], My, H, Ny) <= kSmemMax) {
+        if (!p->capturing) p->kt.begin(st, MOT_K_INV_HISTORY);
         MOT_TRY((launch_xy_inverse<T, EpiHistory>(Bf, r->B * 3 * Nz, Nx, Ny, Nz, H, tx, ty, e, st)));
+        if (!p->capturing) p->kt.end(st);
     } else {
         MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
         MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
@@ -1553,9 +1580,9 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         cudaEventElapsedTime(&stats->ms_solve, r->ev[1], r->ev[2]);
         cudaEventElapsedTime(&stats->ms_push, r->ev[2], r->ev[3]);
         stats->mvps = (int32_t)mvps;
-        stats->ms_zhist = p->kt.total(kTimeZHist);
-        const int ng = p->kt.count(kTimeZGreen);
-        stats->ms_zgreen = ng > 0 ? p->kt.total(kTimeZGreen) / ng : 0.f;
+        stats->ms_zhist = p->kt.total(MOT_K_Z_HISTORY);
+        const int ng = p->kt.count(MOT_K_Z_GREEN);
+        stats->ms_zgreen = ng > 0 ? p->kt.total(MOT_K_Z_GREEN) / ng : 0.f;
     }
     p->kt.on = false;
     r->n += 1;
@@ -1918,6 +1945,24 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
         r->pw_host[b] = d;
     }
     mot_status s;
+    {
+        // axis tables of the fast incident path: ts[B][S] doubles, ph[B][S] float2, tsf[B][S] floats
+        const long S = (long)p->N[0] + p->N[1] + p->N[2];
+        std::vector<double> ts(S * nrhs);
+        std::vector<float2> ph(S * nrhs);
+        std::vector<float> tsf(S * nrhs);
+        for (int b = 0; b < nrhs; ++b)
+            incident_tables(r->pw_host[b], p->N, p->h, ts.data() + b * S, tsf.data() + b * S, ph.data() + b * S);
+        if ((s = dalloc(r->inctab, (sizeof(double) + sizeof(float2) + sizeof(float)) * S * nrhs)) != MOT_OK)
+            return fail(s);
+        char *base = (char *)r->inctab.p;
+        if (cudaMemcpy(base, ts.data(), sizeof(double) * S * nrhs, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(base + sizeof(double) * S * nrhs, ph.data(), sizeof(float2) * S * nrhs,
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(base + (sizeof(double) + sizeof(float2)) * S * nrhs, tsf.data(), sizeof(float) * S * nrhs,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(MOT_ECUDA);
+    }
     if ((s = dalloc(r->pw, sizeof(PlaneWaveDev) * nrhs + sizeof(double) * 3 * nrhs)) != MOT_OK) return fail(s);
     cudaMemcpy(r->pw.p, r->pw_host.data(), sizeof(PlaneWaveDev) * nrhs, cudaMemcpyHostToDevice);
     cudaMemcpy((char *)r->pw.p + sizeof(PlaneWaveDev) * nrhs, pol.data(), sizeof(double) * 3 * nrhs,
@@ -2058,6 +2103,17 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     return result;
 }
 
+mot_status mot_run_kernel_times(mot_run *r, int cls, int32_t *launches, float *mean_ms) {
+    if (!r || !launches || !mean_ms) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (cls < 0 || cls >= MOT_K_CLASSES) MOT_FAIL(MOT_EINVAL, "kernel class out of range");
+    MOT_CUDA_TRY(cudaSetDevice(r->p->ctx->device));
+    MOT_CUDA_TRY(cudaStreamSynchronize(r->p->ctx->stream));
+    const int n = r->p->kt.count(cls);
+    *launches = n;
+    *mean_ms = n > 0 ? r->p->kt.total(cls) / n : 0.f;
+    return MOT_OK;
+}
+
 mot_status mot_run_current_device(mot_run *r, const void **J_dev) {
     if (!r || !J_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
     *J_dev = r->J.p;
@@ -2105,6 +2161,7 @@ void mot_run_destroy(mot_run *r) {
     }
     dfree(r->ctl);
     dfree(r->ctr);
+    dfree(r->inctab);
     if (r->step_exec) cudaGraphExecDestroy(r->step_exec);
     if (r->step_graph) cudaGraphDestroy(r->step_graph);
     dfree(r->sdev);

@@ -23,6 +23,32 @@ struct TfqmrScal {
     int conv;            // 1 once tau sqrt(m+1) <= tolabs (or b == 0)
     int pending;         // 1 if x += eta_prev d is still to be applied
     int pad;
+    // the vector-update coefficients rounded to FP32 once per scalar update,
+    // so FP32 kernels read them without FP64 arithmetic:
+    // alpha, theta^2 eta / alpha, eta_prev, beta
+    float f_alpha, f_coef, f_eta_prev, f_beta;
+};
+
+__host__ __device__ inline void refresh_coefs(TfqmrScal &s) {
+    s.f_alpha = (float)s.alpha;
+    s.f_coef = s.alpha != 0.0 ? (float)(s.theta * s.theta * s.eta / s.alpha) : 0.f;
+    s.f_eta_prev = (float)s.eta_prev;
+    s.f_beta = (float)s.beta;
+}
+
+// the coefficients of a vector update in the vector precision V
+template <typename V> struct Coefs;
+template <> struct Coefs<float> {
+    __device__ static float al(const TfqmrScal &s) { return s.f_alpha; }
+    __device__ static float coef(const TfqmrScal &s) { return s.f_coef; }
+    __device__ static float ep(const TfqmrScal &s) { return s.f_eta_prev; }
+    __device__ static float be(const TfqmrScal &s) { return s.f_beta; }
+};
+template <> struct Coefs<double> {
+    __device__ static double al(const TfqmrScal &s) { return s.alpha; }
+    __device__ static double coef(const TfqmrScal &s) { return s.theta * s.theta * s.eta / s.alpha; }
+    __device__ static double ep(const TfqmrScal &s) { return s.eta_prev; }
+    __device__ static double be(const TfqmrScal &s) { return s.beta; }
 };
 
 constexpr int kRedBlocks = 296;  // 2 x 148 SMs
@@ -44,10 +70,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the block, valid in thread 0: the warp sums in the accumulator
+// precision A, the sum of the warp sums in FP64
+template <typename A> __device__ __forceinline__ double block_sum(A v, double *sh) {
     v = warp_sum(v);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
+    if (lane == 0) sh[wid] = (double)v;
     __syncthreads();
     double r = 0.0;
     if (wid == 0) {
@@ -70,7 +103,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const TA *__restrict__
     A s = A(0);
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
         s += (A)pa[i] * (A)pc[i];
-    const double bs = block_sum((double)s, sh);
+    const double bs = block_sum(s, sh);
     if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
 }
 
@@ -103,6 +136,7 @@ __global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double 
         s.conv = b2 == 0.0 ? 3 : ((s.tau <= s.tolabs || r2 == 0.0) ? 1 : 0);
         s.pending = 0;
         s.pad = 0;
+        refresh_coefs(s);
         sc[b] = s;
     }
 }
@@ -127,7 +161,12 @@ __global__ void k_tfqmr_alpha(TfqmrScal *sc, const double *part) {
     double sigma = reduce_parts(part, b);
     if (threadIdx.x == 0 && !sc[b].conv) {
         if (sigma == 0.0) sc[b].conv = 2;  // breakdown: keep the current iterate
-        else sc[b].alpha = sc[b].rho / sigma;
+        else {
+            TfqmrScal u = sc[b];
+            u.alpha = u.rho / sigma;
+            refresh_coefs(u);
+            sc[b] = u;
+        }
     }
 }
 
@@ -166,6 +205,7 @@ __device__ __forceinline__ void half_scalars(TfqmrScal &s, double w2) {
     s.pending = 1;
     s.m += 1;
     if (s.tau * sqrt((double)s.m + 1.0) <= s.tolabs) s.conv = 2;
+    refresh_coefs(s);
 }
 
 // first half step of an iteration, on (y1, Ay1):
@@ -183,9 +223,9 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_a(V *__restrict__ x,
     const TfqmrScal s = sc[b];
     A w2 = A(0);
     if (!s.conv) {
-        const V al = (V)s.alpha;
-        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
-        const V ep = (V)s.eta_prev;
+        const V al = Coefs<V>::al(s);
+        const V coef = Coefs<V>::coef(s);
+        const V ep = Coefs<V>::ep(s);
         const long o = (long)b * L;
         constexpr int W = PackW<V>::W;
         const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
@@ -223,7 +263,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_a(V *__restrict__ x,
             w2 += wn * wn;
         }
     }
-    const double bs = block_sum((double)w2, sh);
+    const double bs = block_sum(w2, sh);
     if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
     if (!last_block(ctr, gridDim.x * gridDim.y)) return;
     const int lane = threadIdx.x & 31;
@@ -253,9 +293,9 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x,
     const TfqmrScal s = sc[b];
     A w2 = A(0), rw = A(0);
     if (!s.conv) {
-        const V al = (V)s.alpha;
-        const V coef = (V)(s.theta * s.theta * s.eta / s.alpha);
-        const V ep = (V)s.eta_prev;
+        const V al = Coefs<V>::al(s);
+        const V coef = Coefs<V>::coef(s);
+        const V ep = Coefs<V>::ep(s);
         const long o = (long)b * L;
         constexpr int W = PackW<V>::W;
         const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
@@ -292,8 +332,8 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x,
             rw += rs[o + i] * wn;
         }
     }
-    const double bw = block_sum((double)w2, sh);
-    const double br = block_sum((double)rw, sh);
+    const double bw = block_sum(w2, sh);
+    const double br = block_sum(rw, sh);
     if (threadIdx.x == 0) {
         part_w2[b * kRedBlocks + blockIdx.x] = bw;
         part_rw[b * kRedBlocks + blockIdx.x] = br;
@@ -311,6 +351,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_half_b(V *__restrict__ x,
                 else {
                     u.beta = rn / u.rho;
                     u.rho = rn;
+                    refresh_coefs(u);
                 }
             }
             sc[bb] = u;
@@ -325,7 +366,7 @@ __global__ void k_tfqmr_y1(V *__restrict__ y1, const V *__restrict__ w, const V 
                            const TfqmrScal *__restrict__ sc, long L) {
     const int b = blockIdx.y;
     if (sc[b].conv) return;
-    const V be = (V)sc[b].beta;
+    const V be = Coefs<V>::be(sc[b]);
     const long o = (long)b * L;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
         y1[o + i] = w[o + i] + be * y2[o + i];
@@ -375,7 +416,7 @@ template <typename V> struct SrcY1 {
     __device__ __forceinline__ Plane bind(long plane, long plane_size) const {
         const long off = plane * plane_size;
         const int b = (int)(off / L);
-        return Plane{y1 + off, w + off, y2 + off, (V)sc[b].beta, sc[b].conv != 0};
+        return Plane{y1 + off, w + off, y2 + off, Coefs<V>::be(sc[b]), sc[b].conv != 0};
     }
     __device__ __forceinline__ void finish(const Plane &, long, long) const {}
 };
@@ -398,8 +439,8 @@ __device__ __forceinline__ double reduce_parts_n(const double *part, int b, int 
 }
 
 // block sums of NV thread values into part[k][slot]; true in the last block
-template <int NV>
-__device__ __forceinline__ bool plane_block_done(const double (&v)[NV], double *const (&part)[NV], long slot,
+template <int NV, typename A>
+__device__ __forceinline__ bool plane_block_done(const A (&v)[NV], double *const (&part)[NV], long slot,
                                                  unsigned *ctr) {
     __shared__ double sh[32];
 #pragma unroll
@@ -482,15 +523,15 @@ template <typename V> struct SrcHalfA {
         Plane p{x + off, w + off, d + off, y2 + off, y1 + off, Ay1 + off, v + off, V(0), V(0), V(0),
                 s.pending, s.conv != 0, 0};
         if (!p.skip) {
-            p.al = (V)s.alpha;
-            p.coef = (V)(s.theta * s.theta * s.eta / s.alpha);
-            p.ep = (V)s.eta_prev;
+            p.al = Coefs<V>::al(s);
+            p.coef = Coefs<V>::coef(s);
+            p.ep = Coefs<V>::ep(s);
         }
         return p;
     }
     __device__ __forceinline__ void finish(const Plane &pl, long plane, long plane_size) const {
         const int b = (int)(plane * plane_size / L);
-        const double vals[1] = {(double)pl.w2};
+        const typename AccOf<V>::type vals[1] = {pl.w2};
         double *const parts[1] = {part};
         if (!plane_block_done<1>(vals, parts, (long)b * P + (plane - (long)b * P), ctr)) return;
         const int lane = threadIdx.x & 31, B = (int)(gridDim.x / P);
@@ -572,15 +613,15 @@ template <typename V> struct EpiHalfB {
         Plane p{y2 + off, Ay2 + off, eps + zoff, x + off, w + off, d + off, rs + off, V(0), V(0), V(0),
                 s.pending, s.conv != 0, 0, 0};
         if (!p.skip) {
-            p.al = (V)s.alpha;
-            p.coef = (V)(s.theta * s.theta * s.eta / s.alpha);
-            p.ep = (V)s.eta_prev;
+            p.al = Coefs<V>::al(s);
+            p.coef = Coefs<V>::coef(s);
+            p.ep = Coefs<V>::ep(s);
         }
         return p;
     }
     __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
         const int b = (int)(plane / P);
-        const double vals[2] = {(double)pl.w2, (double)pl.rw};
+        const typename AccOf<V>::type vals[2] = {pl.w2, pl.rw};
         double *const parts[2] = {part_w2, part_rw};
         if (!plane_block_done<2>(vals, parts, plane, ctr)) return;
         const int lane = threadIdx.x & 31, B = (int)(gridDim.x / P);
@@ -596,6 +637,7 @@ template <typename V> struct EpiHalfB {
                     else {
                         u.beta = rn / u.rho;
                         u.rho = rn;
+                        refresh_coefs(u);
                     }
                 }
                 sc[bb] = u;
@@ -662,11 +704,11 @@ template <typename V> struct EpiV {
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
         const TfqmrScal s = sc[(int)(plane / P)];
-        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, (V)s.beta, s.conv != 0, 0};
+        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, Coefs<V>::be(s), s.conv != 0, 0};
     }
     __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
         __shared__ int active;
-        const double vals[1] = {(double)pl.acc};
+        const typename AccOf<V>::type vals[1] = {pl.acc};
         double *const parts[1] = {part};
         if (!plane_block_done<1>(vals, parts, plane, ctr)) return;
         if (threadIdx.x == 0) active = 0;
@@ -675,11 +717,16 @@ template <typename V> struct EpiV {
         for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
             const double sigma = reduce_parts_n(part, bb, lane, P);
             if (lane == 0) {
-                if (!sc[bb].conv) {
-                    if (sigma == 0.0) sc[bb].conv = 2;
-                    else sc[bb].alpha = sc[bb].rho / sigma;
+                TfqmrScal u = sc[bb];
+                if (!u.conv) {
+                    if (sigma == 0.0) u.conv = 2;
+                    else {
+                        u.alpha = u.rho / sigma;
+                        refresh_coefs(u);
+                    }
+                    sc[bb] = u;
                 }
-                if (sc[bb].conv == 0) active = 1;
+                if (u.conv == 0) active = 1;
             }
         }
         __syncthreads();
@@ -711,7 +758,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, cons
     const int b = blockIdx.y;
     A acc = A(0);
     if (!sc[b].conv) {
-        const V be = (V)sc[b].beta;
+        const V be = Coefs<V>::be(sc[b]);
         const long o = (long)b * L;
         constexpr int W = PackW<V>::W;
         const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
@@ -737,7 +784,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, cons
             acc += rs[o + i] * vn;
         }
     }
-    const double bs = block_sum((double)acc, sh);
+    const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
     if (!last_block(ctr, gridDim.x * gridDim.y)) return;
     if (threadIdx.x == 0) active = 0;
@@ -746,11 +793,16 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_v(V *__restrict__ v, cons
     for (int bb = threadIdx.x >> 5; bb < (int)gridDim.y; bb += blockDim.x >> 5) {
         const double sigma = reduce_parts_lane(part, bb, lane);
         if (lane == 0) {
-            if (!sc[bb].conv) {
-                if (sigma == 0.0) sc[bb].conv = 2;
-                else sc[bb].alpha = sc[bb].rho / sigma;
+            TfqmrScal u = sc[bb];
+            if (!u.conv) {
+                if (sigma == 0.0) u.conv = 2;
+                else {
+                    u.alpha = u.rho / sigma;
+                    refresh_coefs(u);
+                }
+                sc[bb] = u;
             }
-            if (sc[bb].conv == 0) active = 1;
+            if (u.conv == 0) active = 1;
         }
     }
     __syncthreads();
@@ -842,7 +894,13 @@ struct PlaneWaveDev {
     //   E(tau) = exp(-tau^2/(2 sigma^2) + i w tau), C(s) = exp(-delta^2/(2 sigma^2) - i w delta).
     double beta[3];
     double Cre[8], Cim[8], delta[8];
-    float delta_over_sigma[8];  // delta(s) / sigma for the FP32 path
+    // FP32 copies for the fast path: delta(s)/sigma, C(s), beta_i/sigma, w sigma,
+    // and the FP64 scale eps0 (1/(sigma sqrt(2 pi))) E0 (1/8) / sigma
+    float delta_over_sigma[8];
+    float f_Cre[8], f_Cim[8];
+    float f_beta_over_sigma[3];
+    float f_w_sigma;
+    double fast_scale;
 };
 
 // host: fill beta, C(s), delta(s) of a plane wave for voxel size h
@@ -859,15 +917,94 @@ inline void planewave_factors(PlaneWaveDev &P, double h) {
         P.Cim[q] = -mag * sin(w * d);
         P.delta[q] = d;
         P.delta_over_sigma[q] = (float)(d / P.sigma);
+        P.f_Cre[q] = (float)P.Cre[q];
+        P.f_Cim[q] = (float)P.Cim[q];
+    }
+    for (int i = 0; i < 3; ++i) P.f_beta_over_sigma[i] = (float)(P.beta[i] / P.sigma);
+    P.f_w_sigma = (float)(w * P.sigma);
+    const double eps0 = 8.8541878128e-12;
+    P.fast_scale = eps0 * P.E0 / (P.sigma * 2.5066282746310005024) * 0.125 / P.sigma;
+}
+
+// Per-axis tables of the fast incident path, per plane wave b (S = Nx+Ny+Nz
+// entries, x then y then z): time offsets s_i(m) = -khat_i ((m + 1/2) h -
+// rref_i) / c0 in FP64 and FP32, and phase factors exp(i w s_i(m)) in FP32, so
+// that tau_c = (t - t0) + s_x + s_y + s_z and exp(i w tau_c) is a product of
+// table entries.  Layout: ts[B][S] doubles, tsf[B][S] floats, ph[B][S] float2.
+inline void incident_tables(const PlaneWaveDev &P, const int N[3], double h, double *ts, float *tsf, float2 *ph) {
+    const double c0 = 299792458.0, w = 2.0 * 3.141592653589793238462643 * P.f0;
+    int o = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int m = 0; m < N[i]; ++m, ++o) {
+            const double sv = -P.khat[i] * ((m + 0.5) * h - P.rref[i]) / c0;
+            ts[o] = sv;
+            tsf[o] = (float)sv;
+            ph[o] = make_float2((float)cos(w * sv), (float)sin(w * sv));
+        }
+}
+
+// fast incident right-hand side (mixed-precision path): one block row per
+// (z, y) line of plane wave blockIdx.y; the FP64 work is the line's time
+// (t - t0) + s_y + s_z and exp(i w (t - t0)) once per block; per voxel only
+// FP32.  inc as k_incident (FP64 storage).
+__global__ void k_incident_rows(double *__restrict__ inc, const float *__restrict__ eps32,
+                                const PlaneWaveDev *__restrict__ pw, const double *__restrict__ ts,
+                                const float *__restrict__ tsf, const float2 *__restrict__ ph, int Nx, int Ny, int Nz,
+                                double t, const long long *__restrict__ nptr, double dt) {
+    if (nptr) t = (double)(*nptr) * dt;
+    const int b = blockIdx.y, S = Nx + Ny + Nz;
+    const PlaneWaveDev &P = pw[b];
+    const double *sy = ts + (long)b * S + Nx, *sz = sy + Ny;
+    const float *sxf = tsf + (long)b * S;
+    const float2 *px = ph + (long)b * S, *py = px + Nx, *pz = py + Ny;
+    const double T = t - P.t0;
+    __shared__ float2 pt;
+    if (threadIdx.x == 0) {
+        double sn, cs;
+        sincos(2.0 * 3.141592653589793238462643 * P.f0 * T, &sn, &cs);
+        pt = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    const float is = (float)(1.0 / P.sigma), ws = P.f_w_sigma;
+    const long nv = (long)Nx * Ny * Nz;
+    for (int row = blockIdx.x; row < Ny * Nz; row += gridDim.x) {
+        const int z = row / Ny, y = row - z * Ny;
+        const float trow = (float)(T + sy[y] + sz[z]);
+        const float2 a = py[y], c = pz[z];
+        const float2 yz = make_float2(a.x * c.x - a.y * c.y, a.x * c.y + a.y * c.x);
+        const float2 pr = make_float2(pt.x * yz.x - pt.y * yz.y, pt.x * yz.y + pt.y * yz.x);
+        for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+            const long m = (long)row * Nx + x;
+            const float e = eps32[m];
+            double out = 0.0;
+            if (e != 1.f) {
+                const float tcs = (trow + sxf[x]) * is;  // tau_c / sigma
+                const float2 q = px[x];
+                const float g = expf(-0.5f * tcs * tcs);
+                const float Er = g * (pr.x * q.x - pr.y * q.y), Ei = g * (pr.x * q.y + pr.y * q.x);
+                const float a0 = P.f_beta_over_sigma[0] * tcs, a1 = P.f_beta_over_sigma[1] * tcs,
+                            a2 = P.f_beta_over_sigma[2] * tcs;
+                const float u0 = expf(a0), u1 = expf(a1), u2 = expf(a2);
+                const float v0 = 1.f / u0, v1 = 1.f / u1, v2 = 1.f / u2;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float f = ((k & 1) ? u0 : v0) * ((k & 2) ? u1 : v1) * ((k & 4) ? u2 : v2);
+                    const float zr = f * (Er * P.f_Cre[k] - Ei * P.f_Cim[k]);
+                    const float zi = f * (Er * P.f_Cim[k] + Ei * P.f_Cre[k]);
+                    acc += -(tcs - P.delta_over_sigma[k]) * zr - ws * zi;
+                }
+                out = (double)((e - 1.f) * acc) * P.fast_scale;
+            }
+            inc[(long)b * nv + m] = out;
+        }
     }
 }
 
 // inc[b][m] = (eps_r(m) - 1) eps0 E0 (1/8) sum_s g'(tau_c - delta(s)),
-// g'(tau) = Re[(-tau/sigma^2 + i w) E(tau)] / (sigma sqrt(2 pi))
-// FAST: transcendentals in FP32 after an FP64 reduction of the phase to
-// [-pi, pi] (relative error ~1e-7, used by the mixed-precision path); else FP64.
+// g'(tau) = Re[(-tau/sigma^2 + i w) E(tau)] / (sigma sqrt(2 pi)), all FP64
+// (the FP64 path; k_incident_rows is the mixed path's FP32 form).
 // nptr (graph mode): t = (*nptr) * dt instead of the argument t
-template <bool FAST>
 __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ eps,
                            const PlaneWaveDev *__restrict__ pw, int Nx, int Ny, int Nz, double h, double t,
                            int nrhs, const long long *__restrict__ nptr, double dt) {
@@ -886,34 +1023,7 @@ __global__ void k_incident(double *__restrict__ inc, const double *__restrict__ 
         double rx = (mx + 0.5) * h - P.rref[0], ry = (my + 0.5) * h - P.rref[1], rz = (mz + 0.5) * h - P.rref[2];
         double tc = t - P.t0 - (P.khat[0] * rx + P.khat[1] * ry + P.khat[2] * rz) / c0;
         double acc;
-        if (FAST) {
-            // phase reduced to [-pi, pi] in FP64, the rest in FP32 (relative error ~1e-7)
-            const double twopi = 6.283185307179586476925287;
-            double ph = w * tc;
-            ph -= twopi * rint(ph / twopi);
-            float sf, cf;
-            sincosf((float)ph, &sf, &cf);
-            const float g = expf((float)(-0.5 * tc * tc * is2));
-            const float Er = g * cf, Ei = g * sf;
-            const float a0 = (float)(P.beta[0] * tc * is2), a1 = (float)(P.beta[1] * tc * is2),
-                        a2 = (float)(P.beta[2] * tc * is2);
-            const float u0 = expf(a0), u1 = expf(a1), u2 = expf(a2);
-            const float v0 = expf(-a0), v1 = expf(-a1), v2 = expf(-a2);
-            const float tcs = (float)(tc / P.sigma);  // tau_c / sigma
-            const float ws = (float)(w * P.sigma);
-            float accf = 0.f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float f = ((q & 1) ? u0 : v0) * ((q & 2) ? u1 : v1) * ((q & 4) ? u2 : v2);
-                const float cr = (float)P.Cre[q], ci = (float)P.Cim[q];
-                const float zr = f * (Er * cr - Ei * ci);
-                const float zi = f * (Er * ci + Ei * cr);
-                // scaled by sigma: (-tau/sigma^2) sigma = -tau/sigma, w sigma
-                const float tau_s = tcs - P.delta_over_sigma[q];
-                accf += -tau_s * zr - ws * zi;
-            }
-            acc = (double)accf / P.sigma;
-        } else {
+        {
             double s, c;
             sincos(w * tc, &s, &c);
             double g = exp(-0.5 * tc * tc * is2);
