@@ -135,19 +135,10 @@ class ClockSampler:
 def workload(name: str):
     from paper_2607_28309_b300 import synthetic
 
-    if name == "cube64_a8":
-        return synthetic.cube64(8.0)
-    if name == "cube64_a16":
-        return synthetic.cube64(16.0)
-    if name == "cube64_a4":
-        return synthetic.cube64(4.0)
-    if name == "cube16_a4":
-        return synthetic.cube16()
-    if name == "cube64_b16":
-        return synthetic.cube64_batch16()
-    if name == "pillars8x8":
-        return synthetic.pillars8x8()
-    raise SystemExit(f"unknown workload {name}")
+    try:
+        return synthetic.workload(name)
+    except ValueError as e:
+        raise SystemExit(str(e))
 
 
 def describe(w, precision):
@@ -434,6 +425,21 @@ def native(args, ws, rank, local):
         except Exception as e:  # reported, not fatal
             compare[label] = {"error": str(e)[:200]}
 
+    # ---- the Z0 product alone on the 60%-of-HBM target workloads: the
+    # 16-excitation cube (72^3 grid) and the 256x256x80 pillar array
+    targets = {}
+    if not args.no_targets:
+        from paper_2607_28309_b300 import mvp_bench
+
+        for label, wl, nr, dtn in (("cube64_b16_f32", "cube64_b16", 16, "f32"), ("pillars8x8_f32", "pillars8x8", 1, "f32"),
+                                   ("cube64_b16_f64", "cube64_b16", 16, "f64"), ("pillars8x8_f64", "pillars8x8", 1, "f64")):
+            try:
+                r_ = mvp_bench.run(wl, nr, dtn, warmup=3, reps=10, device=local)
+                targets[label] = {k: r_[k] for k in ("us_median", "alg_bytes", "pass_bytes", "alg_GBps", "pass_GBps",
+                                                     "pass_frac", "M0", "nrhs") if k in r_}
+            except Exception as e:  # reported, not fatal
+                targets[label] = {"error": str(e)[:200]}
+
     # ---- e2e: public API from host buffers, one call per step with a host J_n
     e2e = end_to_end(mot, ctx, w, prec, K, stream, gopt)
 
@@ -457,7 +463,7 @@ def native(args, ws, rank, local):
         "step_device_ms": statistics.mean(s[7] for s in stats),
         "same_gpu": compare,
         "setup_s": t_setup,
-        "z0_mvp": mvp, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "z0_mvp": mvp, "z0_mvp_targets": targets, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
     }
     return res, w, mvps / K
 
@@ -563,6 +569,7 @@ def main():
     ap.add_argument("--workload", default="cube64_a8")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-targets", action="store_true", help="skip the Z0 product timings on cube64_b16 and pillars8x8")
     ap.add_argument("--graph-mode", default="step", choices=list(GRAPH_MODES),
                     help="step: one CUDA graph per MOT step (default); loop: host-driven steps, one graph per TFQMR "
                          "loop; none: no CUDA graphs (for per-kernel profilers)")

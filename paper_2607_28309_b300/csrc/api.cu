@@ -521,6 +521,78 @@ bool xy_inverse_r(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw 
     }
 }
 
+// specialised row / column passes for the compiled lengths of planes too
+// large for shared memory; false -> generic
+template <typename TI, typename T, int R1, int R2, int P>
+bool x_forward_r_go(const TI *x, cplx<T> *out, long nrows, int Nx, AxisTw *tw, cudaStream_t st) {
+    constexpr int M = R1 * R2;
+    const size_t smem = (size_t)(M + 2 * P * (M + 2)) * sizeof(cplx<T>);
+    if (smem > kSmemMax || allow_smem<k_x_forward_r<TI, T, R1, R2, P>>() != MOT_OK) return false;
+    count_launch();
+    k_x_forward_r<TI, T, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(x, out, Nx, twp<T>(tw));
+    return true;
+}
+
+template <typename T, class Epi, int R1, int R2, int P>
+bool x_inverse_r_go(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *tw, Epi epi, cudaStream_t st) {
+    constexpr int M = R1 * R2;
+    const size_t smem = (size_t)(M + 2 * P * (M + 2)) * sizeof(cplx<T>);
+    if (smem > kSmemMax || allow_smem<k_x_inverse_r<T, Epi, R1, R2, P>>() != MOT_OK) return false;
+    count_launch();
+    k_x_inverse_r<T, Epi, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(in, Nx, Ny, Nz, twp<T>(tw),
+                                                                                        epi);
+    return true;
+}
+
+template <typename T, int S, int R1, int R2, int TC>
+bool col_r_go(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int planes, long ips, long ops,
+              cudaStream_t st) {
+    constexpr int M = R1 * R2;
+    const size_t smem = (size_t)(M + TC * (M + 1)) * sizeof(cplx<T>);
+    if (smem > kSmemMax || allow_smem<k_col_r<T, S, R1, R2, TC>>() != MOT_OK) return false;
+    count_launch();
+    k_col_r<T, S, R1, R2, TC><<<dim3((H + TC - 1) / TC, planes), TC * R2, smem, st>>>(in, out, twp<T>(tw), H, Lin, Lout,
+                                                                                      ips, ops);
+    return true;
+}
+
+// rows per block 2P: the largest of 32, 16, 8 dividing Ny (blocks stay inside one plane)
+template <typename TI, typename T>
+bool x_forward_r(const TI *x, cplx<T> *out, long nrows, int Nx, int Ny, AxisTw *tw, cudaStream_t st) {
+    if (specialised_off()) return false;
+    switch (tw->M) {
+        case 270:
+            if (Ny % 32 == 0) return x_forward_r_go<TI, T, 15, 18, 16>(x, out, nrows, Nx, tw, st);
+            if (Ny % 16 == 0) return x_forward_r_go<TI, T, 15, 18, 8>(x, out, nrows, Nx, tw, st);
+            if (Ny % 8 == 0) return x_forward_r_go<TI, T, 15, 18, 4>(x, out, nrows, Nx, tw, st);
+            return false;
+        default: return false;
+    }
+}
+
+template <typename T, class Epi>
+bool x_inverse_r(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *tw, Epi epi, cudaStream_t st) {
+    if (specialised_off()) return false;
+    switch (tw->M) {
+        case 270:
+            if (Ny % 32 == 0) return x_inverse_r_go<T, Epi, 15, 18, 16>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+            if (Ny % 16 == 0) return x_inverse_r_go<T, Epi, 15, 18, 8>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+            if (Ny % 8 == 0) return x_inverse_r_go<T, Epi, 15, 18, 4>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+            return false;
+        default: return false;
+    }
+}
+
+template <typename T, int S>
+bool col_r(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int planes, long ips, long ops,
+           cudaStream_t st) {
+    if (specialised_off()) return false;
+    switch (tw->M) {
+        case 270: return col_r_go<T, S, 15, 18, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
+        default: return false;
+    }
+}
+
 template <class Src, typename T>
 mot_status launch_xy_forward(Src x, cplx<T> *out, int planes, int Nx, int Ny, int H, AxisTw *tx, AxisTw *ty,
                              cudaStream_t st) {
@@ -599,7 +671,9 @@ template <typename T> bool launch_z_green_r(mot_problem *p, cplx<T> *Bf, AxisTw 
         case 32: return z_green_r_go<T, 8, 4>(p, Bf, tz, nrhs, st);
         case 64: return z_green_r_go<T, 8, 8>(p, Bf, tz, nrhs, st);
         case 72: return z_green_r_go<T, 9, 8>(p, Bf, tz, nrhs, st);
+        case 75: return z_green_r_go<T, 5, 15>(p, Bf, tz, nrhs, st);
         case 80: return z_green_r_go<T, 5, 16>(p, Bf, tz, nrhs, st);
+        case 90: return z_green_r_go<T, 9, 10>(p, Bf, tz, nrhs, st);
         case 128: return z_green_r_go<T, 16, 8>(p, Bf, tz, nrhs, st);
         default: return false;
     }
@@ -657,8 +731,10 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_FAIL(MOT_EUNSUPPORTED, "fused solver epilogue needs the plane passes");
     } else {
         if (!plain) MOT_FAIL(MOT_EUNSUPPORTED, "row-pass product needs a stored input vector");
-        MOT_TRY(launch_x_forward<TI, T>(plain, A, nrows, Nx, H, tx, st));
-        MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+        if (x_forward_r<TI, T>(plain, A, nrows, Nx, Ny, tx, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY(launch_x_forward<TI, T>(plain, A, nrows, Nx, H, tx, st));
+        if (col_r<T, -1>(A, Bf, ty, H, Ny, My, planes, (long)Ny * H, (long)My * H, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
     }
     if (launch_z_green_r<T>(p, Bf, tz, nrhs, st)) {
         MOT_CHECK_LAUNCH();
@@ -679,8 +755,10 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
         if (timed) p->kt.end(st);
     } else if constexpr (!Epi::kPlaneOnly) {
-        MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
-        MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
+        if (col_r<T, +1>(Bf, A, ty, H, My, Ny, planes, (long)My * H, (long)Ny * H, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+        if (x_inverse_r<T, Epi>(A, nrows, Nx, Ny, Nz, tx, epi, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
     }
     return MOT_OK;
 }

@@ -159,6 +159,28 @@ template <> struct Root<9> {
     }
 };
 
+template <> struct Root<10> {
+    // cos / sin of 2 pi j / 10 for j = 0..5; the rest by j -> 10 - j symmetry
+    __host__ __device__ static constexpr double ch(int k) { return k == 0 ? 1.000000000000000000000 : k == 1 ? 0.8090169943749474241023 : k == 2 ? 0.3090169943749474241023 : k == 3 ? -0.3090169943749474241023 : k == 4 ? -0.8090169943749474241023 : -1.000000000000000000000; }
+    __host__ __device__ static constexpr double sh(int k) { return k == 0 ? 0.0 : k == 1 ? 0.5877852522924731291687 : k == 2 ? 0.9510565162951535721164 : k == 3 ? 0.9510565162951535721164 : k == 4 ? 0.5877852522924731291687 : 0.0; }
+    __host__ __device__ static constexpr double c(int j) { return ch((j % 10) <= 5 ? j % 10 : 10 - j % 10); }
+    __host__ __device__ static constexpr double s(int j) { return (j % 10) <= 5 ? sh(j % 10) : -sh(10 - j % 10); }
+};
+template <> struct Root<15> {
+    // cos / sin of 2 pi j / 15 for j = 0..7; the rest by j -> 15 - j symmetry
+    __host__ __device__ static constexpr double ch(int k) { return k == 0 ? 1.000000000000000000000 : k == 1 ? 0.9135454576426008955021 : k == 2 ? 0.6691306063588582138263 : k == 3 ? 0.3090169943749474241023 : k == 4 ? -0.1045284632676534713998 : k == 5 ? -0.5000000000000000000000 : k == 6 ? -0.8090169943749474241023 : -0.9781476007338056379286; }
+    __host__ __device__ static constexpr double sh(int k) { return k == 0 ? 0.0 : k == 1 ? 0.4067366430758002077540 : k == 2 ? 0.7431448254773942350147 : k == 3 ? 0.9510565162951535721164 : k == 4 ? 0.9945218953682733369227 : k == 5 ? 0.8660254037844386467637 : k == 6 ? 0.5877852522924731291687 : 0.2079116908177593371017; }
+    __host__ __device__ static constexpr double c(int j) { return ch((j % 15) <= 7 ? j % 15 : 15 - j % 15); }
+    __host__ __device__ static constexpr double s(int j) { return (j % 15) <= 7 ? sh(j % 15) : -sh(15 - j % 15); }
+};
+template <> struct Root<18> {
+    // cos / sin of 2 pi j / 18 for j = 0..9; the rest by j -> 18 - j symmetry
+    __host__ __device__ static constexpr double ch(int k) { return k == 0 ? 1.000000000000000000000 : k == 1 ? 0.9396926207859083840541 : k == 2 ? 0.7660444431189780352024 : k == 3 ? 0.5000000000000000000000 : k == 4 ? 0.1736481776669303488517 : k == 5 ? -0.1736481776669303488517 : k == 6 ? -0.5000000000000000000000 : k == 7 ? -0.7660444431189780352024 : k == 8 ? -0.9396926207859083840541 : -1.000000000000000000000; }
+    __host__ __device__ static constexpr double sh(int k) { return k == 0 ? 0.0 : k == 1 ? 0.3420201433256687330441 : k == 2 ? 0.6427876096865393263226 : k == 3 ? 0.8660254037844386467637 : k == 4 ? 0.9848077530122080593667 : k == 5 ? 0.9848077530122080593667 : k == 6 ? 0.8660254037844386467637 : k == 7 ? 0.6427876096865393263226 : k == 8 ? 0.3420201433256687330441 : 0.0; }
+    __host__ __device__ static constexpr double c(int j) { return ch((j % 18) <= 9 ? j % 18 : 18 - j % 18); }
+    __host__ __device__ static constexpr double s(int j) { return (j % 18) <= 9 ? sh(j % 18) : -sh(18 - j % 18); }
+};
+
 template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C *v);
 
 // N1 x N2 Cooley-Tukey in registers: x[t + N2 m] -> DFT_N1 over m, twiddle
@@ -202,7 +224,11 @@ template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C 
     else if constexpr (N == 5) dft5<S>(v);
     else if constexpr (N == 8) dft_nested<4, 2, S>(v);
     else if constexpr (N == 9) dft_nested<3, 3, S>(v);
+    else if constexpr (N == 10) dft_nested<5, 2, S>(v);
+    else if constexpr (N == 15) dft_nested<5, 3, S>(v);
     else if constexpr (N == 16) dft_nested<4, 4, S>(v);
+    else if constexpr (N == 18) dft_nested<9, 2, S>(v);
+    else static_assert(N == 1, "no register DFT of this length");
 }
 
 // one Stockham stage over nb pencils; src/dst share the (ps, es) layout.

@@ -878,6 +878,209 @@ __global__ void __launch_bounds__(256) k_x_inverse(const cplx<T> *__restrict__ i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row and column passes specialised for a compile-time length M = R1 * R2,
+// for planes too large for shared memory (the 270-point planes of the
+// 256 x 256 pillar grid).  Register DFTs of R1 points per thread and R2 per
+// task, one shared-memory exchange, as in the specialised plane kernels.
+// ---------------------------------------------------------------------------
+
+// forward x pass: a block takes 2P consecutive rows of one (b, q, z) plane
+// (2P divides Ny), stages them with 16-byte loads, transforms the P row pairs
+// as complex sequences of length M (zero padded from Nx) and writes both rows'
+// half spectra, k < H, k fastest.  grid = nrows / (2P); block = P * R2;
+// smem = (M + 2 P (M + 2)) complex
+template <typename TI, typename T, int R1, int R2, int P>
+__global__ void __launch_bounds__(P * R2) k_x_forward_r(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
+                                                        const cplx<T> *__restrict__ tw_g) {
+    using C = cplx<T>;
+    constexpr int M = R1 * R2, H = M / 2 + 1, RS = M + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *A = tw + M;       // [P][RS]
+    C *Bf = A + P * RS;  // [P][RS]; first holds the staged 2P*Nx inputs
+    load_twiddles(tw, tw_g, M);
+    const long row0 = (long)blockIdx.x * 2 * P;
+    T *stg = reinterpret_cast<T *>(Bf);
+    const int n = 2 * P * Nx;
+    const TI *src = x + row0 * Nx;
+    constexpr int W = 16 / sizeof(T);
+    if (Nx % W == 0) {
+        for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+            TI v[W];
+            ldv<W>(v, src + (long)j * W);
+#pragma unroll
+            for (int k = 0; k < W; ++k) stg[j * W + k] = (T)v[k];
+        }
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) stg[i] = (T)src[i];
+    }
+    __syncthreads();
+    {
+        const int p = threadIdx.x / R2, t = threadIdx.x - p * R2;
+        C v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int e = t + R2 * m;
+            v[m] = e < Nx ? cmake<C>(stg[(2 * p) * Nx + e], stg[(2 * p + 1) * Nx + e]) : cmake<C>(T(0), T(0));
+        }
+        dft_small<R1, -1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) A[p * RS + k1 * R2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], tw[t * k1]) : v[k1];
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < P * R1; task += blockDim.x) {
+        const int p = task / R1, k1 = task - p * R1;
+        C u[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + k1 * R2 + t];
+        dft_small<R2, -1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) Bf[p * RS + k1 + R1 * k2] = u[k2];
+    }
+    __syncthreads();
+    C *dst = out + row0 * H;
+    for (int i = threadIdx.x; i < 2 * P * H; i += blockDim.x) {
+        const int rr = i / H, k = i - rr * H;
+        const C *row = Bf + (rr >> 1) * RS;
+        const C z = row[k], zm = cconj(row[k == 0 ? 0 : M - k]);
+        C v;
+        if ((rr & 1) == 0) { const C s2 = cadd(z, zm); v = cmake<C>(T(0.5) * s2.x, T(0.5) * s2.y); }
+        else { const C d2 = csub(z, zm); v = cmake<C>(T(0.5) * d2.y, T(-0.5) * d2.x); }
+        dst[i] = v;
+    }
+}
+
+// inverse x pass with the epilogue: 2P consecutive rows of one plane (2P
+// divides Ny); Hermitian extension of each row pair, inverse DFT of length M,
+// rows' x < Nx to the epilogue (packs of 16 bytes when Nx allows).
+// grid = nrows / (2P); block = P * R2; smem = (M + 2 P (M + 2)) complex
+template <typename T, class Epi, int R1, int R2, int P>
+__global__ void __launch_bounds__(P * R2) k_x_inverse_r(const cplx<T> *__restrict__ in, int Nx, int Ny, int Nz,
+                                                        const cplx<T> *__restrict__ tw_g, Epi epi) {
+    using C = cplx<T>;
+    constexpr int M = R1 * R2, H = M / 2 + 1, RS = M + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *A = tw + M;       // [P][RS]
+    C *Bf = A + P * RS;  // [P][RS]; first holds the staged 2P*H spectra
+    load_twiddles(tw, tw_g, M);
+    const long row0 = (long)blockIdx.x * 2 * P;
+    const C *src = in + row0 * H;
+    C *stg = Bf;
+    for (int i = threadIdx.x; i < 2 * P * H; i += blockDim.x) {
+        C v = src[i];
+        const int k = i % H;
+        if (k == 0 || 2 * k == M) v.y = T(0);  // DC and (even M) Nyquist bins of a real row are real
+        stg[i] = v;
+    }
+    __syncthreads();
+    {
+        const int p = threadIdx.x / R2, t = threadIdx.x - p * R2;
+        C v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int k = t + R2 * m;
+            C a, b;
+            if (k < H) { a = stg[(2 * p) * H + k]; b = stg[(2 * p + 1) * H + k]; }
+            else { a = cconj(stg[(2 * p) * H + (M - k)]); b = cconj(stg[(2 * p + 1) * H + (M - k)]); }
+            v[m] = cmake<C>(a.x - b.y, a.y + b.x);
+        }
+        dft_small<R1, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+            A[p * RS + k1 * R2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(tw[t * k1])) : v[k1];
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < P * R1; task += blockDim.x) {
+        const int p = task / R1, k1 = task - p * R1;
+        C u[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + k1 * R2 + t];
+        dft_small<R2, +1>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) Bf[p * RS + k1 + R1 * k2] = u[k2];
+    }
+    __syncthreads();
+    const long plane = row0 / Ny;
+    const int y0 = (int)(row0 - plane * Ny);
+    auto pe = epi.bind(plane, Nz, Ny * Nx);
+    const int n = 2 * P * Nx;
+    const FastDiv fNx = make_fastdiv((unsigned)Nx);
+    constexpr int W = 16 / sizeof(T);
+    if (Nx % W == 0) {
+        for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
+            T v[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int il = j * W + k, rr = (int)fdiv((unsigned)il, fNx), e = il - rr * Nx;
+                const C z = Bf[(rr >> 1) * RS + e];
+                v[k] = (rr & 1) ? z.y : z.x;
+            }
+            pe.template pack<W>(y0 * Nx + j * W, v);
+        }
+    } else {
+        for (int il = threadIdx.x; il < n; il += blockDim.x) {
+            const int rr = (int)fdiv((unsigned)il, fNx), e = il - rr * Nx;
+            const C z = Bf[(rr >> 1) * RS + e];
+            pe(y0 * Nx + il, (rr & 1) ? z.y : z.x);
+        }
+    }
+}
+
+// FFT along a strided axis (y) of length M for TC consecutive columns of one
+// plane: element e of column c at in + plane*ips + e*H + c0 + c, e < Lin (zero
+// beyond); results e < Lout to out + plane*ops + e*H + c0 + c.  Stage A holds
+// R1 points per thread, stage B writes straight to HBM (c fastest).
+// grid = (ceil(H/TC), planes); block = TC * R2; smem = (M + TC (M + 1)) complex
+template <typename T, int S, int R1, int R2, int TC>
+__global__ void __launch_bounds__(TC * R2) k_col_r(const cplx<T> *__restrict__ in, cplx<T> *__restrict__ out,
+                                                   const cplx<T> *__restrict__ tw_g, int H, int Lin, int Lout,
+                                                   long ips, long ops) {
+    using C = cplx<T>;
+    constexpr int M = R1 * R2, RS = M + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *Sm = tw + M;  // [TC][RS]
+    load_twiddles(tw, tw_g, M);
+    const int c0 = blockIdx.x * TC;
+    const C *src = in + blockIdx.y * ips + c0;
+    C *dst = out + blockIdx.y * ops + c0;
+    const int c = threadIdx.x % TC, t = threadIdx.x / TC;
+    const bool live = c0 + c < H;
+    __syncthreads();
+    {
+        C v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int e = t + R2 * m;
+            v[m] = (live && e < Lin) ? src[(long)e * H + c] : cmake<C>(T(0), T(0));
+        }
+        dft_small<R1, S>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            C x = v[k1];
+            if (k1 > 0 && t > 0) x = cmul(x, S < 0 ? tw[t * k1] : cconj(tw[t * k1]));
+            Sm[c * RS + k1 * R2 + t] = x;
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < R1 * TC; task += blockDim.x) {
+        const int k1 = task / TC, cc = task - k1 * TC;
+        C u[R2];
+#pragma unroll
+        for (int tt = 0; tt < R2; ++tt) u[tt] = Sm[cc * RS + k1 * R2 + tt];
+        dft_small<R2, S>(u);
+        if (c0 + cc < H) {
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const int e = k1 + R1 * k2;
+                if (e < Lout) dst[(long)e * H + cc] = u[k2];
+            }
+        }
+    }
+}
+
 // ----- epilogues (row = ((b*3 + p)*Nz + z)*Ny + y, element row*Nx + e) -----
 // operator()(row, e, G) serves the row-wise C2R kernel; bind(plane) returns a
 // functor for one whole (b, p, z) plane, element i = y*Nx + x, used by the

@@ -129,3 +129,20 @@ def cube64_batch16(seed: int = 4):
     N = (64, 64, 64)
     return {"name": "cube64_b16_a8", "N": N, "h": H_DEFAULT, "eps": block_eps(N, 4, 2.0, 4.0, seed), "alpha": 8.0,
             "steps": 200, "exc": oblique_set(200, 8.0)}
+
+
+WORKLOADS = {
+    "cube16_a4": lambda: cube16(),
+    "cube64_a4": lambda: cube64(4.0),
+    "cube64_a8": lambda: cube64(8.0),
+    "cube64_a16": lambda: cube64(16.0),
+    "cube64_b16": lambda: cube64_batch16(),
+    "pillars8x8": lambda: pillars8x8(),
+}
+
+
+def workload(name: str):
+    """The named synthetic workload (see WORKLOADS)."""
+    if name not in WORKLOADS:
+        raise ValueError(f"unknown workload {name}; one of {sorted(WORKLOADS)}")
+    return WORKLOADS[name]()
