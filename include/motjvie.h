@@ -215,6 +215,24 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
  * Errors: MOT_EINVAL, MOT_ENOTCONV (state still advanced), MOT_ECUDA.         */
 mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *stats);
 
+/* Checkpoint: write run r's state to the file at path -- the problem's
+ * fingerprint (grid, h, alpha, a hash of eps_r), precision, plane waves, the
+ * next step index, J_{n-1}, J_{n-2} and the whole history ring of spectra
+ * (ell slots; for large grids this is most of the file) -- so that marching
+ * can resume in another process.  Synchronises the context stream.  The
+ * format is this library's own (little-endian, version 1).
+ * Errors: MOT_EINVAL (null, file cannot be written), MOT_ECUDA.              */
+mot_status mot_run_save(mot_run *r, const char *path);
+
+/* Resume: create a run on problem p from a checkpoint written by
+ * mot_run_save.  p must describe the same problem (grid, h, alpha and eps_r
+ * are checked against the checkpoint; options may differ).  The first step
+ * after loading runs host-driven, then graph mode resumes.  *out is owned by
+ * the caller (mot_run_destroy).
+ * Errors: MOT_EINVAL (null, unreadable/corrupt file, another problem),
+ * MOT_ENOMEM, MOT_ECUDA.                                                      */
+mot_status mot_run_load(mot_problem *p, const char *path, mot_run **out);
+
 /* Device pointer to the latest J_n: nrhs*3*Nz*Ny*Nx doubles (borrowed).      */
 mot_status mot_run_current_device(mot_run *r, const void **J_dev);
 

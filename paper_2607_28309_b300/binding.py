@@ -21,6 +21,8 @@ MOT_ENOTCONV = -3
 MOT_EUNSUPPORTED = -4
 MOT_ECUDA = -5
 MOT_ETIMEOUT = -6
+MOT_EBUSY = -7
+MOT_ECANCELLED = -8
 MOT_FP64 = 0
 MOT_MIXED = 1
 MOT_F64 = 0
@@ -35,6 +37,7 @@ __all__ = [
     "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
     "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
+    "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED",
 ]
 
 # every symbol include/motjvie.h declares
@@ -42,7 +45,7 @@ EXPORTED = [
     "mot_last_error", "mot_ctx_create", "mot_ctx_destroy", "mot_problem_create", "mot_problem_info_get",
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
-    "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times",
+    "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times", "mot_run_save", "mot_run_load",
 ]
 
 # mot_kernel_class values, in order
@@ -109,6 +112,8 @@ def lib():
         L.mot_run_step_index.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.mot_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.mot_run_kernel_times.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+        L.mot_run_save.argtypes = [P, ctypes.c_char_p]
+        L.mot_run_load.argtypes = [P, ctypes.c_char_p, PP]
         L.mot_run_destroy.argtypes = [P]
         L.mot_run_destroy.restype = None
         for name in EXPORTED:
@@ -243,6 +248,18 @@ def mot_run_step_index(run) -> int:
     n = ctypes.c_int64()
     _check(lib().mot_run_step_index(run, ctypes.byref(n)))
     return n.value
+
+
+def mot_run_save(run, path):
+    """Write the run's state (J history, history ring, step index) to path."""
+    _check(lib().mot_run_save(run, os.fsencode(path)))
+
+
+def mot_run_load(prob, path):
+    """A run resumed on prob from a checkpoint written by mot_run_save."""
+    out = ctypes.c_void_p()
+    _check(lib().mot_run_load(prob, os.fsencode(path), ctypes.byref(out)))
+    return out
 
 
 def mot_run_kernel_times(run) -> dict:

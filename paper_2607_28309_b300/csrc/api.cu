@@ -3,6 +3,7 @@
 // matrix-free Z0 product (Eq. 11-12), the history right-hand side (Eq. 3),
 // the TFQMR solve of each step and the history ring.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -347,6 +348,8 @@ struct mot_run {
     int prec = MOT_FP64;
     long n = 0;  // next step index
     std::vector<PlaneWaveDev> pw_host;
+    std::vector<mot_planewave> exc_host;  // the plane waves as given (checkpoints)
+    bool warmed = false;  // one host-driven step done in this process (graph mode needs it first)
     DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
     DBuf ring, wsAh, wsBh;
     // Krylov vectors (type of the solve) and scratch
@@ -504,6 +507,7 @@ bool xy_forward_r(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, A
         case 20: return xy_forward_r_go<Src, T, 5, 4, 5, 4>(x, out, planes, Nx, Ny, tx, ty, st);
         case 32: return xy_forward_r_go<Src, T, 8, 4, 8, 4>(x, out, planes, Nx, Ny, tx, ty, st);
         case 72: return xy_forward_r_go<Src, T, 9, 8, 9, 8>(x, out, planes, Nx, Ny, tx, ty, st);
+        case 75: return xy_forward_r_go<Src, T, 5, 15, 5, 15>(x, out, planes, Nx, Ny, tx, ty, st);
         case 128: return xy_forward_r_go<Src, T, 16, 8, 16, 8>(x, out, planes, Nx, Ny, tx, ty, st);
         default: return false;
     }
@@ -516,6 +520,7 @@ bool xy_inverse_r(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw 
         case 20: return xy_inverse_r_go<T, Epi, 5, 4, 5, 4>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
         case 32: return xy_inverse_r_go<T, Epi, 8, 4, 8, 4>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
         case 72: return xy_inverse_r_go<T, Epi, 9, 8, 9, 8>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
+        case 75: return xy_inverse_r_go<T, Epi, 5, 15, 5, 15>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
         case 128: return xy_inverse_r_go<T, Epi, 16, 8, 16, 8>(in, planes, Nx, Ny, Nz, tx, ty, epi, st);
         default: return false;
     }
@@ -2004,6 +2009,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     };
     const long nv = (long)p->N[0] * p->N[1] * p->N[2];
     const long n = 3 * nv * nrhs;
+    r->exc_host.assign(exc, exc + nrhs);
     // plane waves, then pol[B][3] right after them
     r->pw_host.resize(nrhs);
     std::vector<double> pol(3 * nrhs);
@@ -2105,7 +2111,7 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     // attributes), each step is one graph launch with its control on the
     // device; graph = 0 or 2 keeps host-driven steps
     const bool eager_env = r->p->opt.graph != 1;
-    if (!eager_env && r->n >= 1 && nsteps > 0) {
+    if (!eager_env && r->warmed && nsteps > 0) {
         cudaStream_t st = r->p->ctx->stream;
         if (!r->step_exec) MOT_TRY(build_step_graph(r));
         // device step index follows the host's
@@ -2165,12 +2171,13 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
         return result;
     }
     for (int s = 0; s < nsteps; ++s) {
-        if (!eager_env && r->n >= 1) {  // switch to graph mode after the first step
+        if (!eager_env && r->warmed) {  // switch to graph mode after the first step
             mot_status g = mot_run_step(r, nsteps - s, J_out ? J_out + (size_t)s * n : nullptr, stats ? stats + s : nullptr);
             return g != MOT_OK ? g : result;
         }
         mot_status st = run_one_step(r, stats ? stats + s : nullptr);
         if (st != MOT_OK && st != MOT_ENOTCONV) return st;
+        r->warmed = true;
         if (st == MOT_ENOTCONV) result = st;
         if (J_out) {
             MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)s * n, r->J.p, sizeof(double) * n, cudaMemcpyDeviceToHost,
@@ -2179,6 +2186,135 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     }
     if (J_out || stats) MOT_CUDA_TRY(cudaStreamSynchronize(r->p->ctx->stream));
     return result;
+}
+
+// ---------------------------------------------------------------- checkpoints
+namespace {
+struct CkptHeader {
+    char magic[8];  // "MOTJVIE\0"
+    uint32_t version;
+    int32_t precision;
+    int32_t N[3];
+    int32_t nrhs;
+    double h, alpha;
+    int64_t n;  // next step index
+    int32_t ell, pad;
+    uint64_t eps_hash;    // FNV-1a over the eps_r bytes
+    uint64_t vec_bytes;   // one [nrhs][3][n] FP64 array
+    uint64_t ring_bytes;  // the whole history ring
+    mot_options opt;
+};
+constexpr uint32_t kCkptVersion = 1;
+
+uint64_t fnv1a(const void *data, size_t bytes) {
+    const unsigned char *c = (const unsigned char *)data;
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+size_t run_ring_bytes(const mot_run *r) {
+    const mot_problem *p = r->p;
+    const size_t cs = r->prec == MOT_MIXED ? sizeof(float2) : sizeof(double2);
+    return (size_t)p->ell * r->B * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
+}
+
+// device <-> file through a bounded host buffer
+mot_status dev_to_file(FILE *f, const void *dev, size_t bytes) {
+    std::vector<char> buf(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t o = 0; o < bytes; o += buf.size()) {
+        const size_t k = std::min(buf.size(), bytes - o);
+        MOT_CUDA_TRY(cudaMemcpy(buf.data(), (const char *)dev + o, k, cudaMemcpyDeviceToHost));
+        if (fwrite(buf.data(), 1, k, f) != k) MOT_FAIL(MOT_EINVAL, "checkpoint write failed");
+    }
+    return MOT_OK;
+}
+
+mot_status file_to_dev(FILE *f, void *dev, size_t bytes) {
+    std::vector<char> buf(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t o = 0; o < bytes; o += buf.size()) {
+        const size_t k = std::min(buf.size(), bytes - o);
+        if (fread(buf.data(), 1, k, f) != k) MOT_FAIL(MOT_EINVAL, "checkpoint truncated");
+        MOT_CUDA_TRY(cudaMemcpy((char *)dev + o, buf.data(), k, cudaMemcpyHostToDevice));
+    }
+    return MOT_OK;
+}
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+}  // namespace
+
+mot_status mot_run_save(mot_run *r, const char *path) {
+    if (!r || !path) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    mot_problem *p = r->p;
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "MOTJVIE", 8);
+    hd.version = kCkptVersion;
+    hd.precision = r->prec;
+    for (int i = 0; i < 3; ++i) hd.N[i] = p->N[i];
+    hd.nrhs = r->B;
+    hd.h = p->h;
+    hd.alpha = p->alpha;
+    hd.n = r->n;
+    hd.ell = p->ell;
+    hd.eps_hash = fnv1a(p->eps_host.data(), p->eps_host.size() * sizeof(double));
+    hd.vec_bytes = sizeof(double) * 3 * (size_t)p->N[0] * p->N[1] * p->N[2] * r->B;
+    hd.ring_bytes = run_ring_bytes(r);
+    hd.opt = p->opt;
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) MOT_FAIL(MOT_EINVAL, std::string("cannot open checkpoint for writing: ") + path);
+    if (fwrite(&hd, sizeof(hd), 1, fc.f) != 1 ||
+        fwrite(r->exc_host.data(), sizeof(mot_planewave), r->B, fc.f) != (size_t)r->B)
+        MOT_FAIL(MOT_EINVAL, "checkpoint write failed");
+    MOT_TRY(dev_to_file(fc.f, r->J.p, hd.vec_bytes));
+    MOT_TRY(dev_to_file(fc.f, r->J2.p, hd.vec_bytes));
+    MOT_TRY(dev_to_file(fc.f, r->ring.p, hd.ring_bytes));
+    if (fflush(fc.f) != 0) MOT_FAIL(MOT_EINVAL, "checkpoint write failed");
+    return MOT_OK;
+}
+
+mot_status mot_run_load(mot_problem *p, const char *path, mot_run **out) {
+    if (!p || !path || !out) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    *out = nullptr;
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) MOT_FAIL(MOT_EINVAL, std::string("cannot open checkpoint: ") + path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, fc.f) != 1 || memcmp(hd.magic, "MOTJVIE", 8) != 0)
+        MOT_FAIL(MOT_EINVAL, "not a libmotjvie checkpoint");
+    if (hd.version != kCkptVersion) MOT_FAIL(MOT_EINVAL, "checkpoint version not supported");
+    bool same = hd.h == p->h && hd.alpha == p->alpha && hd.ell == p->ell &&
+                hd.eps_hash == fnv1a(p->eps_host.data(), p->eps_host.size() * sizeof(double));
+    for (int i = 0; i < 3; ++i) same = same && hd.N[i] == p->N[i];
+    if (!same) MOT_FAIL(MOT_EINVAL, "checkpoint belongs to another problem (grid, h, alpha or eps_r differ)");
+    if (hd.nrhs < 1 || hd.nrhs > 1024 || hd.n < 0) MOT_FAIL(MOT_EINVAL, "corrupt checkpoint header");
+    std::vector<mot_planewave> exc(hd.nrhs);
+    if (fread(exc.data(), sizeof(mot_planewave), hd.nrhs, fc.f) != (size_t)hd.nrhs)
+        MOT_FAIL(MOT_EINVAL, "checkpoint truncated");
+    mot_run *r = nullptr;
+    MOT_TRY(mot_run_create(p, hd.nrhs, exc.data(), hd.precision, &r));
+    const size_t vec = sizeof(double) * 3 * (size_t)p->N[0] * p->N[1] * p->N[2] * r->B;
+    mot_status s = MOT_OK;
+    if (hd.vec_bytes != vec || hd.ring_bytes != run_ring_bytes(r)) {
+        set_error("checkpoint sizes do not match the run it describes");
+        s = MOT_EINVAL;
+    }
+    if (s == MOT_OK) s = file_to_dev(fc.f, r->J.p, vec);
+    if (s == MOT_OK) s = file_to_dev(fc.f, r->J2.p, vec);
+    if (s == MOT_OK) s = file_to_dev(fc.f, r->ring.p, hd.ring_bytes);
+    if (s != MOT_OK) {
+        mot_run_destroy(r);
+        return s;
+    }
+    r->n = hd.n;
+    *out = r;
+    return MOT_OK;
 }
 
 mot_status mot_run_kernel_times(mot_run *r, int cls, int32_t *launches, float *mean_ms) {
