@@ -243,6 +243,65 @@ mot_status mot_kernel_launches(uint64_t *count);
 /* Index of the next step to be computed.                                       */
 mot_status mot_run_step_index(const mot_run *r, int64_t *n);
 
+/* ---------------------------------------------------------------- serving
+ * A server runs many scattering runs (different grids, permittivities, step
+ * sizes) on one GPU with continuous batching: requests are admitted in arrival
+ * order whenever a slot is free and their estimated device memory fits under
+ * the budget and in free memory; each admitted run keeps its Green spectra and
+ * history ring on the device and advances one MOT step per worker pass on its
+ * own stream, so runs that arrive while others are on the GPU overlap with
+ * them.  Each run's currents are the same as the run alone (the same kernels
+ * and drivers).  No counterpart in the paper (a deployment pattern).          */
+typedef struct mot_server mot_server;
+
+typedef struct {
+    int32_t n[3];              /* Nx, Ny, Nz                                        */
+    double h;                  /* voxel size [m]                                   */
+    const double *eps_r;       /* host [Nz][Ny][Nx], copied at submit               */
+    double alpha;              /* dt = alpha dt_CFL                                */
+    int32_t precision;         /* MOT_FP64 or MOT_MIXED                            */
+    int32_t nrhs;              /* plane waves                                      */
+    const mot_planewave *exc;  /* host [nrhs], copied at submit                    */
+    int32_t nsteps;            /* steps to march                                  */
+    const mot_options *opt;    /* nullable (defaults), copied at submit           */
+    double *J_final;           /* host [nrhs][3][Nz][Ny][Nx] or NULL: receives J of
+                                  the last step; must stay valid until the wait on
+                                  this request's ticket returns                    */
+} mot_request;
+
+typedef struct {
+    int32_t status;        /* MOT_OK, MOT_ENOTCONV (some step missed its tolerance),
+                              MOT_ENOMEM (never fits the budget / free memory),
+                              MOT_ECANCELLED (server destroyed), other errors     */
+    int32_t steps;         /* steps completed                                     */
+    double queue_ms;       /* submit -> admission (host clock)                   */
+    double run_ms;         /* admission -> completion (host clock)               */
+    float step_p50_ms;     /* per-step device time (CUDA events), median          */
+    float step_p99_ms;     /* per-step device time, 99th percentile               */
+    uint64_t device_bytes; /* device memory reserved for the run                  */
+} mot_result;
+
+/* Start a server on ctx's device with a device-memory budget in bytes (0:
+ * 80% of the free memory now) and at most max_slots runs on the GPU at once.
+ * Errors: MOT_EINVAL (null, max_slots outside [1, 256]), MOT_ECUDA.          */
+mot_status mot_server_create(mot_ctx *ctx, size_t mem_budget, int max_slots, mot_server **out);
+
+/* Queue a run; *ticket identifies it for mot_server_wait.  Host inputs are
+ * copied before returning.  Errors: MOT_EINVAL (bad request), MOT_EBUSY
+ * (4096 requests already waiting).                                          */
+mot_status mot_server_submit(mot_server *s, const mot_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_s seconds for the run of ticket to finish and collect
+ * its result (the ticket is then released).  Errors: MOT_EINVAL (null,
+ * unknown or collected ticket), MOT_ETIMEOUT (not finished in time; the
+ * ticket stays valid).                                                        */
+mot_status mot_server_wait(mot_server *s, uint64_t ticket, double timeout_s, mot_result *res);
+
+/* Stop the server: runs on the GPU finish their current step and are
+ * abandoned, waiting requests are cancelled.  Call after every wait has
+ * returned.                                                                    */
+void mot_server_destroy(mot_server *s);
+
 /* Kernel classes timed by the timing option (mot_options.timing = 1 with
  * graph = 0 or 2): CUDA events around every launch of these kernels during a
  * step (kernels inside CUDA graphs cannot be bracketed).  Instrumentation; no

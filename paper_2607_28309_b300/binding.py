@@ -37,7 +37,8 @@ __all__ = [
     "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
     "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
-    "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED",
+    "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED", "mot_request", "mot_result",
+    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy",
 ]
 
 # every symbol include/motjvie.h declares
@@ -46,6 +47,7 @@ EXPORTED = [
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times", "mot_run_save", "mot_run_load",
+    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy",
 ]
 
 # mot_kernel_class values, in order
@@ -81,6 +83,19 @@ class mot_step_stats(ctypes.Structure):
                 ("mvps", ctypes.c_int32), ("ms_zhist", ctypes.c_float), ("ms_zgreen", ctypes.c_float)]
 
 
+class mot_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("h", ctypes.c_double), ("eps_r", ctypes.c_void_p),
+                ("alpha", ctypes.c_double), ("precision", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("exc", ctypes.c_void_p), ("nsteps", ctypes.c_int32), ("opt", ctypes.c_void_p),
+                ("J_final", ctypes.c_void_p)]
+
+
+class mot_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("step_p50_ms", ctypes.c_float), ("step_p99_ms", ctypes.c_float),
+                ("device_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -113,11 +128,17 @@ def lib():
         L.mot_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.mot_run_kernel_times.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
         L.mot_run_save.argtypes = [P, ctypes.c_char_p]
+        L.mot_server_create.argtypes = [P, ctypes.c_size_t, I, PP]
+        L.mot_server_submit.argtypes = [P, ctypes.POINTER(mot_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.mot_server_wait.argtypes = [P, ctypes.c_uint64, D, ctypes.POINTER(mot_result)]
+        L.mot_server_destroy.argtypes = [P]
+        L.mot_server_destroy.restype = None
         L.mot_run_load.argtypes = [P, ctypes.c_char_p, PP]
         L.mot_run_destroy.argtypes = [P]
         L.mot_run_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("mot_ctx_destroy", "mot_problem_destroy", "mot_run_destroy", "mot_last_error"):
+            if name not in ("mot_ctx_destroy", "mot_problem_destroy", "mot_run_destroy", "mot_last_error",
+                            "mot_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -260,6 +281,49 @@ def mot_run_load(prob, path):
     out = ctypes.c_void_p()
     _check(lib().mot_run_load(prob, os.fsencode(path), ctypes.byref(out)))
     return out
+
+
+_served = {}  # (server, ticket) -> the host output array the library writes before the wait returns
+
+
+def mot_server_create(ctx, mem_budget: int = 0, max_slots: int = 4):
+    out = ctypes.c_void_p()
+    _check(lib().mot_server_create(ctx, int(mem_budget), int(max_slots), ctypes.byref(out)))
+    return out
+
+
+def mot_server_submit(server, N, h, eps_r, alpha, exc, nsteps, precision=MOT_MIXED, opt=None, J_final=None) -> int:
+    """Queue a run; J_final (C-contiguous float64 [nrhs, 3, nv] or None) receives the last step's J."""
+    eps = np.ascontiguousarray(eps_r, dtype=np.float64)
+    arr = _planewaves(exc)
+    if J_final is not None:
+        assert J_final.dtype == np.float64 and J_final.flags["C_CONTIGUOUS"]
+        assert J_final.size == len(exc) * 3 * int(np.prod(N))
+    q = mot_request()
+    for i in range(3):
+        q.n[i] = int(N[i])
+    q.h, q.alpha, q.precision, q.nrhs, q.nsteps = float(h), float(alpha), int(precision), len(exc), int(nsteps)
+    q.eps_r = eps.ctypes.data
+    q.exc = ctypes.cast(arr, ctypes.c_void_p).value
+    q.opt = ctypes.cast(ctypes.byref(opt), ctypes.c_void_p).value if opt is not None else None
+    q.J_final = J_final.ctypes.data if J_final is not None else None
+    t = ctypes.c_uint64()
+    _check(lib().mot_server_submit(server, ctypes.byref(q), ctypes.byref(t)))
+    _served[(server.value, t.value)] = J_final
+    return t.value
+
+
+def mot_server_wait(server, ticket: int, timeout_s: float = 60.0) -> mot_result:
+    res = mot_result()
+    _check(lib().mot_server_wait(server, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(res)))
+    _served.pop((server.value, ticket), None)
+    return res
+
+
+def mot_server_destroy(server):
+    lib().mot_server_destroy(server)
+    for k in [k for k in _served if k[0] == server.value]:
+        del _served[k]
 
 
 def mot_run_kernel_times(run) -> dict:

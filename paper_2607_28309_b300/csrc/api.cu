@@ -2432,3 +2432,6 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
     EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
 }
+
+// ---------------------------------------------------------------- serving
+#include "server.cuh"

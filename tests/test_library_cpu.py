@@ -68,7 +68,8 @@ def test_ctypes_structs_match_header(tmp_path):
     import subprocess
 
     structs = {"mot_planewave": mot.mot_planewave, "mot_options": mot.mot_options,
-               "mot_problem_info": mot.mot_problem_info, "mot_step_stats": mot.mot_step_stats}
+               "mot_problem_info": mot.mot_problem_info, "mot_step_stats": mot.mot_step_stats,
+               "mot_request": mot.mot_request, "mot_result": mot.mot_result}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/motjvie.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
