@@ -245,18 +245,27 @@ def kernel_bytes(info, N, B, prec, lags):
     }
 
 
-def profiled_traffic(cls):
-    """DRAM bytes per launch from the committed ncu summary of this kernel on
-    this workload, if one exists and was taken from the current kernel sources
-    (its digest of csrc/*.cuh matches); else None."""
-    import glob
+# the headers that hold the kernels (host-only sources such as the server are left out)
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2607_28309_b300", "csrc", f)
+                  for f in ("common.cuh", "fft.cuh", "krylov.cuh", "spectral.cuh")]
+
+
+def kernel_digest():
+    """sha256 of the kernel headers, first 16 hex digits."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2607_28309_b300", "csrc", "*.cuh"))):
+    for f in KERNEL_SOURCES:
         with open(f, "rb") as fh:
             h.update(fh.read())
-    digest = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(cls):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, if one exists and was taken from the current kernel sources
+    (its recorded kernel digest matches); else None."""
+    digest = kernel_digest()
     path = os.path.join(ROOT, "profiles", f"{cls}_cube64_a8.md")
     if not os.path.exists(path):
         return None
