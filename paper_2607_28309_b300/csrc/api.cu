@@ -352,6 +352,7 @@ struct mot_run {
     bool warmed = false;  // one host-driven step done in this process (graph mode needs it first)
     DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
     DBuf ring, wsAh, wsBh;
+    DBuf hacc;  // history accumulation on the full Mh grid [B][3][Mhz][Mhy][Hh]
     // Krylov vectors (type of the solve) and scratch
     DBuf kv[10];
     DBuf scal, part1, part2, part3, dots;
@@ -593,6 +594,10 @@ bool col_r(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout
            cudaStream_t st) {
     if (specialised_off()) return false;
     switch (tw->M) {
+        case 32: return col_r_go<T, S, 8, 4, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
+        case 64: return col_r_go<T, S, 8, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
+        case 128: return col_r_go<T, S, 16, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
+        case 160: return col_r_go<T, S, 10, 16, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
         case 270: return col_r_go<T, S, 15, 18, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
         default: return false;
     }
@@ -1525,7 +1530,23 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
                                                               nptr, p->dt);
     MOT_CHECK_LAUNCH();
     const int kmax = (int)std::min<long>(r->n, p->ell);
-    {
+    const long hist_threads = (long)r->B * (Mz / 2 + 1) * (My / 2 + 1) * H;
+    if (r->hacc.p && hist_threads < (1L << 31)) {
+        // streaming accumulation over the ring into the full-z spectrum, then the
+        // inverse z FFT of the Nz kept planes
+        Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
+        C *acc = (C *)r->hacc.p;
+        const unsigned blocks = (unsigned)std::min<long>((hist_threads + 255) / 256, 16L * p->ctx->sms);
+        if (!p->capturing) p->kt.begin(st, MOT_K_Z_HISTORY);
+        count_launch();
+        k_hist_acc<T><<<blocks, 256, 0, st>>>((const C *)r->ring.p, Lh_of<T>(p), acc, Mz, My, H, oc, r->B, p->ell, r->n,
+                                            kmax, nptr);
+        MOT_CHECK_LAUNCH();
+        const long zp = (long)My * H;
+        if (col_r<T, +1>(acc, Bf, tz, (int)zp, Mz, Nz, r->B * 3, (long)Mz * zp, (long)Nz * zp, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_axis<T, +1>(acc, Bf, tz, H, Mz, Nz, r->B * 3, My, (long)Mz * zp, H, zp, (long)Nz * zp, H, zp, st)));
+        if (!p->capturing) p->kt.end(st);
+    } else {
         // ~100 KB of shared memory per CTA keeps two CTAs resident per SM
         int tw = sizeof(T) == 4 ? 8 : 4;
         while (tw > 1 && (size_t)(12 * Mz * tw + Mz) * sizeof(C) > 112 * 1024) tw /= 2;
@@ -2060,6 +2081,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->r, sizeof(double) * n)) != MOT_OK) return fail(s);
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
     if ((s = dalloc(r->ring, ring_bytes)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->hacc, ring_bytes / p->ell)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     for (int i = 0; i < 10; ++i)
@@ -2357,6 +2379,7 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->b);
     dfree(r->r);
     dfree(r->ring);
+    dfree(r->hacc);
     dfree(r->wsAh);
     dfree(r->wsBh);
     for (int i = 0; i < 10; ++i) dfree(r->kv[i]);

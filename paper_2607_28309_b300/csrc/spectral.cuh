@@ -746,6 +746,84 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// history accumulation (Eq. 3), streaming: acc_q(kz, ky, kx) =
+// sum_{k=1..kmax} sum_p Lambda_k,qp(kz, ky, kx) Jhat_{n-k},p(kz, ky, kx) on the
+// full Mh grid, in [B][3][Mz][My][H].  One thread per (b, fz <= Mz/2, j <=
+// My/2, kx): the up to four rows (kz, ky) in {fz, Mz - fz} x {j, My - j} share
+// the octant value Lambda_k(fz, j, kx) (the mixed components change sign with
+// the folded axis), so every Lambda_k value and every ring value is read once;
+// kx fastest, so a warp reads contiguous runs.  No shared memory: as many
+// blocks as the registers allow stream from HBM.  The inverse z FFT follows.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
+                                                  cplx<T> *__restrict__ acc, int Mz, int My, int H, Octant oc,
+                                                  int nrhs, int ell, long n, int kmax,
+                                                  const long long *__restrict__ nptr) {
+    if (nptr) {  // graph mode: step index from device memory
+        n = (long)*nptr;
+        kmax = (int)(n < ell ? n : ell);
+    }
+    using C = cplx<T>;
+    const int hz = Mz / 2 + 1, hy = My / 2 + 1;
+    const unsigned total = (unsigned)nrhs * hz * hy * H;
+    const long plane = (long)My * H;
+    const long slot_comp = (long)Mz * plane;
+    const long slot_size = (long)nrhs * 3 * slot_comp;
+    const long cs = (long)oc.Kz * oc.Ky * oc.H;
+    const FastDiv fH = make_fastdiv((unsigned)H), fy = make_fastdiv((unsigned)hy), fz_ = make_fastdiv((unsigned)hz);
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        unsigned t = fdiv(idx, fH);
+        const int kx = (int)(idx - t * H);
+        unsigned t2 = fdiv(t, fy);
+        const int j = (int)(t - t2 * hy);
+        const unsigned b = fdiv(t2, fz_);
+        const int fz = (int)(t2 - b * hz);
+        const bool twoy = j != 0 && 2 * j != My;
+        const bool twoz = fz != 0 && 2 * fz != Mz;
+        // rows: r = (z-side, y-side); z-side 1 is kz = Mz - fz, y-side 1 is ky = My - j
+        // rows that do not exist (self-mirrored folds) read row 0 again and are not stored
+        long off[4];
+        off[0] = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
+        off[1] = twoy ? off[0] + (long)(My - 2 * j) * H : off[0];             // (fz, My - j)
+        off[2] = twoz ? off[0] + (long)(Mz - 2 * fz) * plane : off[0];        // (Mz - fz, j)
+        off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];  // (Mz - fz, My - j)
+        C a[4][3];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a[r][q] = cmake<C>(T(0), T(0));
+        const long lidx = ((long)fz * oc.Ky + j) * oc.H + kx;
+        long s = (n - 1) % ell;
+        if (s < 0) s += ell;
+#pragma unroll 2
+        for (int k = 1; k <= kmax; ++k) {
+            const T *L = Lh + (long)k * 6 * cs + lidx;
+            const T gxx = L[0], gyy = L[cs], gzz = L[2 * cs], gxy = L[3 * cs], gxz = L[4 * cs], gyz = L[5 * cs];
+            const C *R = ring + s * slot_size;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
+                const T exy = sy * gxy, exz = sz * gxz, eyz = sy * sz * gyz;
+                const C u0 = R[off[r]], u1 = R[off[r] + slot_comp], u2 = R[off[r] + 2 * slot_comp];
+                a[r][0] = cmake<C>(a[r][0].x + gxx * u0.x + exy * u1.x + exz * u2.x, a[r][0].y + gxx * u0.y + exy * u1.y + exz * u2.y);
+                a[r][1] = cmake<C>(a[r][1].x + exy * u0.x + gyy * u1.x + eyz * u2.x, a[r][1].y + exy * u0.y + gyy * u1.y + eyz * u2.y);
+                a[r][2] = cmake<C>(a[r][2].x + exz * u0.x + eyz * u1.x + gzz * u2.x, a[r][2].y + exz * u0.y + eyz * u1.y + gzz * u2.y);
+            }
+            s = (s == 0) ? ell - 1 : s - 1;
+        }
+        // acc has the ring slot's layout [b][q][kz][ky][kx]
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const bool on = (r == 0) || (r == 1 && twoy) || (r == 2 && twoz) || (r == 3 && twoy && twoz);
+            if (!on) continue;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[off[r] + q * slot_comp] = a[r][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // history z pass over the mirrored row pair (ky, My - ky): both rows fold to
 // the same Green-spectrum octant row (odd components change sign), so each
 // Lambda_k value is read once for the two rows.  grid = (ceil(H/tx), B*(My/2+1));
