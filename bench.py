@@ -198,7 +198,7 @@ def oracle_sample(w, mvps_per_step: float, rows: int = 2048, seed: int = 0):
 # ---------------------------------------------------------------- roofline bookkeeping
 KERNEL_NAMES = {
     "z_green": "k_z_green_r (present-time z pass)",
-    "z_history": "k_z_history2 (history z pass)",
+    "z_history": "k_hist_acc + k_col_r (history sum and its inverse z pass)",
     "fwd_half": "k_xy_forward_r<SrcHalfA> (forward xy pass of Z0 y2 + first TFQMR half step)",
     "fwd_y1": "k_xy_forward_r<SrcY1> (forward xy pass of Z0 y1)",
     "fwd_plain": "k_xy_forward_r<SrcPlain> (forward xy pass, stored input)",
