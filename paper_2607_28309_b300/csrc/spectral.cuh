@@ -755,6 +755,9 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
 // kx fastest, so a warp reads contiguous runs.  No shared memory: as many
 // blocks as the registers allow stream from HBM.  The inverse z FFT follows.
 // ---------------------------------------------------------------------------
+constexpr int kHistPrefetch = 2;  // lags ahead
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
                                                   cplx<T> *__restrict__ acc, int Mz, int My, int H, Octant oc,
@@ -798,6 +801,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
         if (s < 0) s += ell;
 #pragma unroll 2
         for (int k = 1; k <= kmax; ++k) {
+            if (k + kHistPrefetch <= kmax) {  // L2 prefetch of lag k + kHistPrefetch: more loads in flight per SM
+                long sp = s - kHistPrefetch;
+                if (sp < 0) sp += ell;
+                const C *Rp = ring + sp * slot_size;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) prefetch_l2(Rp + off[r] + q * slot_comp);
+                const T *Lp = Lh + (long)(k + kHistPrefetch) * 6 * cs + lidx;
+#pragma unroll
+                for (int c6 = 0; c6 < 6; ++c6) prefetch_l2(Lp + c6 * cs);
+            }
             const T *L = Lh + (long)k * 6 * cs + lidx;
             const T gxx = L[0], gyy = L[cs], gzz = L[2 * cs], gxy = L[3 * cs], gxz = L[4 * cs], gyz = L[5 * cs];
             const C *R = ring + s * slot_size;
