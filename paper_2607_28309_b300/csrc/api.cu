@@ -552,13 +552,13 @@ bool x_inverse_r_go(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisT
 
 template <typename T, int S, int R1, int R2, int TC>
 bool col_r_go(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int planes, long ips, long ops,
-              cudaStream_t st) {
+              cudaStream_t st, const long long *nptr, int ell, long slot_stride) {
     constexpr int M = R1 * R2;
     const size_t smem = (size_t)(M + TC * (M + 1)) * sizeof(cplx<T>);
     if (smem > kSmemMax || allow_smem<k_col_r<T, S, R1, R2, TC>>() != MOT_OK) return false;
     count_launch();
     k_col_r<T, S, R1, R2, TC><<<dim3((H + TC - 1) / TC, planes), TC * R2, smem, st>>>(in, out, twp<T>(tw), H, Lin, Lout,
-                                                                                      ips, ops);
+                                                                                      ips, ops, nptr, ell, slot_stride);
     return true;
 }
 
@@ -591,14 +591,14 @@ bool x_inverse_r(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *
 
 template <typename T, int S>
 bool col_r(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout, int planes, long ips, long ops,
-           cudaStream_t st) {
+           cudaStream_t st, const long long *nptr = nullptr, int ell = 1, long slot_stride = 0) {
     if (specialised_off()) return false;
     switch (tw->M) {
-        case 32: return col_r_go<T, S, 8, 4, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
-        case 64: return col_r_go<T, S, 8, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
-        case 128: return col_r_go<T, S, 16, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
-        case 160: return col_r_go<T, S, 10, 16, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
-        case 270: return col_r_go<T, S, 15, 18, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st);
+        case 32: return col_r_go<T, S, 8, 4, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+        case 64: return col_r_go<T, S, 8, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+        case 128: return col_r_go<T, S, 16, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+        case 160: return col_r_go<T, S, 10, 16, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+        case 270: return col_r_go<T, S, 15, 18, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
         default: return false;
     }
 }
@@ -1498,8 +1498,12 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
     }
     const long slot_elems = (long)r->B * 3 * Mz * My * H;
     C *slot = nptr ? (C *)r->ring.p : (C *)ring_slot<T>(r, r->n % p->ell);
-    MOT_TRY((launch_axis<T, -1>(Bf, slot, tz, H, Nz, Mz, r->B * 3, My, (long)Nz * My * H, H, (long)My * H,
-                                (long)Mz * My * H, H, (long)My * H, st, nptr, p->ell, slot_elems)));
+    if (col_r<T, -1>(Bf, slot, tz, (int)((long)My * H), Nz, Mz, r->B * 3, (long)Nz * My * H, (long)Mz * My * H, st, nptr,
+                     p->ell, slot_elems))
+        MOT_CHECK_LAUNCH();
+    else
+        MOT_TRY((launch_axis<T, -1>(Bf, slot, tz, H, Nz, Mz, r->B * 3, My, (long)Nz * My * H, H, (long)My * H,
+                                    (long)Mz * My * H, H, (long)My * H, st, nptr, p->ell, slot_elems)));
     return MOT_OK;
 }
 

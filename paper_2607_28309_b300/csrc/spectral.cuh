@@ -1124,17 +1124,21 @@ __global__ void __launch_bounds__(P * R2) k_x_inverse_r(const cplx<T> *__restric
 // FFT along a strided axis (y) of length M for TC consecutive columns of one
 // plane: element e of column c at in + plane*ips + e*H + c0 + c, e < Lin (zero
 // beyond); results e < Lout to out + plane*ops + e*H + c0 + c.  Stage A holds
-// R1 points per thread, stage B writes straight to HBM (c fastest).
+// R1 points per thread, stage B writes straight to HBM (c fastest).  With
+// nptr, out is advanced by (*nptr mod ell) * slot_stride (history-ring slot).
 // grid = (ceil(H/TC), planes); block = TC * R2; smem = (M + TC (M + 1)) complex
 template <typename T, int S, int R1, int R2, int TC>
 __global__ void __launch_bounds__(TC * R2) k_col_r(const cplx<T> *__restrict__ in, cplx<T> *__restrict__ out,
                                                    const cplx<T> *__restrict__ tw_g, int H, int Lin, int Lout,
-                                                   long ips, long ops) {
+                                                   long ips, long ops, const long long *__restrict__ nptr,
+                                                   int ell, long slot_stride) {
     using C = cplx<T>;
     constexpr int M = R1 * R2, RS = M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *Sm = tw + M;  // [TC][RS]
+    // graph mode: write into history-ring slot (*nptr mod ell)
+    if (nptr) out += (long)(*nptr % ell) * slot_stride;
     load_twiddles(tw, tw_g, M);
     const int c0 = blockIdx.x * TC;
     const C *src = in + blockIdx.y * ips + c0;
