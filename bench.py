@@ -417,12 +417,13 @@ def native(args, ws, rank, local):
 
     # ---- the plain FP64 form and a 16-excitation batch on the same GPU
     compare = {}
-    for label, wl, pr_, steps_c in (("fp64", w, mot.MOT_FP64, 8),
-                                    ("mixed_batch16", workload("cube64_b16"), mot.MOT_MIXED, 6)):
+    for label, wl, pr_, steps_c in (("fp64", w, mot.MOT_FP64, 10),
+                                    ("mixed_batch16", workload("cube64_b16"), mot.MOT_MIXED, 10)):
         try:
             pb = mot.mot_problem_create(ctx, wl["N"], wl["h"], wl["eps"], wl["alpha"], gopt)
             rb = mot.mot_run_create(pb, wl["exc"], pr_)
-            mot.mot_run_step(rb, 3, None, None, allow_notconv=True)
+            # past the history length: the timed steps sum all ell lags
+            mot.mot_run_step(rb, max(3, mot.mot_problem_info_get(pb).ell + 1), None, None, allow_notconv=True)
             torch.cuda.synchronize()
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -431,7 +432,8 @@ def native(args, ws, rank, local):
             torch.cuda.synchronize()
             sec = a.elapsed_time(b_) / 1e3
             compare[label] = {"steps_per_s": steps_c / sec, "nrhs": len(wl["exc"]),
-                              "rhs_steps_per_s": steps_c * len(wl["exc"]) / sec, "steps": steps_c}
+                              "rhs_steps_per_s": steps_c * len(wl["exc"]) / sec, "steps": steps_c,
+                              "after_steps": mot.mot_run_step_index(rb) - steps_c}
             mot.mot_run_destroy(rb)
             mot.mot_problem_destroy(pb)
         except Exception as e:  # reported, not fatal

@@ -353,6 +353,11 @@ struct mot_run {
     DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
     DBuf ring, wsAh, wsBh;
     DBuf hacc;  // history accumulation on the full Mh grid [B][3][Mhz][Mhy][Hh]
+    DBuf hpart;  // the lags 2.. part of a step's history sum (same layout as hacc)
+    bool hpart_ok = false;  // hpart holds the lags 2.. sum of step n (the step graph leaves it so)
+    cudaStream_t hside = nullptr;  // step graph: low-priority branch of the next step's partial sum
+    cudaEvent_t hfork = nullptr, hjoin = nullptr;
+    bool hjoin_open = false;  // capture: the branch still has to join the step's stream
     // Krylov vectors (type of the solve) and scratch
     DBuf kv[10];
     DBuf scal, part1, part2, part3, dots;
@@ -1397,7 +1402,8 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
     count_launch();
     k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(rhs, rhs, L, k.p2);
     count_launch();
-    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol);
+    // FP32 inner solves stop at stagnation; the FP64 solve runs to tol or maxit
+    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol, sizeof(V) == 4 ? 1 : 0);
     count_launch();
     k_tfqmr_zero_rhs<V><<<gv, 256, 0, st>>>(x, k.sc, L);
     count_launch();
@@ -1508,6 +1514,69 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
 }
 
 // b_n = E^i_n - eps T(dt) J_{n-1} + (eps - 1) sum_k G_k J_{n-k}
+// the streaming history sum applies (grid within the 32-bit thread index)
+bool hist_streaming(const mot_run *r) {
+    const mot_problem *p = r->p;
+    const long threads = (long)r->B * (p->Mh[2] / 2 + 1) * (p->Mh[1] / 2 + 1) * p->Hh;
+    return r->hacc.p && r->hpart.p && threads < (1L << 31);
+}
+
+// blocks of bt threads for the streaming history sum, at most per_sm_x2 / 2 per SM
+unsigned hist_blocks(const mot_run *r, long per_sm_x2, int bt = 256) {
+    const mot_problem *p = r->p;
+    const long threads = (long)r->B * (p->Mh[2] / 2 + 1) * (p->Mh[1] / 2 + 1) * p->Hh;
+    return (unsigned)std::max<long>(1, std::min<long>((threads + bt - 1) / bt, per_sm_x2 * p->ctx->sms / 2));
+}
+
+// the step graph's side branch: one block of kHistSideThreads per SM leaves
+// room beside it for the solve's kernels (MOTJVIE_HIST_SIDE_BPS2 = blocks per
+// two SMs and MOTJVIE_HIST_SIDE_THREADS override, for sweeps)
+long hist_side_per_sm_x2() {
+    static const long f = getenv("MOTJVIE_HIST_SIDE_BPS2") ? std::max(1, atoi(getenv("MOTJVIE_HIST_SIDE_BPS2"))) : 1;
+    return f;
+}
+int hist_side_threads() {
+    static const int f = getenv("MOTJVIE_HIST_SIDE_THREADS") ? atoi(getenv("MOTJVIE_HIST_SIDE_THREADS")) : 256;
+    return (f == 64 || f == 128 || f == 256) ? f : 256;
+}
+
+// hpart = sum over lags 2..min(m, ell) of Lambda_k Jhat_{m-k}, m = r->n (or *nptr + dm)
+int hist_side_mode() {
+    static const int f = getenv("MOTJVIE_HIST_SIDE_MODE") ? atoi(getenv("MOTJVIE_HIST_SIDE_MODE")) : 1;
+    return (f >= 0 && f <= 2) ? f : 1;
+}
+
+template <typename T>
+mot_status hist_partial(mot_run *r, cudaStream_t st, const long long *nptr, int dm, unsigned blocks, int bt = 256,
+                        int mode = 0) {
+    mot_problem *p = r->p;
+    const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
+    Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
+    const auto *ring = (const cplx<T> *)r->ring.p;
+    auto *out = (cplx<T> *)r->hpart.p;
+    count_launch();
+    if (mode == 1)
+        k_hist_acc<T, 1><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
+                                                p->ell, nptr, dm);
+    else if (mode == 2)
+        k_hist_acc<T, 2><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
+                                                p->ell, nptr, dm);
+    else
+        k_hist_acc<T, 0><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
+                                                p->ell, nptr, dm);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+// before a step-graph launch: the graph expects the partial sum of step n in hpart
+mot_status hist_prime(mot_run *r, cudaStream_t st) {
+    if (!hist_streaming(r) || r->hpart_ok) return MOT_OK;
+    if (r->prec == MOT_MIXED) MOT_TRY(hist_partial<float>(r, st, nullptr, 0, hist_blocks(r, 32)));
+    else MOT_TRY(hist_partial<double>(r, st, nullptr, 0, hist_blocks(r, 32)));
+    r->hpart_ok = true;
+    return MOT_OK;
+}
+
 template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const long long *nptr = nullptr) {
     mot_problem *p = r->p;
     const int Nx = p->N[0], Ny = p->N[1], Nz = p->N[2];
@@ -1534,18 +1603,32 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
                                                               nptr, p->dt);
     MOT_CHECK_LAUNCH();
     const int kmax = (int)std::min<long>(r->n, p->ell);
-    const long hist_threads = (long)r->B * (Mz / 2 + 1) * (My / 2 + 1) * H;
-    if (r->hacc.p && hist_threads < (1L << 31)) {
-        // streaming accumulation over the ring into the full-z spectrum, then the
-        // inverse z FFT of the Nz kept planes
+    if (hist_streaming(r)) {
+        // streaming accumulation over the ring into the full-z spectrum (the
+        // lags 2.. partial sum, then lag 1 onto it), then the inverse z FFT of
+        // the Nz kept planes.  In the step graph the partial sum is the one the
+        // previous step computed beside its solve, and this step's branch
+        // computes the next one.
         Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
         C *acc = (C *)r->hacc.p;
-        const unsigned blocks = (unsigned)std::min<long>((hist_threads + 255) / 256, 16L * p->ctx->sms);
+        const unsigned blocks = hist_blocks(r, 32);
         if (!p->capturing) p->kt.begin(st, MOT_K_Z_HISTORY);
+        if (!nptr) {
+            MOT_TRY(hist_partial<T>(r, st, nullptr, 0, blocks));
+            r->hpart_ok = false;  // hpart now holds this step's partial sum, not the next one's
+        }
         count_launch();
-        k_hist_acc<T><<<blocks, 256, 0, st>>>((const C *)r->ring.p, Lh_of<T>(p), acc, Mz, My, H, oc, r->B, p->ell, r->n,
-                                            kmax, nptr);
+        k_hist_acc<T><<<blocks, 256, 0, st>>>((const C *)r->ring.p, Lh_of<T>(p), (const C *)r->hpart.p, acc, Mz, My, H,
+                                              oc, r->B, p->ell, r->n, 1, 1, nptr, 0);
         MOT_CHECK_LAUNCH();
+        if (nptr) {
+            MOT_CUDA_TRY(cudaEventRecord(r->hfork, st));
+            MOT_CUDA_TRY(cudaStreamWaitEvent(r->hside, r->hfork, 0));
+            const int bt = hist_side_threads();
+            MOT_TRY(hist_partial<T>(r, r->hside, nptr, 1, hist_blocks(r, hist_side_per_sm_x2(), bt), bt, hist_side_mode()));
+            MOT_CUDA_TRY(cudaEventRecord(r->hjoin, r->hside));
+            r->hjoin_open = true;
+        }
         const long zp = (long)My * H;
         if (col_r<T, +1>(acc, Bf, tz, (int)zp, Mz, Nz, r->B * 3, (long)Mz * zp, (long)Nz * zp, st)) MOT_CHECK_LAUNCH();
         else MOT_TRY((launch_axis<T, +1>(acc, Bf, tz, H, Mz, Nz, r->B * 3, My, (long)Mz * zp, H, zp, (long)Nz * zp, H, zp, st)));
@@ -1977,6 +2060,10 @@ mot_status build_step_graph(mot_run *r) {
             r->k_outer -= r->k_inner;  // the nested loop body is counted per iteration
             MOT_TRY(ring_push<float>(r, st, nptr));
         }
+        if (r->hjoin_open) {  // the next step's partial history sum is part of this step
+            MOT_CUDA_TRY(cudaStreamWaitEvent(st, r->hjoin, 0));
+            r->hjoin_open = false;
+        }
         count_launch();
         k_step_end<<<1, 32, 0, st>>>(sd, (StepStatDev *)r->sstats.p, r->sstats_cap);
         MOT_CHECK_LAUNCH();
@@ -1993,7 +2080,13 @@ mot_status build_step_graph(mot_run *r) {
     r->k_fixed = (int)captured - r->k_outer - r->k_inner;
     if (s != MOT_OK) return s;
     if (ce != cudaSuccess) MOT_FAIL(MOT_ECUDA, std::string("step capture: ") + cudaGetErrorString(ce));
-    cudaError_t ie = cudaGraphInstantiate(&r->step_exec, r->step_graph, 0);
+    // node priorities: the solve's kernels (captured on high-priority streams)
+    // go ahead of the side branch's blocks
+    cudaError_t ie = cudaGraphInstantiate(&r->step_exec, r->step_graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        ie = cudaGraphInstantiate(&r->step_exec, r->step_graph, 0);
+    }
     if (ie != cudaSuccess) MOT_FAIL(MOT_ECUDA, std::string("step graph instantiate: ") + cudaGetErrorString(ie));
     return MOT_OK;
 }
@@ -2086,6 +2179,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
     if ((s = dalloc(r->ring, ring_bytes)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->hacc, ring_bytes / p->ell)) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->hpart, ring_bytes / p->ell)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     for (int i = 0; i < 10; ++i)
@@ -2101,9 +2195,14 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->ctl, sizeof(int) * 4)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->ctr, sizeof(unsigned) * 4)) != MOT_OK) return fail(s);
     if (cudaMemset(r->ctr.p, 0, sizeof(unsigned) * 4) != cudaSuccess) return fail(MOT_ECUDA);
-    if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
-    if (cudaStreamCreateWithFlags(&r->cap2, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
-    if (cudaStreamCreateWithFlags(&r->cap3, cudaStreamNonBlocking) != cudaSuccess) return fail(MOT_ECUDA);
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithPriority(&r->cap, cudaStreamNonBlocking, prio_hi) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithPriority(&r->cap2, cudaStreamNonBlocking, prio_hi) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithPriority(&r->cap3, cudaStreamNonBlocking, prio_hi) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaStreamCreateWithPriority(&r->hside, cudaStreamNonBlocking, prio_lo) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaEventCreateWithFlags(&r->hfork, cudaEventDisableTiming) != cudaSuccess) return fail(MOT_ECUDA);
+    if (cudaEventCreateWithFlags(&r->hjoin, cudaEventDisableTiming) != cudaSuccess) return fail(MOT_ECUDA);
     r->sstats_cap = 1024;
     if ((s = dalloc(r->sdev, sizeof(StepDev))) != MOT_OK) return fail(s);
     if ((s = dalloc(r->sstats, sizeof(StepStatDev) * r->sstats_cap)) != MOT_OK) return fail(s);
@@ -2143,6 +2242,7 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
         // device step index follows the host's
         long long n0 = r->n;
         MOT_CUDA_TRY(cudaMemcpyAsync(r->sdev.p, &n0, sizeof(long long), cudaMemcpyHostToDevice, st));
+        MOT_TRY(hist_prime(r, st));
         int done = 0;
         while (done < nsteps) {
             const int chunk = std::min(nsteps - done, r->sstats_cap);
@@ -2384,6 +2484,7 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->r);
     dfree(r->ring);
     dfree(r->hacc);
+    dfree(r->hpart);
     dfree(r->wsAh);
     dfree(r->wsBh);
     for (int i = 0; i < 10; ++i) dfree(r->kv[i]);
@@ -2412,6 +2513,9 @@ void mot_run_destroy(mot_run *r) {
     if (r->cap) cudaStreamDestroy(r->cap);
     if (r->cap2) cudaStreamDestroy(r->cap2);
     if (r->cap3) cudaStreamDestroy(r->cap3);
+    if (r->hside) cudaStreamDestroy(r->hside);
+    if (r->hfork) cudaEventDestroy(r->hfork);
+    if (r->hjoin) cudaEventDestroy(r->hjoin);
     delete r;
 }
 

@@ -27,7 +27,17 @@ struct TfqmrScal {
     // so FP32 kernels read them without FP64 arithmetic:
     // alpha, theta^2 eta / alpha, eta_prev, beta
     float f_alpha, f_coef, f_eta_prev, f_beta;
+    // stagnation test (inner FP32 solves of the mixed form): tau at half step
+    // m_ck; stag = 1 enables it
+    double tau_ck;
+    int m_ck, stag;
 };
+
+// an inner solve whose tau has not halved over kStagHalfSteps half steps has
+// met its precision's floor: it stops (conv 2) and the FP64 refinement goes on
+// from the true residual
+constexpr int kStagHalfSteps = 16;
+constexpr double kStagRatio = 0.5;
 
 __host__ __device__ inline void refresh_coefs(TfqmrScal &s) {
     s.f_alpha = (float)s.alpha;
@@ -116,7 +126,7 @@ __device__ __forceinline__ double reduce_parts(const double *part, int b) {
 
 // ---- initialisation: r = b - A x0 already in w; tau = ||w||, rho = tau^2 --
 // grid B, block 32
-__global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol) {
+__global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol, int stag) {
     const int b = blockIdx.x;
     double r2 = reduce_parts(part_r2, b);
     double b2 = reduce_parts(part_b2, b);
@@ -136,6 +146,9 @@ __global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double 
         s.conv = b2 == 0.0 ? 3 : ((s.tau <= s.tolabs || r2 == 0.0) ? 1 : 0);
         s.pending = 0;
         s.pad = 0;
+        s.tau_ck = s.tau;
+        s.m_ck = 0;
+        s.stag = stag;
         refresh_coefs(s);
         sc[b] = s;
     }
@@ -205,6 +218,11 @@ __device__ __forceinline__ void half_scalars(TfqmrScal &s, double w2) {
     s.pending = 1;
     s.m += 1;
     if (s.tau * sqrt((double)s.m + 1.0) <= s.tolabs) s.conv = 2;
+    else if (s.stag && s.m - s.m_ck >= kStagHalfSteps) {
+        if (s.tau > kStagRatio * s.tau_ck) s.conv = 2;
+        s.tau_ck = s.tau;
+        s.m_ck = s.m;
+    }
     refresh_coefs(s);
 }
 

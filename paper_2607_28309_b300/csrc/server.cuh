@@ -85,7 +85,7 @@ size_t serve_estimate(const ServeJob &j) {
     b += (size_t)(ell + 1) * 6 * (Mh[2] / 2 + 1) * (Mh[1] / 2 + 1) * Hh * (mixed ? 4 : 8);  // history spectra
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + M0[1]) * H0 * 16;                        // product workspace
     b += 5 * n3 * 8 + 10 * n3 * (mixed ? 4 : 8) + (mixed ? 2 * n3 * 4 : 0);               // J, b, r, Krylov
-    b += (size_t)ell * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;                              // history ring
+    b += (size_t)(ell + 2) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum and partial sum
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + Mh[1]) * Hh * cs;                       // history workspace
     return b + b / 10 + ((size_t)64 << 20);
 }
@@ -158,6 +158,7 @@ mot_status serve_launch(ServeJob *j) {
     }
     MOT_CUDA_TRY(cudaMemsetAsync((char *)r->sdev.p + offsetof(StepDev, nstat), 0, sizeof(int), st));
     MOT_CUDA_TRY(cudaEventRecord(j->e0, st));
+    MOT_TRY(hist_prime(r, st));
     MOT_CUDA_TRY(cudaGraphLaunch(r->step_exec, st));
     MOT_CUDA_TRY(cudaEventRecord(j->e1, st));
     r->n += 1;

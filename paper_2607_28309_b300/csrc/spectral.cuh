@@ -746,9 +746,12 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// history accumulation (Eq. 3), streaming: acc_q(kz, ky, kx) =
-// sum_{k=1..kmax} sum_p Lambda_k,qp(kz, ky, kx) Jhat_{n-k},p(kz, ky, kx) on the
-// full Mh grid, in [B][3][Mz][My][H].  One thread per (b, fz <= Mz/2, j <=
+// history accumulation (Eq. 3), streaming: acc_q(kz, ky, kx) = base_q +
+// sum_{k=klo..kend} sum_p Lambda_k,qp(kz, ky, kx) Jhat_{m-k},p(kz, ky, kx), kend =
+// min(m, ell, kcap), on the full Mh grid, in [B][3][Mz][My][H] (base optional,
+// same layout).  A step's sum is taken as the lags 2.. partial sum, then lag 1
+// added onto it: the partial sum of step m+1 needs no J_m, so the step graph
+// computes it beside step m's solve.  With nptr, m = *nptr + dm.  One thread per (b, fz <= Mz/2, j <=
 // My/2, kx): the up to four rows (kz, ky) in {fz, Mz - fz} x {j, My - j} share
 // the octant value Lambda_k(fz, j, kx) (the mixed components change sign with
 // the folded axis), so every Lambda_k value and every ring value is read once;
@@ -757,16 +760,21 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
 // ---------------------------------------------------------------------------
 constexpr int kHistPrefetch = 2;  // lags ahead
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// Mode 0: plain loads with L2 prefetch; 1: evict-first loads (ld.global.cs)
+// with prefetch; 2: evict-first loads, no prefetch (a branch beside other work)
+template <int Mode, typename V> __device__ __forceinline__ V hist_ld(const V *p) {
+    if constexpr (Mode == 0) return *p;
+    else return __ldcs(p);
+}
 
-template <typename T>
+template <typename T, int Mode = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
-                                                  cplx<T> *__restrict__ acc, int Mz, int My, int H, Octant oc,
-                                                  int nrhs, int ell, long n, int kmax,
-                                                  const long long *__restrict__ nptr) {
-    if (nptr) {  // graph mode: step index from device memory
-        n = (long)*nptr;
-        kmax = (int)(n < ell ? n : ell);
-    }
+                                                  const cplx<T> *__restrict__ base, cplx<T> *__restrict__ acc, int Mz,
+                                                  int My, int H, Octant oc, int nrhs, int ell, long m, int klo,
+                                                  int kcap, const long long *__restrict__ nptr, int dm) {
+    if (nptr) m = (long)*nptr + dm;  // graph mode: step index from device memory
+    int kend = (int)(m < ell ? m : ell);
+    if (kend > kcap) kend = kcap;
     using C = cplx<T>;
     const int hz = Mz / 2 + 1, hy = My / 2 + 1;
     const unsigned total = (unsigned)nrhs * hz * hy * H;
@@ -795,13 +803,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) a[r][q] = cmake<C>(T(0), T(0));
+            for (int q = 0; q < 3; ++q) a[r][q] = base ? base[off[r] + q * slot_comp] : cmake<C>(T(0), T(0));
         const long lidx = ((long)fz * oc.Ky + j) * oc.H + kx;
-        long s = (n - 1) % ell;
+        long s = (m - klo) % ell;
         if (s < 0) s += ell;
 #pragma unroll 2
-        for (int k = 1; k <= kmax; ++k) {
-            if (k + kHistPrefetch <= kmax) {  // L2 prefetch of lag k + kHistPrefetch: more loads in flight per SM
+        for (int k = klo; k <= kend; ++k) {
+            if (Mode != 2 && k + kHistPrefetch <= kend) {  // L2 prefetch of lag k + kHistPrefetch: more loads in flight per SM
                 long sp = s - kHistPrefetch;
                 if (sp < 0) sp += ell;
                 const C *Rp = ring + sp * slot_size;
@@ -814,13 +822,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
                 for (int c6 = 0; c6 < 6; ++c6) prefetch_l2(Lp + c6 * cs);
             }
             const T *L = Lh + (long)k * 6 * cs + lidx;
-            const T gxx = L[0], gyy = L[cs], gzz = L[2 * cs], gxy = L[3 * cs], gxz = L[4 * cs], gyz = L[5 * cs];
+            const T gxx = hist_ld<Mode>(L), gyy = hist_ld<Mode>(L + cs), gzz = hist_ld<Mode>(L + 2 * cs);
+            const T gxy = hist_ld<Mode>(L + 3 * cs), gxz = hist_ld<Mode>(L + 4 * cs), gyz = hist_ld<Mode>(L + 5 * cs);
             const C *R = ring + s * slot_size;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
                 const T exy = sy * gxy, exz = sz * gxz, eyz = sy * sz * gyz;
-                const C u0 = R[off[r]], u1 = R[off[r] + slot_comp], u2 = R[off[r] + 2 * slot_comp];
+                const C u0 = hist_ld<Mode>(R + off[r]), u1 = hist_ld<Mode>(R + off[r] + slot_comp);
+                const C u2 = hist_ld<Mode>(R + off[r] + 2 * slot_comp);
                 a[r][0] = cmake<C>(a[r][0].x + gxx * u0.x + exy * u1.x + exz * u2.x, a[r][0].y + gxx * u0.y + exy * u1.y + exz * u2.y);
                 a[r][1] = cmake<C>(a[r][1].x + exy * u0.x + gyy * u1.x + eyz * u2.x, a[r][1].y + exy * u0.y + gyy * u1.y + eyz * u2.y);
                 a[r][2] = cmake<C>(a[r][2].x + exz * u0.x + eyz * u1.x + gzz * u2.x, a[r][2].y + exz * u0.y + eyz * u1.y + gzz * u2.y);

@@ -143,6 +143,38 @@ def test_step_drivers_agree(ctx, orc):
         assert _mot_errors(J[1], J[0]).max() <= 1e-12, precision
 
 
+def test_steps_in_several_calls_match_one_call(ctx):
+    """The step graph takes each step's lags 2.. history partial sum from the
+    previous step (computed beside its solve); the first graph step of every
+    mot_run_step call computes it in front.  Any split of a march into calls
+    gives the same currents bit for bit, past the history length."""
+    N = (9, 7, 8)
+    eps = synthetic.block_eps(N, 3, 2.0, 5.0, 8)
+    alpha, steps = 8.0, 16
+    exc = [synthetic.pulse(steps, alpha)]
+    nv = int(np.prod(N))
+    for precision in (mot.MOT_FP64, mot.MOT_MIXED):
+        prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+        try:
+            J = {}
+            for split in ((steps,), (1, 4, 2, 9), (3, 1, 1, 11)):
+                run = mot.mot_run_create(prob, exc, precision)
+                try:
+                    Js, k = np.zeros((steps, 1, 3, nv)), 0
+                    for c in split:
+                        mot.mot_run_step(run, c, Js[k:k + c])
+                        k += c
+                finally:
+                    mot.mot_run_destroy(run)
+                J[split] = Js
+            ref = J[(steps,)]
+            assert np.abs(ref[-1]).max() > 0
+            for split, Js in J.items():
+                assert np.array_equal(Js, ref), (precision, split)
+        finally:
+            mot.mot_problem_destroy(prob)
+
+
 def test_zero_contrast_gives_zero_current(ctx):
     N = (7, 6, 5)
     J = _march_pair(ctx, None, N, np.ones(N[::-1]), 4.0, [synthetic.pulse(20, 4.0)], 20, mot.MOT_FP64)
