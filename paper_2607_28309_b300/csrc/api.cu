@@ -479,6 +479,33 @@ mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw
     return MOT_OK;
 }
 
+// the chain kernels of a Z0 product (plane passes, z pass) go out with
+// programmatic dependent launch: the next kernel's blocks start while the
+// previous kernel finishes (its last blocks and its reduction tail) and wait on
+// the device; MOTJVIE_PDL=0 turns it off (timing comparisons)
+inline bool chain_pdl_on() {
+    static const bool f = !(getenv("MOTJVIE_PDL") && atoi(getenv("MOTJVIE_PDL")) == 0);
+    return f;
+}
+template <typename... KArgs, typename... Args>
+void launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    if (!chain_pdl_on()) {
+        kern<<<grid, block, smem, st>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);  // an error stays the last error, checked by the caller
+}
+
 // specialised plane kernels for the compiled (Mx, My) shapes; false -> generic
 template <class Src, typename T, int RX1, int RX2, int RY1, int RY2>
 bool xy_forward_r_go(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
@@ -486,7 +513,8 @@ bool xy_forward_r_go(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx
     if (smem > kSmemMax) return false;
     if (allow_smem<k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
     count_launch();
-    k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(x, out, Nx, Ny, twp<T>(tx), twp<T>(ty));
+    launch_chain(k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>, dim3(planes), dim3(512), smem, st, x, out, Nx, Ny,
+                 twp<T>(tx), twp<T>(ty));
     return true;
 }
 
@@ -497,7 +525,8 @@ bool xy_inverse_r_go(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, Axis
     if (smem > kSmemMax) return false;
     if (allow_smem<k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
     count_launch();
-    k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2><<<planes, 512, smem, st>>>(in, Nx, Ny, Nz, twp<T>(tx), twp<T>(ty), epi);
+    launch_chain(k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>, dim3(planes), dim3(512), smem, st, in, Nx, Ny, Nz,
+                 twp<T>(tx), twp<T>(ty), epi);
     return true;
 }
 
@@ -651,7 +680,8 @@ bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_
     dim3 grid((My * H + TC - 1) / TC, (unsigned)nrhs);
     if (!p->capturing) p->kt.begin(st, MOT_K_Z_GREEN);
     count_launch();
-    k_z_green_r<T, R1, R2, TC><<<grid, 3 * TC * R2, smem, st>>>(Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H, oc);
+    launch_chain(k_z_green_r<T, R1, R2, TC>, grid, dim3(3 * TC * R2), smem, st, Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H,
+                 oc);
     if (!p->capturing) p->kt.end(st);
     return true;
 }

@@ -299,4 +299,13 @@ template <typename C> __device__ __forceinline__ void load_twiddles(C *dst, cons
     for (int i = threadIdx.x; i < M; i += blockDim.x) dst[i] = src[i];
 }
 
+// programmatic dependent launch (the chain kernels of a Z0 product): a block
+// lets the next kernel of the stream start launching once its main work is
+// done (the next kernel's blocks then take the SMs this kernel's tail leaves
+// idle), and waits for the previous kernel's completion (and its memory) before
+// touching anything that kernel writes.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void chain_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void chain_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace mot

@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
     C *Bf = A + nb;   // [np][Mx]  then [H][PY]
     load_twiddles(twx, twx_g, Mx);
     load_twiddles(twy, twy_g, My);
+    chain_wait_prev();  // the source vectors and solver scalars come from the previous kernel
     __syncthreads();
     const long plane = blockIdx.x;
     auto src = x.bind(plane, (long)Ny * Nx);
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
 #pragma unroll
         for (int k2 = 0; k2 < RY2; ++k2) dst[(k1 + RY1 * k2) * H + kx] = u[k2];
     }
+    chain_launch_next();  // main work done: the next kernel may start launching
     x.finish(src, plane, (long)Ny * Nx);
 }
 
@@ -387,6 +389,7 @@ __global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict_
     C *Bf = A + nb;
     load_twiddles(twx, twx_g, Mx);
     load_twiddles(twy, twy_g, My);
+    chain_wait_prev();  // the planes come from the previous kernel
     __syncthreads();
     const long plane = blockIdx.x;
     const C *src = in + plane * (long)My * H;
@@ -457,6 +460,7 @@ __global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict_
         const C z = Bf[(y >> 1) * PX + e];
         return (y & 1) ? z.y : z.x;
     });
+    chain_launch_next();  // main work done: the next kernel may start launching
     epi.finish(pe, plane);
 }
 
@@ -660,6 +664,7 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
         }
     }
     load_twiddles(tw, tw_g, M);
+    chain_wait_prev();  // the planes come from the previous kernel (Lambda0 and the twiddles do not)
     __syncthreads();
     // ---- stage A
     {
@@ -728,6 +733,7 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
         }
     }
     __syncthreads();
+    chain_launch_next();  // only the last stage and the stores remain
     // ---- stage A': inverse R1-point DFT over k1, rows z = t + R2 m < Nz
     {
         C v[R1];
