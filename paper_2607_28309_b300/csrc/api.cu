@@ -1402,11 +1402,18 @@ template <typename V> mot_status build_loop_graph(mot_run *r, V *x, LoopGraph &G
     return MOT_OK;
 }
 
+// the solve start from x0 = 0 runs as two kernels plus a product (the plane
+// passes carry v = Z0 y1 and the first alpha)
+template <typename V> bool fused_start(const mot_problem *p) { return z0_planes_fit<V>(p); }
+
 // start of a solve on st: r0 = rhs - Z0 x0 into w (x0 = 0 if zero_x0), y1 = r* =
 // w, d = 0, tau and rho, x = 0 where rhs = 0, v = Z0 y1 and the first alpha.
-// *mvps: products applied.
+// With src64 (zero_x0 and fused_start only) the right-hand side is 2^-e src64,
+// e from the squared norms n2 (the mixed form's correction solve), and rhs is
+// not read.  *mvps: products applied.
 template <typename V>
-mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, cudaStream_t st, int *mvps) {
+mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, cudaStream_t st, int *mvps,
+                       const double *src64 = nullptr, const double *n2 = nullptr) {
     mot_problem *p = r->p;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
@@ -1414,6 +1421,22 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B), gr(kRedBlocks, B);
     *mvps = 1;
+    if (src64 && !(zero_x0 && fused_start<V>(p))) MOT_FAIL(MOT_EINVAL, "scaled start needs the fused path");
+    if (zero_x0 && fused_start<V>(p)) {
+        unsigned *ctr = (unsigned *)r->ctr.p;
+        const int stag = sizeof(V) == 4 ? 1 : 0;  // FP32 solves stop at stagnation
+        count_launch();
+        if (src64)
+            k_tfqmr_start_zero<V, double><<<gr, kRedThreads, 0, st>>>(src64, n2, x, k.v[kW], k.v[kY1], k.v[kRS],
+                                                                      k.v[kD], L, k.p1, k.sc, tol, stag, ctr + 3);
+        else
+            k_tfqmr_start_zero<V, V><<<gr, kRedThreads, 0, st>>>(rhs, nullptr, x, k.v[kW], k.v[kY1], k.v[kRS], k.v[kD],
+                                                                 L, k.p1, k.sc, tol, stag, ctr + 3);
+        MOT_CHECK_LAUNCH();
+        EpiV<V> ev = {k.v[kY1], k.v[kAY1], eps_of<V>(p), k.v[kV], k.v[kAY2], k.v[kRS], k.sc, k.p3, 3 * p->N[2],
+                      ctr + 2, (int *)r->ctl.p, cudaGraphConditionalHandle{}, 0, 1};
+        return z0_product<V, V>(p, (const V *)k.v[kY1], B, p->wsA.p, p->wsB.p, ev, st);
+    }
     if (zero_x0) {
         MOT_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
         MOT_CUDA_TRY(cudaMemcpyAsync(k.v[kW], rhs, sizeof(V) * n, cudaMemcpyDeviceToDevice, st));
@@ -1455,7 +1478,7 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
 // iters_out: iterations (max over the batch); mvps_out: Z0 products applied.
 template <typename V>
 mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
-                 bool *conv_out, int *mvps_out) {
+                 bool *conv_out, int *mvps_out, const double *src64 = nullptr, const double *n2 = nullptr) {
     mot_problem *p = r->p;
     cudaStream_t st = p->ctx->stream;
     const int B = r->B;
@@ -1463,7 +1486,7 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B);
     int mvps = 0;
-    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &mvps));
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &mvps, src64, n2));
     int ctl_h[2] = {0, maxit};
     MOT_CUDA_TRY(cudaMemcpyAsync(r->ctl.p, ctl_h, sizeof(ctl_h), cudaMemcpyHostToDevice, st));
     if (p->opt.graph == 2) {
@@ -1704,9 +1727,8 @@ mot_status norms(mot_run *r, const double *v, double *out_host) {
     cudaStream_t st = p->ctx->stream;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     count_launch();
-    k_dot_part<double, double><<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, v, L, (double *)r->part1.p);
-    count_launch();
-    k_finish_dot<<<r->B, 32, 0, st>>>((const double *)r->part1.p, (double *)r->dots.p);
+    k_norm2<<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, L, (double *)r->part1.p, (double *)r->dots.p,
+                                                          (unsigned *)r->ctr.p + 3);
     MOT_CHECK_LAUNCH();
     MOT_CUDA_TRY(cudaMemcpyAsync(out_host, r->dots.p, sizeof(double) * r->B, cudaMemcpyDeviceToHost, st));
     MOT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1770,13 +1792,18 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             if (done || sweeps == p->opt.max_refine) break;
             // r->dots holds the squared residual norms (norms above)
             const dim3 gs(grid_for(L), r->B);
-            count_launch();
-            k_convert_scaled<<<gs, 256, 0, st>>>(r32, (const double *)r->r.p, (const double *)r->dots.p, L);
-            MOT_CHECK_LAUNCH();
             int it;
             bool c;
             int nm;
-            MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm));
+            if (fused_start<float>(p)) {  // the start kernel scales and converts r itself
+                MOT_TRY(tfqmr<float>(r, c32, nullptr, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm,
+                                     (const double *)r->r.p, (const double *)r->dots.p));
+            } else {
+                count_launch();
+                k_convert_scaled<<<gs, 256, 0, st>>>(r32, (const double *)r->r.p, (const double *)r->dots.p, L);
+                MOT_CHECK_LAUNCH();
+                MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm));
+            }
             mvps += nm;
             iters += it;
             count_launch();
@@ -1932,9 +1959,7 @@ mot_status dev_norms2(mot_run *r, const double *v, double *out, cudaStream_t st)
     mot_problem *p = r->p;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     count_launch();
-    k_dot_part<double, double><<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, v, L, (double *)r->part1.p);
-    count_launch();
-    k_finish_dot<<<r->B, 32, 0, st>>>((const double *)r->part1.p, out);
+    k_norm2<<<dim3(kRedBlocks, r->B), kRedThreads, 0, st>>>(v, L, (double *)r->part1.p, out, (unsigned *)r->ctr.p + 3);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
@@ -1990,14 +2015,15 @@ mot_status while_insert(cudaStream_t st, cudaStream_t bst, const WhileNode &w, F
 // body captured on bst, flush), solve statistics into the step record
 template <typename V>
 mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, cudaStream_t st,
-                         cudaStream_t bst, int mark_notconv) {
+                         cudaStream_t bst, int mark_notconv, const double *src64 = nullptr,
+                         const double *n2 = nullptr) {
     mot_problem *p = r->p;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B);
     int init_mvps = 1;
-    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &init_mvps));
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &init_mvps, src64, n2));
     WhileNode w;
     MOT_TRY(while_handle(st, w, 1));
     count_launch();
@@ -2072,10 +2098,15 @@ mot_status build_step_graph(mot_run *r) {
             MOT_TRY(while_insert(st, r->cap2, wo, [&](cudaStream_t cs) -> mot_status {
                 // r->r2 holds the squared residual norms (dev_norms2 before the test)
                 const dim3 gs(grid_for(L), r->B);
-                count_launch();
-                k_convert_scaled<<<gs, 256, 0, cs>>>(r32, (const double *)r->r.p, (const double *)r->r2.p, L);
-                MOT_CHECK_LAUNCH();
-                MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0));
+                if (fused_start<float>(p)) {  // the start kernel scales and converts r itself
+                    MOT_TRY(tfqmr_capture<float>(r, c32, nullptr, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3,
+                                                 0, (const double *)r->r.p, (const double *)r->r2.p));
+                } else {
+                    count_launch();
+                    k_convert_scaled<<<gs, 256, 0, cs>>>(r32, (const double *)r->r.p, (const double *)r->r2.p, L);
+                    MOT_CHECK_LAUNCH();
+                    MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0));
+                }
                 count_launch();
                 k_add_scaled<<<gs, 256, 0, cs>>>((double *)r->J.p, c32, (const double *)r->r2.p, L);
                 MOT_CHECK_LAUNCH();

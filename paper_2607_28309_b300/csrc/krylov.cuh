@@ -125,33 +125,35 @@ __device__ __forceinline__ double reduce_parts(const double *part, int b) {
 }
 
 // ---- initialisation: r = b - A x0 already in w; tau = ||w||, rho = tau^2 --
+// (conv 3: b = 0, whose solution is 0 whatever x0 is; x still to be zeroed)
+__device__ __forceinline__ TfqmrScal init_scalars(double r2, double b2, double tol, int stag) {
+    TfqmrScal s;
+    s.tau = sqrt(r2);
+    s.rho = r2;
+    s.theta = 0.0;
+    s.eta = 0.0;
+    s.alpha = 0.0;
+    s.beta = 0.0;
+    s.eta_prev = 0.0;
+    s.bnorm = sqrt(b2);
+    s.tolabs = tol * s.bnorm;
+    s.m = 0;
+    s.conv = b2 == 0.0 ? 3 : ((s.tau <= s.tolabs || r2 == 0.0) ? 1 : 0);
+    s.pending = 0;
+    s.pad = 0;
+    s.tau_ck = s.tau;
+    s.m_ck = 0;
+    s.stag = stag;
+    refresh_coefs(s);
+    return s;
+}
+
 // grid B, block 32
 __global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol, int stag) {
     const int b = blockIdx.x;
     double r2 = reduce_parts(part_r2, b);
     double b2 = reduce_parts(part_b2, b);
-    if (threadIdx.x == 0) {
-        TfqmrScal s;
-        s.tau = sqrt(r2);
-        s.rho = r2;
-        s.theta = 0.0;
-        s.eta = 0.0;
-        s.alpha = 0.0;
-        s.beta = 0.0;
-        s.eta_prev = 0.0;
-        s.bnorm = sqrt(b2);
-        s.tolabs = tol * s.bnorm;
-        s.m = 0;
-        // b = 0 has the solution 0 whatever x0 is (conv = 3 zeroes x)
-        s.conv = b2 == 0.0 ? 3 : ((s.tau <= s.tolabs || r2 == 0.0) ? 1 : 0);
-        s.pending = 0;
-        s.pad = 0;
-        s.tau_ck = s.tau;
-        s.m_ck = 0;
-        s.stag = stag;
-        refresh_coefs(s);
-        sc[b] = s;
-    }
+    if (threadIdx.x == 0) sc[b] = init_scalars(r2, b2, tol, stag);
 }
 
 // x = 0 for right-hand sides with b = 0 (conv == 3), then mark them done
@@ -681,6 +683,7 @@ template <typename V> struct EpiV {
     int *ctl;
     cudaGraphConditionalHandle h;
     int use_h;
+    int start;  // the solve's first product: v = Ay1, alpha from (r*, v), no loop test
     struct Plane {
         const V *y1;
         V *Ay1;
@@ -690,12 +693,13 @@ template <typename V> struct EpiV {
         V be;
         int skip;
         typename AccOf<V>::type acc;
+        int start;
         __device__ __forceinline__ void operator()(int i, V g) {
             const V e = eps[i];
             const V ay = e * V(0.5) * y1[i] - (e - V(1)) * g;
             Ay1[i] = ay;
             if (skip) return;
-            const V vn = ay + be * (Ay2[i] + be * v[i]);
+            const V vn = start ? ay : ay + be * (Ay2[i] + be * v[i]);
             v[i] = vn;
             acc += rs[i] * vn;
         }
@@ -707,22 +711,27 @@ template <typename V> struct EpiV {
             for (int k = 0; k < W; ++k) ay[k] = e[k] * V(0.5) * yv[k] - (e[k] - V(1)) * g[k];
             stv<W>(Ay1 + i, ay);
             if (skip) return;
-            V a2[W], vv[W], rr[W];
-            ldv<W>(a2, Ay2 + i);
-            ldv<W>(vv, v + i);
+            V vv[W], rr[W];
             ldv<W>(rr, rs + i);
+            if (start) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                vv[k] = ay[k] + be * (a2[k] + be * vv[k]);
-                acc += rr[k] * vv[k];
+                for (int k = 0; k < W; ++k) vv[k] = ay[k];
+            } else {
+                V a2[W];
+                ldv<W>(a2, Ay2 + i);
+                ldv<W>(vv, v + i);
+#pragma unroll
+                for (int k = 0; k < W; ++k) vv[k] = ay[k] + be * (a2[k] + be * vv[k]);
             }
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc += rr[k] * vv[k];
             stv<W>(v + i, vv);
         }
     };
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
         const TfqmrScal s = sc[(int)(plane / P)];
-        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, Coefs<V>::be(s), s.conv != 0, 0};
+        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, Coefs<V>::be(s), s.conv != 0, 0, start};
     }
     __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
         __shared__ int active;
@@ -749,11 +758,13 @@ template <typename V> struct EpiV {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int it = ctl[0] + 1;
-            ctl[0] = it;
-            const int cont = (active && it < ctl[1]) ? 1 : 0;
-            if (use_h) cudaGraphSetConditional(h, (unsigned)cont);
-            else ctl[2] = cont;
+            if (!start) {
+                const int it = ctl[0] + 1;
+                ctl[0] = it;
+                const int cont = (active && it < ctl[1]) ? 1 : 0;
+                if (use_h) cudaGraphSetConditional(h, (unsigned)cont);
+                else ctl[2] = cont;
+            }
             *ctr = 0u;
         }
     }
@@ -889,6 +900,72 @@ __global__ void k_add_scaled(double *__restrict__ J, const float *__restrict__ c
     const long o = (long)b * L;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
         J[o + i] += ldexp((double)c[o + i], e);
+}
+
+// start of a solve from x0 = 0 in one kernel: w = y1 = r* = rhs, x = d = 0, the
+// block partials of ||rhs||^2, and in the last block the scalar
+// initialisation (tau = ||rhs||; b = 0 is done at once, x being 0).  rhs =
+// src, or with n2 given 2^-e src (the scaled residual of the mixed form's
+// correction solve, as k_convert_scaled forms it).  The partials are the
+// ones k_dot_part forms (same grid, same order).  grid (kRedBlocks, B)
+template <typename V, typename S>
+__global__ void __launch_bounds__(kRedThreads) k_tfqmr_start_zero(const S *__restrict__ src,
+                                                                  const double *__restrict__ n2, V *__restrict__ x,
+                                                                  V *__restrict__ w, V *__restrict__ y1,
+                                                                  V *__restrict__ rs, V *__restrict__ d, long L,
+                                                                  double *__restrict__ part,
+                                                                  TfqmrScal *__restrict__ sc, double tol, int stag,
+                                                                  unsigned *ctr) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const long o = (long)b * L;
+    const int e = n2 ? pow2_exponent(n2[b]) : 0;
+    using A = typename AccOf<V>::type;
+    A s = A(0);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
+        const V v = n2 ? (V)ldexp((double)src[o + i], -e) : (V)src[o + i];
+        w[o + i] = v;
+        y1[o + i] = v;
+        rs[o + i] = v;
+        x[o + i] = V(0);
+        d[o + i] = V(0);
+        s += (A)v * (A)v;
+    }
+    const double bs = block_sum(s, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
+    if (!last_block(ctr, gridDim.x * gridDim.y)) return;
+    const int lane = threadIdx.x & 31, B = (int)gridDim.y;
+    for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
+        const double r2 = reduce_parts_lane(part, bb, lane);
+        if (lane == 0) {
+            TfqmrScal u = init_scalars(r2, r2, tol, stag);
+            if (u.conv == 3) u.conv = 1;
+            sc[bb] = u;
+        }
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+// ||v||^2 per right-hand side into out[b] in one kernel (the k_dot_part
+// partials, then the k_finish_dot reduction in the last block).  grid (kRedBlocks, B)
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const double *__restrict__ v, long L,
+                                                       double *__restrict__ part, double *__restrict__ out,
+                                                       unsigned *ctr) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    const double *pv = v + (long)b * L;
+    double s = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        s += pv[i] * pv[i];
+    const double bs = block_sum(s, sh);
+    if (threadIdx.x == 0) part[b * kRedBlocks + blockIdx.x] = bs;
+    if (!last_block(ctr, gridDim.x * gridDim.y)) return;
+    const int lane = threadIdx.x & 31, B = (int)gridDim.y;
+    for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
+        const double t = reduce_parts_lane(part, bb, lane);
+        if (lane == 0) out[bb] = t;
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
 }
 
 
