@@ -35,6 +35,15 @@ __host__ __device__ __forceinline__ unsigned int fdiv(unsigned int x, FastDiv f)
     return (unsigned int)(((unsigned long long)x * f.m) >> f.s);
 }
 
+// where a plane staged into shared memory puts element i: row pairs of rp = 2 Nx
+// elements, each followed by pad elements (pad 0: contiguous).  The padding
+// moves consecutive pencils (row pairs) of the x pass onto different banks.
+struct StageMap {
+    FastDiv frp;
+    int pad;
+    __device__ __forceinline__ int operator()(int i) const { return pad ? i + (int)fdiv((unsigned)i, frp) * pad : i; }
+};
+
 struct FftPlan {
     int M;
     int nstage;

@@ -404,7 +404,7 @@ template <typename V> struct SrcY1 {
         const V *w, *y2;
         V beta;
         int skip;
-        __device__ __forceinline__ void stage(V *sm, int n) const {
+        __device__ __forceinline__ void stage(V *sm, int n, StageMap m = StageMap{FastDiv{}, 0}) const {
             constexpr int W = PackW<V>::W;
             if (n % W == 0) {
                 for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
@@ -417,8 +417,9 @@ template <typename V> struct SrcY1 {
                         for (int k = 0; k < W; ++k) a[k] += beta * c[k];
                         stv<W>(y1 + j * W, a);
                     }
+                    V *dst = sm + m(j * W);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) sm[j * W + k] = a[k];
+                    for (int k = 0; k < W; ++k) dst[k] = a[k];
                 }
             } else {
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -428,7 +429,7 @@ template <typename V> struct SrcY1 {
                         a = w[i] + beta * y2[i];
                         y1[i] = a;
                     }
-                    sm[i] = a;
+                    sm[m(i)] = a;
                 }
             }
         }
@@ -486,7 +487,7 @@ template <typename V> struct SrcHalfA {
         V al, coef, ep;
         int pending, skip;
         typename AccOf<V>::type w2;
-        __device__ __forceinline__ void stage(V *sm, int n) {
+        __device__ __forceinline__ void stage(V *sm, int n, StageMap m = StageMap{FastDiv{}, 0}) {
             constexpr int W = PackW<V>::W;
             if (n % W == 0) {
                 for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
@@ -515,13 +516,14 @@ template <typename V> struct SrcHalfA {
                         stv<W>(d + o, dd);
                         stv<W>(y2 + o, yy);
                     }
+                    V *dst = sm + m((int)o);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) sm[o + k] = yy[k];
+                    for (int k = 0; k < W; ++k) dst[k] = yy[k];
                 }
             } else {
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     if (skip) {
-                        sm[i] = y2[i];
+                        sm[m(i)] = y2[i];
                         continue;
                     }
                     const V dold = d[i], yv = y1[i];
@@ -532,7 +534,7 @@ template <typename V> struct SrcHalfA {
                     d[i] = yv + coef * dold;
                     const V y = yv - al * v[i];
                     y2[i] = y;
-                    sm[i] = y;
+                    sm[m(i)] = y;
                 }
             }
         }

@@ -114,17 +114,19 @@ template <typename TI> struct SrcPlain {
     const TI *x;
     struct Plane {
         const TI *p;
-        template <typename T> __device__ __forceinline__ void stage(T *sm, int n) const {
+        template <typename T>
+        __device__ __forceinline__ void stage(T *sm, int n, StageMap m = StageMap{FastDiv{}, 0}) const {
             constexpr int W = 16 / sizeof(T);
             if (n % W == 0) {
                 for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
                     TI v[W];
                     ldv<W>(v, p + (long)j * W);
+                    T *dst = sm + m(j * W);  // a pack never straddles a padded row pair
 #pragma unroll
-                    for (int k = 0; k < W; ++k) sm[j * W + k] = (T)v[k];
+                    for (int k = 0; k < W; ++k) dst[k] = (T)v[k];
                 }
             } else {
-                for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = (T)p[i];
+                for (int i = threadIdx.x; i < n; i += blockDim.x) sm[m(i)] = (T)p[i];
             }
         }
     };
@@ -300,20 +302,25 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
     const long plane = blockIdx.x;
     auto src = x.bind(plane, (long)Ny * Nx);
     T *stg = reinterpret_cast<T *>(Bf);  // the plane's Ny*Nx inputs (Bf is free until x stage B)
-    src.stage(stg, Ny * Nx);
+    // row pairs (the x pencils) padded by 8 elements where the packs allow it
+    // and Bf has room: consecutive pencils then start on different banks
+    const int pad = ((2 * Nx) % 4 == 0 && (long)np * (2 * Nx + 8) <= 2 * (long)nb) ? 8 : 0;
+    const int PP = 2 * Nx + pad;
+    src.stage(stg, Ny * Nx, StageMap{make_fastdiv((unsigned)(2 * Nx)), pad});
     __syncthreads();
     // x stage A: pencil p = rows (2p, 2p+1) as re/im, thread t < RX2 takes e = t + RX2 m
     for (int task = threadIdx.x; task < np * RX2; task += blockDim.x) {
         const int p = task / RX2, t = task - p * RX2;
         C v[RX1];
         const bool two = 2 * p + 1 < Ny;
+        const T *r0 = stg + p * PP;
 #pragma unroll
         for (int m = 0; m < RX1; ++m) {
             const int e = t + RX2 * m;
             T re = T(0), im = T(0);
             if (e < Nx) {
-                re = stg[(2 * p) * Nx + e];
-                if (two) im = stg[(2 * p + 1) * Nx + e];
+                re = r0[e];
+                if (two) im = r0[Nx + e];
             }
             v[m] = cmake<C>(re, im);
         }
@@ -323,21 +330,22 @@ __global__ void __launch_bounds__(512) k_xy_forward_r(Src x, cplx<T> *__restrict
     }
     __syncthreads();
     // x stage B: RX2-point DFTs -> natural order Z[k1 + RX1 k2] in Bf[p][.]
+    // (pencil fastest across the warp: rows PX apart fall on different banks)
     for (int task = threadIdx.x; task < np * RX1; task += blockDim.x) {
-        const int p = task / RX1, k1 = task - p * RX1;
+        const int k1 = task / np, p = task - k1 * np;
         C u[RX2];
 #pragma unroll
         for (int t = 0; t < RX2; ++t) u[t] = A[p * PX + k1 * RX2 + t];
         dft_small<RX2, -1>(u);
 #pragma unroll
-        for (int k2 = 0; k2 < RX2; ++k2) Bf[p * Mx + k1 + RX1 * k2] = u[k2];
+        for (int k2 = 0; k2 < RX2; ++k2) Bf[p * PX + k1 + RX1 * k2] = u[k2];
     }
     __syncthreads();
     // unpack the two real rows of each pencil into the half spectra, stored
     // transposed for the y pass: A[kx][y]
     for (int task = threadIdx.x; task < Ny * H; task += blockDim.x) {
         const int y = task / H, k = task - y * H;
-        const C *row = Bf + (y >> 1) * Mx;
+        const C *row = Bf + (y >> 1) * PX;
         C z = row[k], zm = cconj(row[k == 0 ? 0 : Mx - k]);
         C v;
         if ((y & 1) == 0) { C s2 = cadd(z, zm); v = cmake<C>(T(0.5) * s2.x, T(0.5) * s2.y); }
@@ -406,8 +414,9 @@ __global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict_
     }
     __syncthreads();
     // inverse y stage B: rows y = k1 + RY1 k2 < Ny kept, stored Bf[kx][y]
+    // (kx fastest across the warp: rows PY apart fall on different banks)
     for (int task = threadIdx.x; task < H * RY1; task += blockDim.x) {
-        const int kx = task / RY1, k1 = task - kx * RY1;
+        const int k1 = task / H, kx = task - k1 * H;
         C u[RY2];
 #pragma unroll
         for (int t = 0; t < RY2; ++t) u[t] = A[kx * PY + k1 * RY2 + t];
@@ -441,9 +450,9 @@ __global__ void __launch_bounds__(512) k_xy_inverse_r(const cplx<T> *__restrict_
             A[p * PX + k1 * RX2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(twx[t * k1])) : v[k1];
     }
     __syncthreads();
-    // inverse x stage B: natural order e = k1 + RX1 k2 into Bf[p][e]
+    // inverse x stage B: natural order e = k1 + RX1 k2 into Bf[p][e] (pencil fastest)
     for (int task = threadIdx.x; task < np * RX1; task += blockDim.x) {
-        const int p = task / RX1, k1 = task - p * RX1;
+        const int k1 = task / np, p = task - k1 * np;
         C u[RX2];
 #pragma unroll
         for (int t = 0; t < RX2; ++t) u[t] = A[p * PX + k1 * RX2 + t];
