@@ -506,6 +506,30 @@ void launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
     cudaLaunchKernelEx(&cfg, kern, args...);  // an error stays the last error, checked by the caller
 }
 
+// threads of a specialised plane-pass block.  512 threads shorten each stage
+// with few planes (one right-hand side: about one block per SM) and suit the
+// vector-heavy solver passes (the FP64 residual epilogue at 16 right-hand
+// sides: 162 us at 512 threads, 231 us at 384).  The plain FP32 product with
+// many waves of planes runs faster in smaller blocks, more of them resident
+// and fewer threads idle at the stage barriers (72^2 planes, 16 right-hand
+// sides: forward 53.4 / 50.5 / 44.8 us and inverse 56.1 / 51.4 / 55.0 us at
+// 512 / 384 / 256 threads).  MOTJVIE_XY_THREADS = 256 | 384 | 512 overrides,
+// for timing sweeps.
+inline int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v;
+    }();
+    return n;
+}
+inline int xy_threads(int planes, bool forward, bool plain32) {
+    static const int f = getenv("MOTJVIE_XY_THREADS") ? atoi(getenv("MOTJVIE_XY_THREADS")) : 0;
+    if (f == 256 || f == 384 || f == 512) return f;
+    if (!plain32 || planes < 4 * sm_count()) return 512;
+    return forward ? 256 : 384;
+}
+
 // specialised plane kernels for the compiled (Mx, My) shapes; false -> generic
 template <class Src, typename T, int RX1, int RX2, int RY1, int RY2>
 bool xy_forward_r_go(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx, AxisTw *ty, cudaStream_t st) {
@@ -513,7 +537,9 @@ bool xy_forward_r_go(Src x, cplx<T> *out, int planes, int Nx, int Ny, AxisTw *tx
     if (smem > kSmemMax) return false;
     if (allow_smem<k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
     count_launch();
-    launch_chain(k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>, dim3(planes), dim3(512), smem, st, x, out, Nx, Ny,
+    launch_chain(k_xy_forward_r<Src, T, RX1, RX2, RY1, RY2>, dim3(planes),
+                 dim3(xy_threads(planes, true, std::is_same<Src, SrcPlain<float>>::value && sizeof(T) == 4)), smem, st,
+                 x, out, Nx, Ny,
                  twp<T>(tx), twp<T>(ty));
     return true;
 }
@@ -525,7 +551,8 @@ bool xy_inverse_r_go(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, Axis
     if (smem > kSmemMax) return false;
     if (allow_smem<k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>>() != MOT_OK) return false;
     count_launch();
-    launch_chain(k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>, dim3(planes), dim3(512), smem, st, in, Nx, Ny, Nz,
+    launch_chain(k_xy_inverse_r<T, Epi, RX1, RX2, RY1, RY2>, dim3(planes),
+                 dim3(xy_threads(planes, false, std::is_same<Epi, EpiZ0<float, float>>::value)), smem, st, in, Nx, Ny, Nz,
                  twp<T>(tx), twp<T>(ty), epi);
     return true;
 }
