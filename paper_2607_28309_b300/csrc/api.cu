@@ -715,7 +715,7 @@ bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_
 
 // columns per block TC: 8 (measured fastest for one and for sixteen
 // right-hand sides on the 72^3 grid), 16 or 32 where that block would not
-// fit; MOTJVIE_Z_COLS = 8 | 16 | 32 forces one for timing sweeps
+// fit; MOTJVIE_Z_COLS = 4 | 8 | 16 | 32 forces one for timing sweeps
 template <typename T, int R1, int R2, int TC> constexpr bool z_tc_ok() {
     return 3 * TC * R2 <= 1024 && z_green_r_smem<T, R1, R2, TC>() <= kSmemMax;
 }
@@ -727,6 +727,8 @@ inline int z_cols_forced() {
 
 template <typename T, int R1, int R2> bool z_green_r_go(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
     const int f = z_cols_forced();
+    if constexpr (z_tc_ok<T, R1, R2, 4>())
+        if (f == 4) return z_green_r_tc<T, R1, R2, 4>(p, Bf, tz, nrhs, st);
     if constexpr (z_tc_ok<T, R1, R2, 32>())
         if (f == 32) return z_green_r_tc<T, R1, R2, 32>(p, Bf, tz, nrhs, st);
     if constexpr (z_tc_ok<T, R1, R2, 16>())
