@@ -592,8 +592,7 @@ bool xy_inverse_r(const cplx<T> *in, int planes, int Nx, int Ny, int Nz, AxisTw 
 // large for shared memory; false -> generic
 template <typename TI, typename T, int R1, int R2, int P>
 bool x_forward_r_go(const TI *x, cplx<T> *out, long nrows, int Nx, AxisTw *tw, cudaStream_t st) {
-    constexpr int M = R1 * R2;
-    const size_t smem = (size_t)(M + 2 * P * (M + 2)) * sizeof(cplx<T>);
+    constexpr size_t smem = x_r_smem<T, R1, R2, P>();
     if (smem > kSmemMax || allow_smem<k_x_forward_r<TI, T, R1, R2, P>>() != MOT_OK) return false;
     count_launch();
     k_x_forward_r<TI, T, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(x, out, Nx, twp<T>(tw));
@@ -602,8 +601,7 @@ bool x_forward_r_go(const TI *x, cplx<T> *out, long nrows, int Nx, AxisTw *tw, c
 
 template <typename T, class Epi, int R1, int R2, int P>
 bool x_inverse_r_go(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *tw, Epi epi, cudaStream_t st) {
-    constexpr int M = R1 * R2;
-    const size_t smem = (size_t)(M + 2 * P * (M + 2)) * sizeof(cplx<T>);
+    constexpr size_t smem = x_r_smem<T, R1, R2, P>();
     if (smem > kSmemMax || allow_smem<k_x_inverse_r<T, Epi, R1, R2, P>>() != MOT_OK) return false;
     count_launch();
     k_x_inverse_r<T, Epi, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(in, Nx, Ny, Nz, twp<T>(tw),

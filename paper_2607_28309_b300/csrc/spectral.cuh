@@ -118,12 +118,23 @@ template <typename TI> struct SrcPlain {
         __device__ __forceinline__ void stage(T *sm, int n, StageMap m = StageMap{FastDiv{}, 0}) const {
             constexpr int W = 16 / sizeof(T);
             if (n % W == 0) {
-                for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
-                    TI v[W];
-                    ldv<W>(v, p + (long)j * W);
-                    T *dst = sm + m(j * W);  // a pack never straddles a padded row pair
+                constexpr int U = 4;  // packs in flight per thread before any is stored
+                for (int j0 = threadIdx.x; j0 < n / W; j0 += U * blockDim.x) {
+                    TI v[U][W];
 #pragma unroll
-                    for (int k = 0; k < W; ++k) dst[k] = (T)v[k];
+                    for (int u = 0; u < U; ++u) {
+                        const int j = j0 + u * blockDim.x;
+                        if (j < n / W) ldv<W>(v[u], p + (long)j * W);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = j0 + u * blockDim.x;
+                        if (j < n / W) {
+                            T *dst = sm + m(j * W);  // a pack never straddles a padded row pair
+#pragma unroll
+                            for (int k = 0; k < W; ++k) dst[k] = (T)v[u][k];
+                        }
+                    }
                 }
             } else {
                 for (int i = threadIdx.x; i < n; i += blockDim.x) sm[m(i)] = (T)p[i];
@@ -1003,55 +1014,96 @@ __global__ void __launch_bounds__(256) k_x_inverse(const cplx<T> *__restrict__ i
 // task, one shared-memory exchange, as in the specialised plane kernels.
 // ---------------------------------------------------------------------------
 
+// Shared-memory layout of the row passes (bank-conflict free where the task
+// order allows; a bank holds 4 bytes, a half-warp's 16 complex FP32 accesses
+// are conflict-free when their indices differ mod 16).  A holds each pencil's
+// stage-A outputs t-major, (t, k1) at t R1 + k1, with pitch RS = R1 (mod 16),
+// so that stage B's task order p R1 + k1 maps to distinct indices mod 16;
+// stage B writes Bf with the same pitch.  Bf first holds the staged rows, row
+// pairs padded so that the next pencil continues the bank sequence: pitch
+// RSB >= 2H + pad2 with 2H + pad2 = R2 (mod 16) for the inverse pass's complex
+// spectra; the forward pass's real rows take 2 Nx + padf floats, 2 Nx + padf
+// = R2 (mod 32).
+template <int R1, int R2> __host__ __device__ constexpr int x_rs() {
+    return R1 * R2 + (((R1 - R1 * R2) % 16) + 16) % 16;
+}
+template <int R1, int R2> __host__ __device__ constexpr int x_rsb() {
+    constexpr int H2 = 2 * (R1 * R2 / 2 + 1), s = H2 + (((R2 - H2) % 16) + 16) % 16;
+    return s > x_rs<R1, R2>() ? s : x_rs<R1, R2>();
+}
+template <typename T, int R1, int R2, int P> __host__ __device__ constexpr size_t x_r_smem() {
+    return (size_t)(R1 * R2 + P * x_rs<R1, R2>() + P * x_rsb<R1, R2>()) * sizeof(cplx<T>);
+}
+
 // forward x pass: a block takes 2P consecutive rows of one (b, q, z) plane
 // (2P divides Ny), stages them with 16-byte loads, transforms the P row pairs
 // as complex sequences of length M (zero padded from Nx) and writes both rows'
 // half spectra, k < H, k fastest.  grid = nrows / (2P); block = P * R2;
-// smem = (M + 2 P (M + 2)) complex
+// smem = x_r_smem
 template <typename TI, typename T, int R1, int R2, int P>
 __global__ void __launch_bounds__(P * R2) k_x_forward_r(const TI *__restrict__ x, cplx<T> *__restrict__ out, int Nx,
                                                         const cplx<T> *__restrict__ tw_g) {
     using C = cplx<T>;
-    constexpr int M = R1 * R2, H = M / 2 + 1, RS = M + 2;
+    constexpr int M = R1 * R2, H = M / 2 + 1, RS = x_rs<R1, R2>(), RSB = x_rsb<R1, R2>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *A = tw + M;       // [P][RS]
-    C *Bf = A + P * RS;  // [P][RS]; first holds the staged 2P*Nx inputs
+    C *A = tw + M;       // [P][RS], (t, k1) at t R1 + k1
+    C *Bf = A + P * RS;  // [P][RSB]; first holds the staged 2P*Nx inputs
     load_twiddles(tw, tw_g, M);
     const long row0 = (long)blockIdx.x * 2 * P;
     T *stg = reinterpret_cast<T *>(Bf);
     const int n = 2 * P * Nx;
+    // row pairs padded by padf floats (0 where the padded rows would not fit)
+    int padf = ((R2 - 2 * Nx) % 32 + 32) % 32;
+    if ((long)P * (2 * Nx + padf) > 2L * P * RSB) padf = 0;
+    const int PP = 2 * Nx + padf;
+    const StageMap sm{make_fastdiv((unsigned)(2 * Nx)), padf};
     const TI *src = x + row0 * Nx;
     constexpr int W = 16 / sizeof(T);
     if (Nx % W == 0) {
-        for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
-            TI v[W];
-            ldv<W>(v, src + (long)j * W);
+        // four packs per thread in flight before any is stored (the block's
+        // loads are the pass's HBM reads: few blocks fit an SM)
+        constexpr int U = 4;
+        for (int j0 = threadIdx.x; j0 < n / W; j0 += U * blockDim.x) {
+            TI v[U][W];
 #pragma unroll
-            for (int k = 0; k < W; ++k) stg[j * W + k] = (T)v[k];
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < n / W) ldv<W>(v[u], src + (long)j * W);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < n / W) {
+                    T *dst = stg + sm(j * W);  // 2 Nx is a multiple of W: a pack stays in its row pair
+#pragma unroll
+                    for (int k = 0; k < W; ++k) dst[k] = (T)v[u][k];
+                }
+            }
         }
     } else {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) stg[i] = (T)src[i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) stg[sm(i)] = (T)src[i];
     }
     __syncthreads();
     {
         const int p = threadIdx.x / R2, t = threadIdx.x - p * R2;
+        const T *r0 = stg + p * PP;
         C v[R1];
 #pragma unroll
         for (int m = 0; m < R1; ++m) {
             const int e = t + R2 * m;
-            v[m] = e < Nx ? cmake<C>(stg[(2 * p) * Nx + e], stg[(2 * p + 1) * Nx + e]) : cmake<C>(T(0), T(0));
+            v[m] = e < Nx ? cmake<C>(r0[e], r0[Nx + e]) : cmake<C>(T(0), T(0));
         }
         dft_small<R1, -1>(v);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) A[p * RS + k1 * R2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], tw[t * k1]) : v[k1];
+        for (int k1 = 0; k1 < R1; ++k1) A[p * RS + t * R1 + k1] = (k1 > 0 && t > 0) ? cmul(v[k1], tw[t * k1]) : v[k1];
     }
     __syncthreads();
     for (int task = threadIdx.x; task < P * R1; task += blockDim.x) {
         const int p = task / R1, k1 = task - p * R1;
         C u[R2];
 #pragma unroll
-        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + k1 * R2 + t];
+        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + t * R1 + k1];
         dft_small<R2, -1>(u);
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) Bf[p * RS + k1 + R1 * k2] = u[k2];
@@ -1072,49 +1124,64 @@ __global__ void __launch_bounds__(P * R2) k_x_forward_r(const TI *__restrict__ x
 // inverse x pass with the epilogue: 2P consecutive rows of one plane (2P
 // divides Ny); Hermitian extension of each row pair, inverse DFT of length M,
 // rows' x < Nx to the epilogue (packs of 16 bytes when Nx allows).
-// grid = nrows / (2P); block = P * R2; smem = (M + 2 P (M + 2)) complex
+// grid = nrows / (2P); block = P * R2; smem = x_r_smem
 template <typename T, class Epi, int R1, int R2, int P>
 __global__ void __launch_bounds__(P * R2) k_x_inverse_r(const cplx<T> *__restrict__ in, int Nx, int Ny, int Nz,
                                                         const cplx<T> *__restrict__ tw_g, Epi epi) {
     using C = cplx<T>;
-    constexpr int M = R1 * R2, H = M / 2 + 1, RS = M + 2;
+    constexpr int M = R1 * R2, H = M / 2 + 1, RS = x_rs<R1, R2>(), RSB = x_rsb<R1, R2>();
+    constexpr int PH = 2 * H + ((R2 - 2 * H) % 16 + 16) % 16;  // padded row-pair pitch of the staged spectra
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *A = tw + M;       // [P][RS]
-    C *Bf = A + P * RS;  // [P][RS]; first holds the staged 2P*H spectra
+    C *A = tw + M;       // [P][RS], (t, k1) at t R1 + k1
+    C *Bf = A + P * RS;  // [P][RSB]; first holds the staged 2P*H spectra, row pairs PH apart
     load_twiddles(tw, tw_g, M);
     const long row0 = (long)blockIdx.x * 2 * P;
     const C *src = in + row0 * H;
     C *stg = Bf;
-    for (int i = threadIdx.x; i < 2 * P * H; i += blockDim.x) {
-        C v = src[i];
-        const int k = i % H;
-        if (k == 0 || 2 * k == M) v.y = T(0);  // DC and (even M) Nyquist bins of a real row are real
-        stg[i] = v;
+    constexpr int U = 8;  // loads in flight per thread before any is stored
+    for (int i0 = threadIdx.x; i0 < 2 * P * H; i0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < 2 * P * H) v[u] = src[i];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < 2 * P * H) {
+                const int k = i % H;
+                if (k == 0 || 2 * k == M) v[u].y = T(0);  // DC and (even M) Nyquist bins of a real row are real
+                const int pr = i / (2 * H);
+                stg[i + pr * (PH - 2 * H)] = v[u];
+            }
+        }
     }
     __syncthreads();
     {
         const int p = threadIdx.x / R2, t = threadIdx.x - p * R2;
+        const C *r0 = stg + p * PH;
         C v[R1];
 #pragma unroll
         for (int m = 0; m < R1; ++m) {
             const int k = t + R2 * m;
             C a, b;
-            if (k < H) { a = stg[(2 * p) * H + k]; b = stg[(2 * p + 1) * H + k]; }
-            else { a = cconj(stg[(2 * p) * H + (M - k)]); b = cconj(stg[(2 * p + 1) * H + (M - k)]); }
+            if (k < H) { a = r0[k]; b = r0[H + k]; }
+            else { a = cconj(r0[M - k]); b = cconj(r0[H + (M - k)]); }
             v[m] = cmake<C>(a.x - b.y, a.y + b.x);
         }
         dft_small<R1, +1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1)
-            A[p * RS + k1 * R2 + t] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(tw[t * k1])) : v[k1];
+            A[p * RS + t * R1 + k1] = (k1 > 0 && t > 0) ? cmul(v[k1], cconj(tw[t * k1])) : v[k1];
     }
     __syncthreads();
     for (int task = threadIdx.x; task < P * R1; task += blockDim.x) {
         const int p = task / R1, k1 = task - p * R1;
         C u[R2];
 #pragma unroll
-        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + k1 * R2 + t];
+        for (int t = 0; t < R2; ++t) u[t] = A[p * RS + t * R1 + k1];
         dft_small<R2, +1>(u);
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) Bf[p * RS + k1 + R1 * k2] = u[k2];
