@@ -314,6 +314,8 @@ template <typename C> __device__ __forceinline__ void load_twiddles(C *dst, cons
 // idle), and waits for the previous kernel's completion (and its memory) before
 // touching anything that kernel writes.  Without the launch attribute both are
 // no-ops.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ void chain_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void chain_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

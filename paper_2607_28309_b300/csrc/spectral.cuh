@@ -14,6 +14,8 @@
 // needed outputs are written.
 #pragma once
 
+#include <type_traits>
+#include <utility>
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -146,11 +148,39 @@ template <typename TI> struct SrcPlain {
 };
 
 // epilogue driver of the inverse plane kernels: g(i) is element i of the
-// plane's result; packs of W elements go to pe.pack when n allows it
+// plane's result; packs of W elements go to pe.pack when n allows it.  An
+// epilogue whose plane view has prefetch(i) (the vectors its pack(i) reads)
+// gets the L2 prefetches of four packs per thread before the first of them
+// runs: its loads cannot move above the previous pack's stores.
+template <class PE, class = void> struct HasPrefetch : std::false_type {};
+template <class PE>
+struct HasPrefetch<PE, std::void_t<decltype(std::declval<const PE &>().prefetch(0))>> : std::true_type {};
+
 template <typename T, class PE, class G>
 __device__ __forceinline__ void run_epilogue(PE &pe, int n, G g) {
     constexpr int W = 16 / sizeof(T);
-    if (n % W == 0) {
+    if (n % W == 0 && HasPrefetch<PE>::value) {
+        constexpr int U = 4;
+        for (int j0 = threadIdx.x; j0 < n / W; j0 += U * blockDim.x) {
+            if constexpr (HasPrefetch<PE>::value) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u * blockDim.x;
+                    if (j < n / W) pe.prefetch(j * W);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < n / W) {
+                    T v[W];
+#pragma unroll
+                    for (int k = 0; k < W; ++k) v[k] = g(j * W + k);
+                    pe.template pack<W>(j * W, v);
+                }
+            }
+        }
+    } else if (n % W == 0) {
         for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
             T v[W];
 #pragma unroll
@@ -785,7 +815,6 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
 // blocks as the registers allow stream from HBM.  The inverse z FFT follows.
 // ---------------------------------------------------------------------------
 constexpr int kHistPrefetch = 2;  // lags ahead
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Mode 0: plain loads with L2 prefetch; 1: evict-first loads (ld.global.cs)
 // with prefetch; 2: evict-first loads, no prefetch (a branch beside other work)
 template <int Mode, typename V> __device__ __forceinline__ V hist_ld(const V *p) {
@@ -1194,15 +1223,29 @@ __global__ void __launch_bounds__(P * R2) k_x_inverse_r(const cplx<T> *__restric
     const FastDiv fNx = make_fastdiv((unsigned)Nx);
     constexpr int W = 16 / sizeof(T);
     if (Nx % W == 0) {
-        for (int j = threadIdx.x; j < n / W; j += blockDim.x) {
-            T v[W];
+        constexpr int U = 4;  // L2 prefetches of four packs' inputs before the first pack runs
+        for (int j0 = threadIdx.x; j0 < n / W; j0 += U * blockDim.x) {
+            if constexpr (HasPrefetch<decltype(pe)>::value) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const int il = j * W + k, rr = (int)fdiv((unsigned)il, fNx), e = il - rr * Nx;
-                const C z = Bf[(rr >> 1) * RS + e];
-                v[k] = (rr & 1) ? z.y : z.x;
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u * blockDim.x;
+                    if (j < n / W) pe.prefetch(y0 * Nx + j * W);
+                }
             }
-            pe.template pack<W>(y0 * Nx + j * W, v);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < n / W) {
+                    T v[W];
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        const int il = j * W + k, rr = (int)fdiv((unsigned)il, fNx), e = il - rr * Nx;
+                        const C z = Bf[(rr >> 1) * RS + e];
+                        v[k] = (rr & 1) ? z.y : z.x;
+                    }
+                    pe.template pack<W>(y0 * Nx + j * W, v);
+                }
+            }
         }
     } else {
         for (int il = threadIdx.x; il < n; il += blockDim.x) {
@@ -1299,6 +1342,10 @@ struct EpiZ0 {
             TY ep = eps[i];
             y[i] = ep * TY(0.5) * (TY)x[i] - (ep - TY(1)) * g;
         }
+        __device__ __forceinline__ void prefetch(int i) const {
+            prefetch_l2(eps + i);
+            prefetch_l2(x + i);
+        }
         template <int W> __device__ __forceinline__ void pack(int i, const TY (&g)[W]) const {
             TY e[W], r[W];
             TX xv[W];
@@ -1339,6 +1386,11 @@ struct EpiResidual {
         __device__ __forceinline__ void operator()(int i, double g) const {
             double ep = eps[i];
             r[i] = b[i] - (ep * 0.5 * x[i] - (ep - 1.0) * g);
+        }
+        __device__ __forceinline__ void prefetch(int i) const {
+            prefetch_l2(eps + i);
+            prefetch_l2(x + i);
+            prefetch_l2(b + i);
         }
         template <int W, typename G> __device__ __forceinline__ void pack(int i, const G (&g)[W]) const {
             double e[W], xv[W], bv[W], rv[W];
