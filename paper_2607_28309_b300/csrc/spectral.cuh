@@ -1063,6 +1063,13 @@ template <int R1, int R2> __host__ __device__ constexpr int x_rsb() {
 template <typename T, int R1, int R2, int P> __host__ __device__ constexpr size_t x_r_smem() {
     return (size_t)(R1 * R2 + P * x_rs<R1, R2>() + P * x_rsb<R1, R2>()) * sizeof(cplx<T>);
 }
+// the compiled row-pass shape (270 = 15 x 18): A rows hold the transform, their
+// pitch is R1 mod 16, Bf holds both the padded staged row pairs and stage B's
+// output; the staged spectra continue the bank sequence (pitch = R2 mod 16)
+static_assert(x_rs<15, 18>() >= 270 && x_rs<15, 18>() % 16 == 15 % 16, "row-pass A pitch");
+static_assert(x_rsb<15, 18>() >= x_rs<15, 18>() && x_rsb<15, 18>() >= 2 * 136 &&
+                  (2 * 136 + ((18 - 2 * 136) % 16 + 16) % 16) % 16 == 18 % 16,
+              "row-pass staging pitch");
 
 // forward x pass: a block takes 2P consecutive rows of one (b, q, z) plane
 // (2P divides Ny), stages them with 16-byte loads, transforms the P row pairs
