@@ -1,0 +1,59 @@
+"""Host-side arithmetic of the measurement: the algorithmic bytes the roofline
+divides by, pinned to figures derived by hand from the array sizes (no GPU).
+
+cube64_a8: 64^3 voxels, alpha 8, one plane wave.  The present-time grid is
+M0 = 72^3 (half spectrum H0 = 37), the history grid Mh = 128^3 (Hh = 65), 26
+history lags.  cube64_b16: the same cube with 16 plane waves.
+"""
+import types
+
+import bench
+from paper_2607_28309_b300 import mvp_bench
+
+INFO = types.SimpleNamespace(M0=(72, 72, 72), Mh=(128, 128, 128))
+N = (64, 64, 64)
+
+
+def test_z_pass_and_history_bytes_cube64_a8():
+    kb = bench.kernel_bytes(INFO, N, 1, 1, [26])
+    planes = 3 * 64 * 72 * 37 * 8          # (component, z, ky, kx) complex FP32
+    lam0 = 6 * 37 * 37 * 37 * 4            # Lambda0 octant, six components, FP32
+    assert kb["z_green"] == 2 * planes + lam0 == 9_399_480
+    slot = 3 * 128 * 128 * 65 * 8          # one history-ring slot
+    lam_h = 6 * 65 ** 3 * 4                # one Lambda_k octant
+    out = 3 * 64 * 128 * 65 * 8            # the Nz kept planes of the inverse z pass
+    assert kb["z_history"] == 26 * (slot + lam_h) + out == 848_680_560
+
+
+def test_fused_solver_pass_bytes_cube64_a8():
+    kb = bench.kernel_bytes(INFO, N, 1, 1, [26])
+    vec = 3 * 64 ** 3 * 4                  # one FP32 solver vector
+    planes = 3 * 64 * 72 * 37 * 8
+    eps = 64 ** 3 * 4
+    assert kb["fwd_half"] == 10 * vec + planes == 35_549_184
+    assert kb["fwd_y1"] == 3 * vec + planes
+    assert kb["inv_half"] == planes + eps + 9 * vec == 33_452_032
+    assert kb["inv_v"] == planes + eps + 6 * vec == 24_014_848
+
+
+def test_fp64_doubles_the_real_element():
+    k32 = bench.kernel_bytes(INFO, N, 1, 1, [26])
+    k64 = bench.kernel_bytes(INFO, N, 1, 0, [26])
+    assert k64["z_green"] == 2 * k32["z_green"]
+    assert k64["z_history"] == 2 * k32["z_history"]
+
+
+def test_product_pass_bytes_cube64_b16():
+    vec = 16 * 3 * 64 ** 3 * 4
+    planes = 16 * 3 * 64 * 72 * 37 * 8
+    lam = 6 * 37 ** 3 * 4
+    eps = 64 ** 3 * 4
+    assert mvp_bench.info_plane_fits(INFO, N, 4)
+    expect = (vec + planes) + (2 * planes + lam) + (planes + eps + 2 * vec)
+    assert mvp_bench.pass_bytes(INFO, N, 16, 4) == expect == 415_141_048
+
+
+def test_profiled_traffic_is_a_number_or_none():
+    assert bench.profiled_traffic("no_such_kernel_class") is None
+    t = bench.profiled_traffic("z_green")
+    assert t is None or t > 0
