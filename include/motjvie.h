@@ -161,24 +161,27 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
 #define MOT_STATIC_SCRATCH_BYTES (64ull << 20)
 
 /* y = Z0 x exactly as mot_apply_Z0 computes it, for callers that must not
- * allocate device memory when they call in: code that runs while a CUDA
- * stream capture is open (allocation is not a capturable stream operation),
- * callers that run under a pool or budget that forbids new allocations, and
- * real-time loops where a cudaMalloc stall is not acceptable.  This call
+ * allocate device memory when they call in: callers that run under a memory
+ * pool or budget that forbids new allocations, and real-time loops where a
+ * cudaMalloc stall (it synchronises the device) is not acceptable.  This call
  * allocates nothing: its scratch is one file-scope __device__ array of
  * MOT_STATIC_SCRATCH_BYTES bytes that every GPU which loads the library holds
  * until the process exits.  (No counterpart in the paper: an ABI addition.)
  * - The first call on a device resolves the array's device address with
- *   cudaGetSymbolAddress (with that device current); make that first call
- *   before any stream capture.
+ *   cudaGetSymbolAddress (with that device current) and keeps it for the
+ *   process; make that first call before any stream capture.  cudaDeviceReset
+ *   invalidates the kept address: do not call this entry point after one.
  * - All calls share the one array, which keeps the previous call's contents:
  *   every scratch element is written before it is read, so nothing needs to
  *   start at zero.  Calls whose kernels overlap on the GPU (other streams or
  *   threads) race on the array; order them on one stream.
- * - x_dev, y_dev, nrhs, dtype as mot_apply_Z0.  The scratch needed is
- *   nrhs * 3 * Nz * (Ny + M0y) * (M0x/2 + 1) complex elements of dtype; a
- *   request above MOT_STATIC_SCRATCH_BYTES fails with MOT_EINVAL (message
- *   gives both sizes) before any device work.
+ * - x_dev, y_dev, nrhs, dtype as mot_apply_Z0.  With c = the byte size of one
+ *   complex element of dtype and H0 = M0x/2 + 1, the scratch needed is
+ *   round_up(nrhs * 3 * Nz * Ny * H0 * c, 256) + nrhs * 3 * Nz * M0y * H0 * c
+ *   bytes; a request above MOT_STATIC_SCRATCH_BYTES fails with MOT_EINVAL
+ *   (message gives both sizes) before any device work.
+ * - No kernel-timing events are recorded by this call (mot_run_kernel_times
+ *   is unaffected by it).
  * Errors: MOT_EINVAL, MOT_ECUDA.                                              */
 mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
 
@@ -239,6 +242,16 @@ mot_status mot_run_current_device(mot_run *r, const void **J_dev);
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation for launch accounting; no counterpart in the paper).        */
 mot_status mot_kernel_launches(uint64_t *count);
+
+/* Measured FMA throughput of device `device` for dtype MOT_F64 or MOT_F32:
+ * one microkernel of independent FMA chains (8 per thread, a whole multiple of
+ * the SM count of 256-thread blocks), calibrated to about 100 ms per launch;
+ * *flop_per_s = 2 * FMAs / time of the fastest of three launches (CUDA
+ * events), *ms (nullable) that time.  The denominator of the FP64 product's
+ * roofline (instrumentation; no counterpart in the paper).  Leaves no device
+ * state behind; GPU clocks are read by the caller, never set.
+ * Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA.                                   */
+mot_status mot_fma_peak(int device, int dtype, double *flop_per_s, double *ms);
 
 /* Index of the next step to be computed.                                       */
 mot_status mot_run_step_index(const mot_run *r, int64_t *n);

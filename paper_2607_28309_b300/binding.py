@@ -38,7 +38,7 @@ __all__ = [
     "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "EXPORTED", "mot_kernel_launches", "default_options",
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
     "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED", "mot_request", "mot_result",
-    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy",
+    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
 ]
 
 # every symbol include/motjvie.h declares
@@ -47,7 +47,7 @@ EXPORTED = [
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times", "mot_run_save", "mot_run_load",
-    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy",
+    "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
 ]
 
 # mot_kernel_class values, in order
@@ -134,6 +134,7 @@ def lib():
         L.mot_server_destroy.argtypes = [P]
         L.mot_server_destroy.restype = None
         L.mot_run_load.argtypes = [P, ctypes.c_char_p, PP]
+        L.mot_fma_peak.argtypes = [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.mot_run_destroy.argtypes = [P]
         L.mot_run_destroy.restype = None
         for name in EXPORTED:
@@ -340,6 +341,13 @@ def mot_kernel_launches() -> int:
     c = ctypes.c_uint64()
     _check(lib().mot_kernel_launches(ctypes.byref(c)))
     return c.value
+
+
+def mot_fma_peak(device: int = 0, dtype: int = MOT_F64):
+    """(FLOP/s, ms) of the library's FMA microkernel on `device`."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mot_fma_peak(int(device), int(dtype), ctypes.byref(f), ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def default_options(**kw) -> mot_options:

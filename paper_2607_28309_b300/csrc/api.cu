@@ -19,6 +19,7 @@
 #include "krylov.cuh"
 #include "spectral.cuh"
 #include "tables.cuh"
+#include "peak.cuh"
 
 #include <atomic>
 #include <mutex>
@@ -2554,6 +2555,67 @@ mot_status mot_kernel_launches(uint64_t *count) {
     return MOT_OK;
 }
 
+mot_status mot_fma_peak(int device, int dtype, double *flop_per_s, double *ms) {
+    if (!flop_per_s) MOT_FAIL(MOT_EINVAL, "flop_per_s is NULL");
+    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    int ndev = 0;
+    MOT_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) MOT_FAIL(MOT_EINVAL, "device index out of range");
+    MOT_CUDA_TRY(cudaSetDevice(device));
+    int sms = 0;
+    MOT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int threads = 256, blocks = sms * 8;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DBuf out;
+    mot_status rc = MOT_OK;
+    auto launch = [&](int iters) -> float {
+        float t = -1.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return t;
+        count_launch();
+        if (dtype == MOT_F64)
+            k_fma_peak<double><<<blocks, threads, 0, st>>>((double *)out.p, iters, 0.999999, 1e-6);
+        else
+            k_fma_peak<float><<<blocks, threads, 0, st>>>((float *)out.p, iters, 0.999f, 1e-3f);
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return -1.f;
+        return t;
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = MOT_ECUDA;
+        set_error("stream or event creation failed");
+    } else if ((rc = dalloc(out, sizeof(double) * (size_t)blocks * threads)) == MOT_OK) {
+        // calibrate to about 100 ms per launch, then keep the best of three
+        int iters = 64;
+        float t = launch(iters);
+        while (t >= 0.f && t < 20.f && iters < (1 << 24)) {
+            iters *= 4;
+            t = launch(iters);
+        }
+        if (t > 0.f) iters = (int)std::min<double>((double)(1 << 28), iters * (100.0 / t));
+        float best = 1e30f;
+        for (int rep = 0; rep < 3 && t >= 0.f; ++rep) {
+            t = launch(iters);
+            if (t > 0.f) best = std::min(best, t);
+        }
+        if (t < 0.f) {
+            rc = MOT_ECUDA;
+            set_error("FMA microkernel launch failed");
+        } else {
+            const double fmas = (double)blocks * threads * iters * 4.0 * kPeakChains;
+            *flop_per_s = 2.0 * fmas / (best * 1e-3);
+            if (ms) *ms = best;
+        }
+    }
+    dfree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
 mot_status mot_run_step_index(const mot_run *r, int64_t *n) {
     if (!r || !n) MOT_FAIL(MOT_EINVAL, "NULL argument");
     *n = r->n;
@@ -2618,7 +2680,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[MOT_STATIC_SCRAT
 
 namespace {
 constexpr int kMaxDevices = 64;
-void *g_static_ptr[kMaxDevices] = {nullptr};
+// device address of g_static_scratch per device ordinal, resolved on the first
+// call on that device; atomic so that threads racing on a first call agree
+std::atomic<void *> g_static_ptr[kMaxDevices];
 }  // namespace
 
 extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
@@ -2637,19 +2701,27 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
         MOT_FAIL(MOT_EINVAL, "mot_apply_Z0_static needs " + std::to_string(a + b) + " bytes of scratch; the static array holds " +
                                  std::to_string((size_t)MOT_STATIC_SCRATCH_BYTES));
     MOT_CUDA_TRY(cudaSetDevice(dev));
-    if (!g_static_ptr[dev]) {
-        void *ptr = nullptr;
+    void *ptr = g_static_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         MOT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_static_scratch));
-        g_static_ptr[dev] = ptr;
+        g_static_ptr[dev].store(ptr, std::memory_order_release);
     }
-    char *ws = (char *)g_static_ptr[dev];
+    char *ws = (char *)ptr;
     const long pr = (long)p->N[2] * p->N[1];
+    // this entry point records no kernel-timing events (the caller's stream may
+    // be in a state where the library's own events must not be recorded)
+    const bool was = p->capturing;
+    p->capturing = true;
+    mot_status st;
     if (dtype == MOT_F64) {
         EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
-        return z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+        st = z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+    } else {
+        EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
+        st = z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
     }
-    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
-    return z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+    p->capturing = was;
+    return st;
 }
 
 // ---------------------------------------------------------------- serving

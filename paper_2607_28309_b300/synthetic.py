@@ -13,7 +13,15 @@ Recipe
   t0 = 5 sigma, sigma_f = 1/(2 pi sigma), f0 = 2.5 sigma_f, f_max = f0 + 3 sigma_f;
 - nanopillars: cylinders of 24-voxel diameter (voxel centre within 12 voxels of
   the axis) at 32-voxel pitch, axes at 16 + 32 i, occupying z in [8, 72): the
-  lower 43 layers eps_r = 3.5, the upper 21 eps_r = 6.0, background 1.
+  lower 43 layers eps_r = 3.5, the upper 21 eps_r = 6.0, background 1;
+- the paper's bilayer metasurface (Sec. V-B): 240 x 240 x 90 voxels of 10 nm, a
+  20-voxel quartz substrate (eps_r 2.1) at the bottom, 8 x 8 pillars of a 40-voxel
+  a-Si base (12.0) under a 20-voxel GST cap, 10 voxels of air on top; pillars are
+  16 x 10-voxel rectangles rotated by 0, 45, 90, 135 degrees in each 2 x 2
+  supercell of 56-voxel period, centred 14 voxels off the supercell centre; caps of
+  the 0 / 90 degree pillars amorphous GST (16.0), of the 45 / 135 degree pillars
+  crystalline GST (25.0); x-polarised pulse along -z with sigma 11.06 fs,
+  t0 68.85 fs, f0 312 THz, dt = 16 dt_CFL.
 """
 from __future__ import annotations
 
@@ -73,6 +81,44 @@ def pillar_eps(nx: int, ny: int, Nz: int = 80, pitch: int = 32, diameter: int = 
     return eps
 
 
+def metasurface_eps(n_super: int = 4, period: int = 56, margin: int = 8, offset: int = 14, long_edge: int = 16,
+                    short_edge: int = 10, z_sub: int = 20, z_base: int = 40, z_cap: int = 20, z_air: int = 10,
+                    eps_quartz: float = 2.10, eps_asi: float = 12.0, eps_gst_a: float = 16.0,
+                    eps_gst_c: float = 25.0) -> np.ndarray:
+    """The bilayer GST/a-Si nanopillar metasurface of Sec. V-B on a voxel grid
+    (array [Nz][Ny][Nx]).  In each 2 x 2 supercell the pillar at (-, -) is rotated
+    by 0 degrees, (+, -) by 45, (-, +) by 90 and (+, +) by 135 (x fastest); a voxel
+    belongs to a pillar when its centre lies in the rotated rectangle."""
+    N = 2 * margin + n_super * period
+    Nz = z_sub + z_base + z_cap + z_air
+    eps = np.ones((Nz, N, N))
+    eps[:z_sub] = eps_quartz
+    yy, xx = np.meshgrid(np.arange(N) + 0.5, np.arange(N) + 0.5, indexing="ij")
+    base = np.zeros((N, N), dtype=bool)
+    cap = np.ones((N, N))
+    angles = ((0, 45), (90, 135))  # [row (y)][column (x)]
+    for sj in range(n_super):
+        for si in range(n_super):
+            cx0 = margin + si * period + period / 2.0
+            cy0 = margin + sj * period + period / 2.0
+            for j in range(2):
+                for i in range(2):
+                    th = math.radians(angles[j][i])
+                    cx = cx0 + (2 * i - 1) * offset
+                    cy = cy0 + (2 * j - 1) * offset
+                    dx, dy = xx - cx, yy - cy
+                    u = dx * math.cos(th) + dy * math.sin(th)
+                    v = -dx * math.sin(th) + dy * math.cos(th)
+                    inside = (np.abs(u) <= long_edge / 2.0) & (np.abs(v) <= short_edge / 2.0)
+                    base |= inside
+                    cap[inside] = eps_gst_a if angles[j][i] in (0, 90) else eps_gst_c
+    for z in range(z_sub, z_sub + z_base):
+        eps[z][base] = eps_asi
+    for z in range(z_sub + z_base, z_sub + z_base + z_cap):
+        eps[z][base] = cap[base]
+    return eps
+
+
 def dt_cfl(h: float = H_DEFAULT) -> float:
     return h / (C0 * math.sqrt(3.0))
 
@@ -124,6 +170,16 @@ def pillars8x8():
             "exc": [pulse(200, 8.0, khat=(0.0, 0.0, -1.0))]}
 
 
+def metasurface8x8(nsteps: int = 1250):
+    """The paper's 8 x 8 bilayer metasurface (Sec. V-B): 240 x 240 x 90 voxels,
+    dt = 16 dt_CFL, its own pulse (sigma 11.06 fs, t0 68.85 fs, f0 312 THz, -z, x-pol);
+    1250 steps span the paper's 385.17 fs window."""
+    pw = {"E0": 1.0, "sigma": 11.06e-15, "t0": 68.85e-15, "f0": 312e12, "khat": (0.0, 0.0, -1.0),
+          "pol": (1.0, 0.0, 0.0)}
+    return {"name": "metasurface8x8_a16", "N": (240, 240, 90), "h": H_DEFAULT, "eps": metasurface_eps(),
+            "alpha": 16.0, "steps": int(nsteps), "exc": [pw]}
+
+
 def cube64_batch16(seed: int = 4):
     """64^3 cube, eps_r U[2,4] per 4^3 block, 16 oblique plane waves, alpha 8, 200 steps."""
     N = (64, 64, 64)
@@ -138,6 +194,7 @@ WORKLOADS = {
     "cube64_a16": lambda: cube64(16.0),
     "cube64_b16": lambda: cube64_batch16(),
     "pillars8x8": lambda: pillars8x8(),
+    "metasurface8x8": lambda: metasurface8x8(),
 }
 
 

@@ -1,10 +1,12 @@
 """mot_apply_Z0_static: the Z0 product for callers that cannot allocate device
-memory when they call in (open stream captures, allocation-free pools,
-real-time loops).  Its scratch is the library's file-scope device array, so the
-call allocates nothing; this checks it against mot_apply_Z0, which uses
-allocated scratch, on two calls in a row (the array keeps the previous call's
-contents), with the parity tolerances used elsewhere (FP64 1e-10, FP32 1e-5
-relative L2), and that an oversized request is refused before any GPU work.
+memory when they call in (allocation-free pools or budgets, real-time loops
+that cannot take cudaMalloc's device synchronisation).  Its scratch is the
+library's file-scope device array, so the call allocates nothing; this checks
+it against mot_apply_Z0, which uses allocated scratch, on two calls in a row
+(the array keeps the previous call's contents), with the parity tolerances used
+elsewhere (FP64 1e-10, FP32 1e-5 relative L2); that the device's free memory
+is the same before and after a call; and that the largest request the array
+holds is accepted while one more right-hand side is refused before any GPU work.
 
 This file is named to be collected last, so that a run stopping at the first
 failure has already run every other test.
@@ -45,8 +47,11 @@ def test_static_scratch_product_matches_allocating_product():
                     mot.mot_apply_Z0(prob, x, ref, nrhs, dtype)
                     for _ in range(2):  # two calls in a row share the static scratch
                         y = torch.full_like(x, float("nan"))
+                        torch.cuda.synchronize()
+                        free0 = torch.cuda.mem_get_info()[0]
                         mot.mot_apply_Z0_static(prob, x, y, nrhs, dtype)
                         torch.cuda.synchronize()
+                        assert torch.cuda.mem_get_info()[0] == free0
                         assert torch.isfinite(y).all()
                         assert _rel(y, ref) <= tol
             # pointers off the 16-byte grid are refused before any device work
@@ -56,12 +61,25 @@ def test_static_scratch_product_matches_allocating_product():
                 with pytest.raises(mot.MotError) as e:
                     f(prob, x[1:].data_ptr(), y[1:].data_ptr(), 1, mot.MOT_F32)
                 assert e.value.status == mot.MOT_EINVAL
-            # a request beyond the static array is refused with MOT_EINVAL
-            big = 1 + mot.MOT_STATIC_SCRATCH_BYTES // (3 * N[2] * N[1] * 16 * 16)
-            x = torch.zeros(big, 3, nv, device="cuda", dtype=torch.float64)
+            # the largest request the array holds (the bound stated in the header) is
+            # accepted; one more right-hand side is refused with MOT_EINVAL
+            info = mot.mot_problem_info_get(prob)
+            H0, c = info.M0[0] // 2 + 1, 16
+
+            def need(b):
+                rows = b * 3 * N[2] * N[1] * H0 * c
+                return (rows + 255) // 256 * 256 + b * 3 * N[2] * info.M0[1] * H0 * c
+
+            big = 1
+            while need(big + 1) <= mot.MOT_STATIC_SCRATCH_BYTES:
+                big += 1
+            x = torch.zeros(big + 1, 3, nv, device="cuda", dtype=torch.float64)
             y = torch.zeros_like(x)
+            mot.mot_apply_Z0_static(prob, x[:big], y[:big], big, mot.MOT_F64)
+            torch.cuda.synchronize()
+            assert float(y[:big].abs().max()) == 0.0
             with pytest.raises(mot.MotError) as e:
-                mot.mot_apply_Z0_static(prob, x, y, big, mot.MOT_F64)
+                mot.mot_apply_Z0_static(prob, x, y, big + 1, mot.MOT_F64)
             assert e.value.status == mot.MOT_EINVAL
         finally:
             mot.mot_problem_destroy(prob)
