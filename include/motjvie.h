@@ -98,6 +98,14 @@ typedef struct {
                          from the host and the TFQMR loop tested on the host
                          after each iteration (slowest; for per-kernel
                          profilers and the timing option over every product)  */
+    int autotune;     /* 1 (default): the launch schedule of the Z0 product (columns
+                         per z-pass block, rows per row-pass block, plane-pass
+                         block sizes, generic-pass widths, programmatic dependent
+                         launch) is picked by timing candidates on first use for
+                         each (number of right-hand sides, precision); every
+                         candidate's product is checked against the built-in
+                         schedule's.  Results are cached per process.  0: the
+                         built-in rules.  Not in the paper (a B300 tuning aid)     */
 } mot_options;
 
 typedef struct {
@@ -146,6 +154,30 @@ void mot_ctx_destroy(mot_ctx *ctx);
 mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const double *eps_r,
                               double alpha, const mot_options *opt, mot_problem **out);
 mot_status mot_problem_info_get(const mot_problem *p, mot_problem_info *info);
+
+/* The launch schedule the autotuner picked for the Z0 product of `nrhs`
+ * right-hand sides in dtype (MOT_F64 / MOT_F32): 0 in a choice field means the
+ * built-in rule.  Tuning happens in mot_run_create (the run's batch and
+ * precision) and in the first mot_apply_Z0 of each (nrhs, dtype), when the
+ * problem's autotune option is on.  Errors: MOT_EINVAL (nothing tuned for that
+ * pair).                                                                       */
+typedef struct {
+    int32_t z_cols;      /* z-pass columns per block (4, 8, 16, 32)            */
+    int32_t x_rows;      /* rows per block of the compiled row passes           */
+    int32_t xy_fwd;      /* plane-pass threads per block, forward / inverse     */
+    int32_t xy_inv;
+    int32_t pdl;         /* programmatic dependent launch on (1) / off (0)      */
+    int32_t gen_pairs;   /* generic row passes: row pairs per block             */
+    int32_t gen_tile;    /* generic column passes: columns per block            */
+    int32_t candidates;  /* candidates timed                                    */
+    int32_t rejected;    /* candidates whose product differed (discarded)       */
+    int32_t cached;      /* 1: taken from this process's cache, not re-timed    */
+    float ms_default;    /* product time with the built-in rules [ms]           */
+    float ms_tuned;      /* product time with the chosen schedule [ms]          */
+    double max_rel_diff; /* largest relative L2 difference of a candidate's
+                            product from the built-in schedule's                */
+} mot_schedule;
+mot_status mot_problem_schedule(const mot_problem *p, int nrhs, int dtype, mot_schedule *out);
 void mot_problem_destroy(mot_problem *p);
 
 /* y = Z0 x for nrhs current vectors (Eq. 12: Z0 x = D x - X (G x), with

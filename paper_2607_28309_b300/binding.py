@@ -39,6 +39,7 @@ __all__ = [
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
     "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED", "mot_request", "mot_result",
     "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
+    "mot_schedule", "mot_problem_schedule",
 ]
 
 # every symbol include/motjvie.h declares
@@ -48,6 +49,7 @@ EXPORTED = [
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times", "mot_run_save", "mot_run_load",
     "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
+    "mot_problem_schedule",
 ]
 
 # mot_kernel_class values, in order
@@ -69,7 +71,15 @@ class mot_planewave(ctypes.Structure):
 class mot_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("delta", ctypes.c_double), ("timing", ctypes.c_int),
-                ("guess", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("guess", ctypes.c_int), ("graph", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class mot_schedule(ctypes.Structure):
+    _fields_ = [("z_cols", ctypes.c_int32), ("x_rows", ctypes.c_int32), ("xy_fwd", ctypes.c_int32),
+                ("xy_inv", ctypes.c_int32), ("pdl", ctypes.c_int32), ("gen_pairs", ctypes.c_int32),
+                ("gen_tile", ctypes.c_int32), ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("cached", ctypes.c_int32), ("ms_default", ctypes.c_float), ("ms_tuned", ctypes.c_float),
+                ("max_rel_diff", ctypes.c_double)]
 
 
 class mot_problem_info(ctypes.Structure):
@@ -135,6 +145,7 @@ def lib():
         L.mot_server_destroy.restype = None
         L.mot_run_load.argtypes = [P, ctypes.c_char_p, PP]
         L.mot_fma_peak.argtypes = [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.mot_problem_schedule.argtypes = [P, I, I, ctypes.POINTER(mot_schedule)]
         L.mot_run_destroy.argtypes = [P]
         L.mot_run_destroy.restype = None
         for name in EXPORTED:
@@ -192,6 +203,13 @@ def mot_problem_info_get(prob) -> mot_problem_info:
     info = mot_problem_info()
     _check(lib().mot_problem_info_get(prob, ctypes.byref(info)))
     return info
+
+
+def mot_problem_schedule(prob, nrhs: int, dtype: int) -> dict:
+    """The autotuned launch schedule of the Z0 product for (nrhs, dtype), as a dict."""
+    sc = mot_schedule()
+    _check(lib().mot_problem_schedule(prob, int(nrhs), int(dtype), ctypes.byref(sc)))
+    return {f: getattr(sc, f) for f, _ in mot_schedule._fields_}
 
 
 def mot_problem_destroy(prob):
@@ -352,7 +370,7 @@ def mot_fma_peak(device: int = 0, dtype: int = MOT_F64):
 
 def default_options(**kw) -> mot_options:
     """mot_options with the library defaults (tol 0 = per-precision default)."""
-    o = mot_options(0.0, 500, 1e-6, 6, 0.0, 0, 0, 1)
+    o = mot_options(0.0, 500, 1e-6, 6, 0.0, 0, 0, 1, 1)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

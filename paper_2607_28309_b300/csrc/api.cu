@@ -116,11 +116,16 @@ void gauss_legendre(int n, double *x, double *w) {
     }
 }
 
-constexpr int kGLN = 20;
+constexpr int kGLN = 20;  // radial panels
+constexpr int kGL8 = 8;   // z-line pieces far from the origin
 
+// the kGLN-point rule followed by the kGL8-point rule
 struct HostRule {
-    double x[kGLN], w[kGLN];
-    HostRule() { gauss_legendre(kGLN, x, w); }
+    double x[kGLN + kGL8], w[kGLN + kGL8];
+    HostRule() {
+        gauss_legendre(kGLN, x, w);
+        gauss_legendre(kGL8, x + kGLN, w + kGLN);
+    }
 };
 const HostRule &host_rule() {
     static HostRule r;
@@ -129,14 +134,20 @@ const HostRule &host_rule() {
 
 // ---------------------------------------------------------------- table items
 // sorted offsets (a <= b <= c) that fit the sorted extents S and the lags in
-// [k0, k1] whose causal support contains them, enumerated offset-major.
+// [k0, k1] whose causal support contains them, enumerated offset-major; the
+// sorted offsets' box-integral records and the distinct plane integrals their
+// diagonal entries need (knot-interval moments, see galerkin.cuh).
 struct ItemSet {
     std::vector<TableItem> items;
     std::vector<int> base, klo, cnt;  // per dense triple index (Rm+1)^3
     int Rm = 0;
+    std::vector<TripleRec> tri;
+    std::vector<FaceRec> faces;
+    long fm_len = 0, bm_len = 0;  // doubles of face / box moments
 };
 
-void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
+// false: a support meets more knot intervals than one record holds (rho < 0.25)
+bool build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
     int Rm = S[2];
     is.Rm = Rm;
     long n3 = (long)(Rm + 1) * (Rm + 1) * (Rm + 1);
@@ -144,6 +155,32 @@ void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
     is.klo.assign(n3, 0);
     is.cnt.assign(n3, 0);
     is.items.clear();
+    is.tri.clear();
+    is.faces.clear();
+    is.fm_len = is.bm_len = 0;
+    const int jg0 = std::max(0, k0 - 2), jg1 = k1;
+    // distinct faces (c, a <= b), c in [0, Rm + 1], a, b in [0, Rm]
+    const long fkeys = (long)(Rm + 2) * (Rm + 1) * (Rm + 1);
+    std::vector<int> fid(fkeys, -1);
+    auto face_of = [&](int c, int a, int b) -> int {
+        c = std::abs(c);
+        a = std::abs(a);
+        b = std::abs(b);
+        if (a > b) std::swap(a, b);
+        const long key = ((long)c * (Rm + 1) + a) * (Rm + 1) + b;
+        int &id = fid[key];
+        if (id >= 0) return id;
+        FaceRec f = {c, a, b, 0, 0, is.fm_len};
+        const double lo2 = std::pow(std::max(a - 1.0, 0.0), 2) + std::pow(std::max(b - 1.0, 0.0), 2);
+        const double hi2 = std::pow(a + 1.0, 2) + std::pow(b + 1.0, 2);
+        if (gk::interval_range(rho, sqrt((double)c * c + lo2), sqrt((double)c * c + hi2), jg0, jg1, &f.jlo, &f.nj))
+            is.fm_len += 3L * f.nj;
+        else
+            f.nj = 0;
+        id = (int)is.faces.size();
+        is.faces.push_back(f);
+        return id;
+    };
     for (int a = 0; a <= S[0]; ++a)
         for (int b = a; b <= S[1]; ++b)
             for (int c = b; c <= S[2]; ++c) {
@@ -165,9 +202,25 @@ void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
                     if (first < 0) {
                         first = (int)is.items.size();
                         kfirst = k;
+                        TripleRec t;
+                        t.x = a;
+                        t.y = b;
+                        t.z = c;
+                        t.off = is.bm_len;
+                        if (gk::interval_range(rho, lo, hi, jg0, jg1, &t.jlo, &t.nj)) {
+                            if (t.nj > gk::kMaxIntervals) return false;
+                            is.bm_len += 9L * t.nj;
+                        } else {
+                            t.jlo = 0;
+                            t.nj = 0;
+                        }
+                        for (int p = 0; p < 3; ++p)
+                            for (int e = -1; e <= 1; ++e)
+                                t.face[3 * p + e + 1] = face_of(d[p] + e, d[(p + 1) % 3], d[(p + 2) % 3]);
+                        is.tri.push_back(t);
                     }
                     // lags of one offset form a contiguous range
-                    is.items.push_back({k, a, b, c});
+                    is.items.push_back({k, a, b, c, (int)is.tri.size() - 1});
                     ++count;
                 }
                 if (first >= 0) {
@@ -176,6 +229,9 @@ void build_items(double rho, const int S[3], int k0, int k1, ItemSet &is) {
                     is.cnt[key] = count;
                 }
             }
+    for (const FaceRec &f : is.faces)
+        if (f.nj > gk::kMaxIntervals) return false;
+    return true;
 }
 
 // process-wide cache of quadrature results: the lag tables depend only on
@@ -308,6 +364,35 @@ struct KTimer {
     }
 };
 
+// ---------------------------------------------------------------- launch schedules
+// Launch choices of the Z0 product that leave its arithmetic unchanged (every
+// output element goes through the same operations in the same order whatever
+// is picked): columns per z-pass block, rows per row-pass block, plane-pass
+// block sizes of the plain product, programmatic dependent launch, and the row
+// pairs / tile widths of the generic passes.  0 = the built-in rule.  The
+// autotuner (tune_product) picks them per (grid, right-hand sides, precision);
+// the product and the march launch under the schedule made current by a
+// SchedScope.  The MOTJVIE_* environment switches, where set, override it.
+struct Sched {
+    int z_cols = 0;     // z-pass columns per block: 4 | 8 | 16 | 32
+    int x_rows = 0;     // rows per block of the compiled row passes: 8 | 16 | 32
+    int xy_fwd = 0;     // plane-pass block size of the plain product: 256 | 384 | 512
+    int xy_inv = 0;
+    int pdl = 1;        // programmatic dependent launch of the chain kernels
+    int gen_pairs = 0;  // generic x passes: row pairs per block, 1..8
+    int gen_tile = 0;   // generic axis passes: columns per block, power of two
+};
+thread_local const Sched *t_sched = nullptr;
+inline const Sched &cur_sched() {
+    static const Sched d;
+    return t_sched ? *t_sched : d;
+}
+struct SchedScope {
+    const Sched *prev;
+    explicit SchedScope(const Sched *s) : prev(t_sched) { t_sched = s; }
+    ~SchedScope() { t_sched = prev; }
+};
+
 struct mot_problem {
     mot_ctx *ctx = nullptr;
     KTimer kt;
@@ -329,6 +414,18 @@ struct mot_problem {
     // Z0 product workspace
     DBuf wsA, wsB;
     mot_options opt;
+    // tuned launch schedules of the Z0 product, per (right-hand sides, FP32)
+    struct Tuned {
+        int nrhs, fp32;
+        Sched s;
+        mot_schedule info;
+    };
+    std::vector<Tuned> tuned;
+    const Sched *sched_for(int nrhs, bool fp32) const {
+        for (auto &t : tuned)
+            if (t.nrhs == nrhs && t.fp32 == (int)fp32) return &t.s;
+        return nullptr;
+    }
 };
 
 struct LoopGraph {
@@ -436,6 +533,8 @@ template <typename TI, typename T>
 mot_status launch_x_forward(const TI *x, cplx<T> *out, long nrows, int Nx, int H, AxisTw *tw, cudaStream_t st) {
     const int M = tw->M;
     int pairs = (int)std::min<long>(8, std::max<long>(1, ((long)(48 * 1024) / ((long)M * sizeof(cplx<T>)) - 1) / 2));
+    const int sp = cur_sched().gen_pairs;
+    if (sp >= 1 && sp <= 8 && (size_t)(2 * sp + 1) * M * sizeof(cplx<T>) <= kSmemMax) pairs = sp;
     size_t smem = (size_t)(2 * pairs + 1) * M * sizeof(cplx<T>);
     MOT_TRY(allow_smem<k_x_forward<TI, T>>());
     long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
@@ -457,6 +556,8 @@ mot_status launch_axis(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int L
                        const long long *nptr = nullptr, int ell = 1, long slot_stride = 0) {
     const int M = tw->M;
     int tx = tile_width<T>(M, 1);
+    const int st_ = cur_sched().gen_tile;
+    if (st_ >= 1 && st_ < tx && (st_ & (st_ - 1)) == 0) tx = st_;
     size_t smem = (size_t)(2 * M * tx + M) * sizeof(cplx<T>);
     MOT_TRY(allow_smem<k_axis<T, S>>());
     dim3 grid((H + tx - 1) / tx, (unsigned)(O1 * O2));
@@ -471,6 +572,8 @@ template <typename T, class Epi>
 mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw *tw, Epi epi, cudaStream_t st) {
     const int M = tw->M;
     int pairs = (int)std::min<long>(8, std::max<long>(1, (long)(64 * 1024) / ((long)(2 * H + 2 * M + M) * sizeof(cplx<T>))));
+    const int sp = cur_sched().gen_pairs;
+    if (sp >= 1 && sp <= 8 && (size_t)(2 * sp * H + 2 * sp * M + M) * sizeof(cplx<T>) <= kSmemMax) pairs = sp;
     size_t smem = (size_t)(2 * pairs * H + 2 * pairs * M + M) * sizeof(cplx<T>);
     MOT_TRY(allow_smem<k_x_inverse<T, Epi>>());
     long grid = (nrows + 2 * pairs - 1) / (2 * pairs);
@@ -485,8 +588,8 @@ mot_status launch_x_inverse(const cplx<T> *in, long nrows, int Nx, int H, AxisTw
 // previous kernel finishes (its last blocks and its reduction tail) and wait on
 // the device; MOTJVIE_PDL=0 turns it off (timing comparisons)
 inline bool chain_pdl_on() {
-    static const bool f = !(getenv("MOTJVIE_PDL") && atoi(getenv("MOTJVIE_PDL")) == 0);
-    return f;
+    static const bool off = getenv("MOTJVIE_PDL") && atoi(getenv("MOTJVIE_PDL")) == 0;
+    return !off && cur_sched().pdl != 0;
 }
 template <typename... KArgs, typename... Args>
 void launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
@@ -527,7 +630,10 @@ inline int sm_count() {
 inline int xy_threads(int planes, bool forward, bool plain32) {
     static const int f = getenv("MOTJVIE_XY_THREADS") ? atoi(getenv("MOTJVIE_XY_THREADS")) : 0;
     if (f == 256 || f == 384 || f == 512) return f;
-    if (!plain32 || planes < 4 * sm_count()) return 512;
+    if (!plain32) return 512;
+    const int s = forward ? cur_sched().xy_fwd : cur_sched().xy_inv;
+    if (s == 256 || s == 384 || s == 512) return s;
+    if (planes < 4 * sm_count()) return 512;
     return forward ? 256 : 384;
 }
 
@@ -622,16 +728,27 @@ bool col_r_go(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int L
     return true;
 }
 
-// rows per block 2P: the largest of 32, 16, 8 dividing Ny (blocks stay inside one plane)
+// rows per block 2P: the schedule's choice where it divides Ny, else the
+// largest of 32, 16, 8 dividing Ny (blocks stay inside one plane)
+inline int x_rows_for(int Ny) {
+    const int s = cur_sched().x_rows;
+    if ((s == 8 || s == 16 || s == 32) && Ny % s == 0) return s;
+    for (int r : {32, 16, 8})
+        if (Ny % r == 0) return r;
+    return 0;
+}
+
 template <typename TI, typename T>
 bool x_forward_r(const TI *x, cplx<T> *out, long nrows, int Nx, int Ny, AxisTw *tw, cudaStream_t st) {
     if (specialised_off()) return false;
     switch (tw->M) {
         case 270:
-            if (Ny % 32 == 0) return x_forward_r_go<TI, T, 15, 18, 16>(x, out, nrows, Nx, tw, st);
-            if (Ny % 16 == 0) return x_forward_r_go<TI, T, 15, 18, 8>(x, out, nrows, Nx, tw, st);
-            if (Ny % 8 == 0) return x_forward_r_go<TI, T, 15, 18, 4>(x, out, nrows, Nx, tw, st);
-            return false;
+            switch (x_rows_for(Ny)) {
+                case 32: return x_forward_r_go<TI, T, 15, 18, 16>(x, out, nrows, Nx, tw, st);
+                case 16: return x_forward_r_go<TI, T, 15, 18, 8>(x, out, nrows, Nx, tw, st);
+                case 8: return x_forward_r_go<TI, T, 15, 18, 4>(x, out, nrows, Nx, tw, st);
+                default: return false;
+            }
         default: return false;
     }
 }
@@ -641,10 +758,12 @@ bool x_inverse_r(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *
     if (specialised_off()) return false;
     switch (tw->M) {
         case 270:
-            if (Ny % 32 == 0) return x_inverse_r_go<T, Epi, 15, 18, 16>(in, nrows, Nx, Ny, Nz, tw, epi, st);
-            if (Ny % 16 == 0) return x_inverse_r_go<T, Epi, 15, 18, 8>(in, nrows, Nx, Ny, Nz, tw, epi, st);
-            if (Ny % 8 == 0) return x_inverse_r_go<T, Epi, 15, 18, 4>(in, nrows, Nx, Ny, Nz, tw, epi, st);
-            return false;
+            switch (x_rows_for(Ny)) {
+                case 32: return x_inverse_r_go<T, Epi, 15, 18, 16>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+                case 16: return x_inverse_r_go<T, Epi, 15, 18, 8>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+                case 8: return x_inverse_r_go<T, Epi, 15, 18, 4>(in, nrows, Nx, Ny, Nz, tw, epi, st);
+                default: return false;
+            }
         default: return false;
     }
 }
@@ -721,7 +840,7 @@ template <typename T, int R1, int R2, int TC> constexpr bool z_tc_ok() {
 
 inline int z_cols_forced() {
     static const int f = getenv("MOTJVIE_Z_COLS") ? atoi(getenv("MOTJVIE_Z_COLS")) : 0;
-    return f;
+    return f ? f : cur_sched().z_cols;
 }
 
 template <typename T, int R1, int R2> bool z_green_r_go(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
@@ -847,6 +966,253 @@ size_t z0_ws_bytes(const mot_problem *p, int nrhs, size_t csize, size_t *a, size
     return *a + *b;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Picks the launch schedule (Sched) of the Z0 product for one (grid, number of
+// right-hand sides, precision) by timing candidates with CUDA events on the
+// context's stream: coordinate descent over z-pass columns per block, row-pass
+// rows per block, plane-pass block sizes, generic-pass row pairs and tile
+// widths and programmatic dependent launch, each candidate's product checked
+// against the built-in schedule's product (every candidate must give the same
+// result; one that does not is discarded and counted).  Results are cached
+// per process by (grid, M0, right-hand sides, precision).
+template <typename T>
+__global__ void k_diff2(const T *__restrict__ a, const T *__restrict__ b, long n, double *__restrict__ acc) {
+    double d2 = 0.0, r2 = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double x = (double)a[i], y = (double)b[i];
+        d2 += (x - y) * (x - y);
+        r2 += y * y;
+    }
+    d2 = warp_sum(d2);
+    r2 = warp_sum(r2);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, d2);
+        atomicAdd(acc + 1, r2);
+    }
+}
+
+struct TuneCacheEntry {
+    int N[3], M0[3], nrhs, fp32;
+    Sched s;
+    mot_schedule info;
+};
+std::mutex g_tune_mu;
+std::vector<TuneCacheEntry> g_tune_cache;
+
+template <typename T> bool z_cols_valid(int M0z, int tc) {
+    auto ok = [&](auto r1, auto r2) {
+        constexpr int R1 = decltype(r1)::value, R2 = decltype(r2)::value;
+        switch (tc) {
+            case 4: return z_tc_ok<T, R1, R2, 4>();
+            case 8: return z_tc_ok<T, R1, R2, 8>();
+            case 16: return z_tc_ok<T, R1, R2, 16>();
+            case 32: return z_tc_ok<T, R1, R2, 32>();
+            default: return false;
+        }
+    };
+    using std::integral_constant;
+    switch (M0z) {
+        case 20: return ok(integral_constant<int, 5>{}, integral_constant<int, 4>{});
+        case 32: return ok(integral_constant<int, 8>{}, integral_constant<int, 4>{});
+        case 64: return ok(integral_constant<int, 8>{}, integral_constant<int, 8>{});
+        case 72: return ok(integral_constant<int, 9>{}, integral_constant<int, 8>{});
+        case 75: return ok(integral_constant<int, 5>{}, integral_constant<int, 15>{});
+        case 80: return ok(integral_constant<int, 5>{}, integral_constant<int, 16>{});
+        case 90: return ok(integral_constant<int, 9>{}, integral_constant<int, 10>{});
+        case 128: return ok(integral_constant<int, 16>{}, integral_constant<int, 8>{});
+        default: return false;
+    }
+}
+
+inline bool compiled_plane(int Mx, int My) {
+    return Mx == My && (Mx == 20 || Mx == 32 || Mx == 72 || Mx == 75 || Mx == 128);
+}
+inline bool compiled_col(int M) { return M == 32 || M == 64 || M == 128 || M == 160 || M == 270; }
+
+template <typename T>
+mot_status tune_product(mot_problem *p, int nrhs, Sched &best, mot_schedule &info) {
+    const bool fp32 = sizeof(T) == 4;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &e : g_tune_cache)
+            if (e.nrhs == nrhs && e.fp32 == (int)fp32 && !memcmp(e.N, p->N, sizeof e.N) && !memcmp(e.M0, p->M0, sizeof e.M0)) {
+                best = e.s;
+                info = e.info;
+                info.cached = 1;
+                return MOT_OK;
+            }
+    }
+    cudaStream_t st = p->ctx->stream;
+    const long n = (long)nrhs * 3 * p->N[0] * p->N[1] * p->N[2];
+    size_t a, b;
+    z0_ws_bytes(p, nrhs, sizeof(cplx<T>), &a, &b);
+    DBuf x, y, yref, wa, wb, acc;
+    MOT_TRY(dalloc(x, sizeof(T) * n));
+    MOT_TRY(dalloc(y, sizeof(T) * n));
+    MOT_TRY(dalloc(yref, sizeof(T) * n));
+    MOT_TRY(dalloc(wa, a));
+    MOT_TRY(dalloc(wb, b));
+    MOT_TRY(dalloc(acc, 2 * sizeof(double)));
+    {   // a fixed pseudo-random input (any input gives the same timing)
+        std::vector<T> hx(n);
+        uint64_t z = 0x9E3779B97F4A7C15ull;
+        for (long i = 0; i < n; ++i) {
+            z ^= z << 13;
+            z ^= z >> 7;
+            z ^= z << 17;
+            hx[i] = (T)((double)(z >> 11) * 0x1.0p-53 - 0.5);
+        }
+        MOT_CUDA_TRY(cudaMemcpyAsync(x.p, hx.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const long pr = (long)p->N[2] * p->N[1];
+    cudaEvent_t e0, e1;
+    MOT_CUDA_TRY(cudaEventCreate(&e0));
+    MOT_CUDA_TRY(cudaEventCreate(&e1));
+    const bool was = p->capturing;
+    p->capturing = true;  // no kernel-timing events while tuning
+    auto run = [&](const Sched &s, T *out) -> mot_status {
+        SchedScope sc(&s);
+        EpiZ0<T, T> e = {(const T *)x.p, out, eps_of<T>(p), pr, p->N[0]};
+        return z0_product<T, T>(p, (const T *)x.p, nrhs, wa.p, wb.p, e, st);
+    };
+    int reps = 3;
+    auto timeit = [&](const Sched &s, float *ms) -> mot_status {
+        for (int w = 0; w < 2; ++w) MOT_TRY(run(s, (T *)y.p));
+        float bestb = 1e30f;
+        for (int batch = 0; batch < 3; ++batch) {
+            MOT_CUDA_TRY(cudaEventRecord(e0, st));
+            for (int r = 0; r < reps; ++r) MOT_TRY(run(s, (T *)y.p));
+            MOT_CUDA_TRY(cudaEventRecord(e1, st));
+            MOT_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            MOT_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            bestb = std::min(bestb, t / reps);
+        }
+        *ms = bestb;
+        return MOT_OK;
+    };
+    auto diff = [&](double *rel) -> mot_status {
+        MOT_CUDA_TRY(cudaMemsetAsync(acc.p, 0, 2 * sizeof(double), st));
+        count_launch();
+        k_diff2<T><<<grid_for(n), 256, 0, st>>>((const T *)y.p, (const T *)yref.p, n, (double *)acc.p);
+        MOT_CHECK_LAUNCH();
+        double h[2];
+        MOT_CUDA_TRY(cudaMemcpyAsync(h, acc.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        MOT_CUDA_TRY(cudaStreamSynchronize(st));
+        *rel = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+        return MOT_OK;
+    };
+    mot_status rc = MOT_OK;
+    memset(&info, 0, sizeof info);
+    do {
+        Sched base;
+        if ((rc = run(base, (T *)yref.p)) != MOT_OK) break;
+        float t1 = 0.f;
+        MOT_CUDA_TRY(cudaEventRecord(e0, st));
+        if ((rc = run(base, (T *)y.p)) != MOT_OK) break;
+        MOT_CUDA_TRY(cudaEventRecord(e1, st));
+        MOT_CUDA_TRY(cudaEventSynchronize(e1));
+        MOT_CUDA_TRY(cudaEventElapsedTime(&t1, e0, e1));
+        reps = std::max(3, std::min(30, (int)ceil(2.0 / std::max(1e-3f, t1))));
+        float tbest = 0.f;
+        if ((rc = timeit(base, &tbest)) != MOT_OK) break;
+        info.ms_default = tbest;
+        best = base;
+        // candidate values per dimension, for the passes this product uses
+        const bool fused = z0_planes_fit<T>(p);
+        const bool zc = z_cols_valid<T>(p->M0[2], 8) || z_cols_valid<T>(p->M0[2], 16);
+        const bool rows270 = !fused && p->M0[0] == 270;
+        const bool gen_x = !fused ? p->M0[0] != 270 : !compiled_plane(p->M0[0], p->M0[1]);
+        const bool gen_axis = fused ? !compiled_plane(p->M0[0], p->M0[1]) : !compiled_col(p->M0[1]);
+        struct Dim {
+            int Sched::*f;
+            std::vector<int> v;
+        };
+        std::vector<Dim> dims;
+        if (zc) {
+            std::vector<int> v;
+            for (int c : {4, 8, 16, 32})
+                if (z_cols_valid<T>(p->M0[2], c)) v.push_back(c);
+            dims.push_back({&Sched::z_cols, v});
+        }
+        if (rows270) {
+            std::vector<int> v;
+            for (int r : {8, 16, 32})
+                if (p->N[1] % r == 0) v.push_back(r);
+            dims.push_back({&Sched::x_rows, v});
+        }
+        if (fused && compiled_plane(p->M0[0], p->M0[1]) && fp32) {
+            dims.push_back({&Sched::xy_fwd, {256, 384, 512}});
+            dims.push_back({&Sched::xy_inv, {256, 384, 512}});
+        }
+        if (gen_x) dims.push_back({&Sched::gen_pairs, {1, 2, 4, 8}});
+        if (gen_axis) dims.push_back({&Sched::gen_tile, {1, 2, 4, 8, 16}});
+        dims.push_back({&Sched::pdl, {1, 0}});
+        for (auto &d : dims) {
+            for (int v : d.v) {
+                Sched c = best;
+                c.*(d.f) = v;
+                float t = 0.f;
+                if ((rc = timeit(c, &t)) != MOT_OK) break;
+                double rel = 0.0;
+                if ((rc = diff(&rel)) != MOT_OK) break;
+                info.candidates += 1;
+                info.max_rel_diff = std::max(info.max_rel_diff, rel);
+                if (rel > (fp32 ? 1e-6 : 1e-13)) {
+                    info.rejected += 1;
+                    continue;
+                }
+                if (t < 0.99f * tbest) {
+                    tbest = t;
+                    best = c;
+                }
+            }
+            if (rc != MOT_OK) break;
+        }
+        if (rc != MOT_OK) break;
+        info.ms_tuned = tbest;
+    } while (0);
+    p->capturing = was;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MOT_OK) return rc;
+    info.z_cols = best.z_cols;
+    info.x_rows = best.x_rows;
+    info.xy_fwd = best.xy_fwd;
+    info.xy_inv = best.xy_inv;
+    info.pdl = best.pdl;
+    info.gen_pairs = best.gen_pairs;
+    info.gen_tile = best.gen_tile;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        TuneCacheEntry e;
+        memcpy(e.N, p->N, sizeof e.N);
+        memcpy(e.M0, p->M0, sizeof e.M0);
+        e.nrhs = nrhs;
+        e.fp32 = fp32;
+        e.s = best;
+        e.info = info;
+        g_tune_cache.push_back(e);
+    }
+    return MOT_OK;
+}
+
+// the problem's schedule for (nrhs, precision), tuned on first use when the
+// problem's options ask for it (nullptr: built-in rules)
+template <typename T> mot_status schedule_for(mot_problem *p, int nrhs, const Sched **out) {
+    const bool fp32 = sizeof(T) == 4;
+    *out = p->sched_for(nrhs, fp32);
+    if (*out || !p->opt.autotune) return MOT_OK;
+    mot_problem::Tuned t;
+    t.nrhs = nrhs;
+    t.fp32 = fp32;
+    MOT_TRY(tune_product<T>(p, nrhs, t.s, t.info));
+    p->tuned.push_back(t);
+    *out = p->sched_for(nrhs, fp32);
+    return MOT_OK;
+}
+
 // ---------------------------------------------------------------- tables
 // octant of lag k from the library's own quadrature (device), into lags[k]
 mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
@@ -858,10 +1224,10 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
     int rmax = lag_reach(k1, p->rho);
     for (int i = 0; i < 3; ++i) S[i] = std::min(S[i], rmax);
     ItemSet is;
-    build_items(p->rho, S, k0, k1, is);
+    if (!build_items(p->rho, S, k0, k1, is))
+        MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (alpha < 0.5)");
     const int nit = (int)is.items.size();
-    DBuf ditems, dA, dmap;
-    MOT_TRY(dalloc(ditems, sizeof(TableItem) * std::max(1, nit)));
+    DBuf dA, dmap;
     MOT_TRY(dalloc(dA, sizeof(double) * 6 * std::max(1, nit)));
     MOT_TRY(dalloc(dmap, sizeof(int) * is.base.size()));
     std::vector<double> cached;
@@ -869,16 +1235,40 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         MOT_CUDA_TRY(cudaMemcpyAsync(dA.p, cached.data(), sizeof(double) * 6 * nit, cudaMemcpyHostToDevice, st));
         MOT_CUDA_TRY(cudaStreamSynchronize(st));
     } else if (nit > 0) {
+        const int nf = (int)is.faces.size(), nt = (int)is.tri.size();
+        DBuf ditems, dfaces, dtri, dFM, dBM;
+        MOT_TRY(dalloc(ditems, sizeof(TableItem) * nit));
+        MOT_TRY(dalloc(dfaces, sizeof(FaceRec) * std::max(1, nf)));
+        MOT_TRY(dalloc(dtri, sizeof(TripleRec) * std::max(1, nt)));
+        MOT_TRY(dalloc(dFM, sizeof(double) * std::max(1L, is.fm_len)));
+        MOT_TRY(dalloc(dBM, sizeof(double) * std::max(1L, is.bm_len)));
         MOT_CUDA_TRY(cudaMemcpyAsync(ditems.p, is.items.data(), sizeof(TableItem) * nit, cudaMemcpyHostToDevice, st));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dfaces.p, is.faces.data(), sizeof(FaceRec) * nf, cudaMemcpyHostToDevice, st));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dtri.p, is.tri.data(), sizeof(TripleRec) * nt, cudaMemcpyHostToDevice, st));
+        const double *glx = (const double *)p->glx.p, *glw = (const double *)p->glw.p;
         count_launch();
-        k_galerkin_items<<<(nit + 63) / 64, 64, 0, st>>>((const TableItem *)ditems.p, nit, p->rho,
-                                                         (const double *)p->glx.p, (const double *)p->glw.p, kGLN,
-                                                         (double *)dA.p);
+        k_face_moments<<<(nf + 63) / 64, 64, 0, st>>>((const FaceRec *)dfaces.p, nf, p->rho, glx, glw, kGLN,
+                                                      (double *)dFM.p);
+        MOT_CHECK_LAUNCH();
+        count_launch();
+        k_box_moments<<<(nt + 63) / 64, 64, 0, st>>>((const TripleRec *)dtri.p, nt, p->rho, glx, glw, kGLN, kGL8,
+                                                     (double *)dBM.p);
+        MOT_CHECK_LAUNCH();
+        count_launch();
+        k_combine_items<<<(nit + 255) / 256, 256, 0, st>>>((const TableItem *)ditems.p, nit,
+                                                           (const TripleRec *)dtri.p, (const FaceRec *)dfaces.p,
+                                                           (const double *)dFM.p, (const double *)dBM.p,
+                                                           (double *)dA.p);
         MOT_CHECK_LAUNCH();
         std::vector<double> A6(6 * (size_t)nit);
         MOT_CUDA_TRY(cudaMemcpyAsync(A6.data(), dA.p, sizeof(double) * 6 * nit, cudaMemcpyDeviceToHost, st));
         MOT_CUDA_TRY(cudaStreamSynchronize(st));
         tcache_put(p->rho, S, k0, k1, std::move(A6));
+        dfree(ditems);
+        dfree(dfaces);
+        dfree(dtri);
+        dfree(dFM);
+        dfree(dBM);
     }
     std::vector<int> map;
     for (int k = k0; k <= k1; ++k) {
@@ -899,7 +1289,6 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         L.ready = true;
     }
     MOT_CUDA_TRY(cudaStreamSynchronize(st));
-    dfree(ditems);
     dfree(dA);
     dfree(dmap);
     return MOT_OK;
@@ -1076,17 +1465,31 @@ mot_status mot_table_host(double rho, int lag, const int32_t R[3], double *g_out
     for (int i = 0; i < 3; ++i)
         if (R[i] < 0 || R[i] > 4096) MOT_FAIL(MOT_EINVAL, "table extent out of range");
     const HostRule &hr = host_rule();
-    gk::Rule q = {hr.x, hr.w, kGLN};
+    gk::Rule q = {hr.x, hr.w, kGLN}, q8 = {hr.x + kGLN, hr.w + kGLN, kGL8};
     int S[3] = {R[0], R[1], R[2]};
     std::sort(S, S + 3);
     ItemSet is;
-    build_items(rho, S, lag, lag, is);
-    std::vector<double> A6(6 * std::max<size_t>(1, is.items.size()));
+    if (!build_items(rho, S, lag, lag, is))
+        MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (rho < 0.25)");
+    std::vector<double> FM(std::max(1L, is.fm_len), 0.0), BM(std::max(1L, is.bm_len), 0.0);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (long i = 0; i < (long)is.items.size(); ++i) {
-        const TableItem &it = is.items[i];
-        gk::galerkin_A(q, it.k, rho, it.a, it.b, it.c, &A6[6 * i]);
+    for (long i = 0; i < (long)is.faces.size(); ++i) {
+        const FaceRec &f = is.faces[i];
+        if (f.nj > 0) gk::face_moments(q, rho, (double)f.c, (double)f.a, (double)f.b, f.jlo, f.nj, &FM[f.off]);
     }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long i = 0; i < (long)is.tri.size(); ++i) {
+        const TripleRec &t = is.tri[i];
+        if (t.nj <= 0) continue;
+        double *o = &BM[t.off];
+        gk::box_moments(q, q8, rho, t.x, t.y, t.z, t.jlo, t.nj, o);
+        gk::box_moments(q, q8, rho, t.x, t.z, t.y, t.jlo, t.nj, o + 3 * t.nj);
+        gk::box_moments(q, q8, rho, t.y, t.z, t.x, t.jlo, t.nj, o + 6 * t.nj);
+    }
+    std::vector<double> A6(6 * std::max<size_t>(1, is.items.size()));
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)is.items.size(); ++i)
+        combine_item(is.items[i], is.tri.data(), is.faces.data(), FM.data(), BM.data(), &A6[6 * i]);
     std::vector<int> map;
     lag_map(is, lag, map);
     int Ri[3] = {R[0], R[1], R[2]};
@@ -1115,12 +1518,13 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     long nv = (long)n[0] * n[1] * n[2];
     for (long i = 0; i < nv; ++i)
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
-    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 0, 1};
+    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 0, 1, 1};
     if (opt) o = *opt;
     if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
     if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
     if (o.graph < 0 || o.graph > 2) MOT_FAIL(MOT_EINVAL, "graph must be 0, 1 or 2");
+    if (o.autotune != 0 && o.autotune != 1) MOT_FAIL(MOT_EINVAL, "autotune must be 0 or 1");
     MOT_CUDA_TRY(cudaSetDevice(ctx->device));
     mot_problem *p = new mot_problem();
     p->ctx = ctx;
@@ -1160,10 +1564,10 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     }
     {
         const HostRule &hr = host_rule();
-        if ((s = dalloc(p->glx, sizeof(double) * kGLN)) != MOT_OK) return fail(s);
-        if ((s = dalloc(p->glw, sizeof(double) * kGLN)) != MOT_OK) return fail(s);
-        cudaMemcpyAsync(p->glx.p, hr.x, sizeof(double) * kGLN, cudaMemcpyHostToDevice, ctx->stream);
-        cudaMemcpyAsync(p->glw.p, hr.w, sizeof(double) * kGLN, cudaMemcpyHostToDevice, ctx->stream);
+        if ((s = dalloc(p->glx, sizeof(double) * (kGLN + kGL8))) != MOT_OK) return fail(s);
+        if ((s = dalloc(p->glw, sizeof(double) * (kGLN + kGL8))) != MOT_OK) return fail(s);
+        cudaMemcpyAsync(p->glx.p, hr.x, sizeof(double) * (kGLN + kGL8), cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(p->glw.p, hr.w, sizeof(double) * (kGLN + kGL8), cudaMemcpyHostToDevice, ctx->stream);
     }
     for (int i = 0; i < 3; ++i)
         if (!get_tw(p, p->M0[i]) || !get_tw(p, p->Mh[i])) {
@@ -1226,12 +1630,28 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
     MOT_TRY(dalloc(p->wsA, a));
     MOT_TRY(dalloc(p->wsB, b));
     const long pr = (long)p->N[2] * p->N[1];
+    const Sched *sc = nullptr;
     if (dtype == MOT_F64) {
+        MOT_TRY(schedule_for<double>(p, nrhs, &sc));
+        SchedScope scope(sc);
         EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
         return z0_product<double, double>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
     }
+    MOT_TRY(schedule_for<float>(p, nrhs, &sc));
+    SchedScope scope(sc);
     EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+}
+
+mot_status mot_problem_schedule(const mot_problem *p, int nrhs, int dtype, mot_schedule *out) {
+    if (!p || !out) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    for (auto &t : p->tuned)
+        if (t.nrhs == nrhs && t.fp32 == (dtype == MOT_F32)) {
+            *out = t.info;
+            return MOT_OK;
+        }
+    MOT_FAIL(MOT_EINVAL, "no tuned schedule for this (nrhs, dtype)");
 }
 
 mot_status mot_kernel_table(mot_problem *p, int lag, double *g_out, int32_t R_out[3]) {
@@ -2311,6 +2731,11 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     for (int i = 0; i < 4; ++i)
         if (cudaEventCreate(&r->ev[i]) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MOT_ECUDA);
+    {   // launch schedule of the batch's products (tuned once per problem and precision)
+        const Sched *sc = nullptr;
+        s = mixed ? schedule_for<float>(p, nrhs, &sc) : schedule_for<double>(p, nrhs, &sc);
+        if (s != MOT_OK) return fail(s);
+    }
     *out = r;
     return MOT_OK;
 }
@@ -2319,6 +2744,7 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     if (!r) MOT_FAIL(MOT_EINVAL, "run is NULL");
     if (nsteps < 0) MOT_FAIL(MOT_EINVAL, "nsteps < 0");
     MOT_CUDA_TRY(cudaSetDevice(r->p->ctx->device));
+    SchedScope scope(r->p->sched_for(r->B, r->prec == MOT_MIXED));
     const long n = 3L * r->p->N[0] * r->p->N[1] * r->p->N[2] * r->B;
     mot_status result = MOT_OK;
     // graph mode (default): after one eager step (which sets every kernel's
@@ -2419,7 +2845,7 @@ struct CkptHeader {
     uint64_t ring_bytes;  // the whole history ring
     mot_options opt;
 };
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;  // 2: mot_options gained autotune
 
 uint64_t fnv1a(const void *data, size_t bytes) {
     const unsigned char *c = (const unsigned char *)data;
@@ -2712,6 +3138,8 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
     // be in a state where the library's own events must not be recorded)
     const bool was = p->capturing;
     p->capturing = true;
+    // a schedule tuned earlier for this (nrhs, dtype) is used; none is tuned here
+    SchedScope scope(p->sched_for(nrhs, dtype == MOT_F32));
     mot_status st;
     if (dtype == MOT_F64) {
         EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};

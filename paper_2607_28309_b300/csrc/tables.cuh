@@ -2,9 +2,12 @@
 // circulant spectra Lambda_k (Sec. IV: "precomputed spectral coefficients of
 // the circulant Green-function kernel").
 //
-// Lag tables are computed once per sorted offset 0 <= a <= b <= c (one GPU
-// thread per lag/offset item) and spread to the nonnegative octant with the
-// permutation covariance of the Galerkin kernel.  Because g_pp is even in every
+// Lag tables are computed once per sorted offset 0 <= a <= b <= c and spread
+// to the nonnegative octant with the permutation covariance of the Galerkin
+// kernel.  The quadrature runs once per distinct plane integral (one GPU thread
+// per face) and once per sorted offset for the box integrals (one thread per
+// offset), as knot-interval moments; a third kernel combines them into the
+// entries of every lag (one thread per lag/offset item).  Because g_pp is even in every
 // coordinate and g_pq (p != q) is odd in d_p and d_q and even in the third, the
 // DFT of the circulant embedding is real and is a product of one-dimensional
 // cosine / sine sums over the octant:
@@ -19,19 +22,78 @@
 
 namespace mot {
 
-// one item: lag k and sorted offset (a, b, c)
+// one item: lag k and sorted offset (a, b, c); t = its TripleRec
 struct TableItem {
-    int k, a, b, c;
+    int k, a, b, c, t;
 };
 
-__global__ void k_galerkin_items(const TableItem *__restrict__ items, int n, double rho,
-                                 const double *__restrict__ glx, const double *__restrict__ glw, int gln,
-                                 double *__restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// one plane integral of the second-difference stencil: plane at distance c,
+// in-plane offset (a, b) with 0 <= a <= b; its moments are FM[off .. off + 3 nj)
+struct FaceRec {
+    int c, a, b, jlo, nj;
+    long off;
+};
+
+// one sorted offset x <= y <= z: the moments of its three box integrals
+// ((x, y; z), (x, z; y), (y, z; x)) are BM[off + 3 nj comp .. + 3 nj), and
+// face[3 p + e + 1] is the FaceRec of the plane at d_p + e (e = -1, 0, 1)
+struct TripleRec {
+    int x, y, z, jlo, nj;
+    long off;
+    int face[9];
+};
+
+__global__ void k_face_moments(const FaceRec *__restrict__ faces, int n, double rho, const double *__restrict__ glx,
+                               const double *__restrict__ glw, int gln, double *__restrict__ FM) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const FaceRec f = faces[i];
+    if (f.nj <= 0) return;
+    double *o = FM + f.off;
+    for (int m = 0; m < 3 * f.nj; ++m) o[m] = 0.0;
     gk::Rule q = {glx, glw, gln};
-    TableItem it = items[i];
-    gk::galerkin_A(q, it.k, rho, it.a, it.b, it.c, out + 6 * (long)i);
+    gk::face_moments(q, rho, (double)f.c, (double)f.a, (double)f.b, f.jlo, f.nj, o);
+}
+
+// glx / glw hold the gln-point rule followed by the gl8-point rule of the z-lines
+__global__ void k_box_moments(const TripleRec *__restrict__ tri, int n, double rho, const double *__restrict__ glx,
+                              const double *__restrict__ glw, int gln, int gl8, double *__restrict__ BM) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TripleRec t = tri[i];
+    if (t.nj <= 0) return;
+    double *o = BM + t.off;
+    for (int m = 0; m < 9 * t.nj; ++m) o[m] = 0.0;
+    gk::Rule q = {glx, glw, gln}, q8 = {glx + gln, glw + gln, gl8};
+    const double x = t.x, y = t.y, z = t.z;
+    gk::box_moments(q, q8, rho, x, y, z, t.jlo, t.nj, o);
+    gk::box_moments(q, q8, rho, x, z, y, t.jlo, t.nj, o + 3 * t.nj);
+    gk::box_moments(q, q8, rho, y, z, x, t.jlo, t.nj, o + 6 * t.nj);
+}
+
+// A_k(d) of one item from its faces' and boxes' moments: A00, A11, A22, A01, A02, A12
+__host__ __device__ inline void combine_item(const TableItem &it, const TripleRec *tri, const FaceRec *faces,
+                                             const double *FM, const double *BM, double *A6) {
+    const TripleRec &t = tri[it.t];
+    for (int p = 0; p < 3; ++p) {
+        double acc = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            const FaceRec &f = faces[t.face[3 * p + e]];
+            const double v = f.nj > 0 ? gk::lag_from_moments(FM + f.off, f.jlo, f.nj, it.k) : 0.0;
+            acc += (e == 1 ? -2.0 : 1.0) * v;
+        }
+        A6[p] = acc;
+    }
+    for (int c = 0; c < 3; ++c)
+        A6[3 + c] = t.nj > 0 ? gk::lag_from_moments(BM + t.off + 3 * t.nj * c, t.jlo, t.nj, it.k) : 0.0;
+}
+
+__global__ void k_combine_items(const TableItem *__restrict__ items, int n, const TripleRec *__restrict__ tri,
+                                const FaceRec *__restrict__ faces, const double *__restrict__ FM,
+                                const double *__restrict__ BM, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    combine_item(items[i], tri, faces, FM, BM, out + 6 * (long)i);
 }
 
 __host__ __device__ inline int a6_index(int p, int q) {

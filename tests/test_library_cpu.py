@@ -69,7 +69,7 @@ def test_ctypes_structs_match_header(tmp_path):
 
     structs = {"mot_planewave": mot.mot_planewave, "mot_options": mot.mot_options,
                "mot_problem_info": mot.mot_problem_info, "mot_step_stats": mot.mot_step_stats,
-               "mot_request": mot.mot_request, "mot_result": mot.mot_result}
+               "mot_request": mot.mot_request, "mot_result": mot.mot_result, "mot_schedule": mot.mot_schedule}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/motjvie.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -87,4 +87,5 @@ def test_ctypes_structs_match_header(tmp_path):
             assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
     # the binding's defaults follow the header's documented defaults
     o = mot.default_options()
-    assert (o.maxit, o.inner_tol, o.max_refine, o.delta, o.timing, o.guess, o.graph) == (500, 1e-6, 6, 0.0, 0, 0, 1)
+    assert (o.maxit, o.inner_tol, o.max_refine, o.delta, o.timing, o.guess, o.graph, o.autotune) == \
+        (500, 1e-6, 6, 0.0, 0, 0, 1, 1)
