@@ -363,7 +363,13 @@ typedef enum {
     MOT_K_INV_Z0 = 8,       /* inverse xy pass with the plain Z0 epilogue (Eq. 12)         */
     MOT_K_INV_RESIDUAL = 9, /* inverse xy pass with the FP64 residual b - Z0 J            */
     MOT_K_INV_HISTORY = 10, /* inverse xy pass of the history sum forming b_n (Eq. 3)     */
-    MOT_K_CLASSES = 11
+    MOT_K_ROW_FWD = 11,     /* planes too large for shared memory: forward row pass (x)
+                               and forward column pass (y) of a Z0 product                 */
+    MOT_K_ROW_INV = 12,     /* the same: inverse column pass (y) and inverse row pass (x)
+                               with the product's epilogue                                 */
+    MOT_K_VEC = 13,         /* the TFQMR vector kernels of the path whose planes do not
+                               fit in shared memory (half steps, y1, v updates)            */
+    MOT_K_CLASSES = 14
 } mot_kernel_class;
 
 /* Timing-option results of the latest step of run r: the number of launches

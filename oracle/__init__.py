@@ -293,12 +293,22 @@ class Problem:
         return Zk_apply(k, self.N, self.eps, R, g, x)
 
     def solve_Z0(self, b):
+        """J = Z0^-1 b exactly (up to rounding): dense LU with partial pivoting
+        (LAPACK) while 3n <= 12288 unknowns, sparse LU (SuperLU) above that."""
+        import scipy.linalg as sla
         import scipy.sparse.linalg as spla
 
+        rhs = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
         if self._lu is None:
             R, g = self.tables[0]
-            self._lu = spla.splu(assemble_Zk(0, self.N, self.eps, R, g))
-        return self._lu.solve(np.ascontiguousarray(b, dtype=np.float64).reshape(-1)).reshape(b.shape)
+            Z = assemble_Zk(0, self.N, self.eps, R, g)
+            if Z.shape[0] <= 12288:
+                self._lu = ("dense", sla.lu_factor(Z.toarray(), check_finite=False))
+            else:
+                self._lu = ("sparse", spla.splu(Z))
+        kind, f = self._lu
+        x = sla.lu_solve(f, rhs, check_finite=False) if kind == "dense" else f.solve(rhs)
+        return x.reshape(b.shape)
 
     def rhs(self, n, pw, Jhist):
         """b_n = E^i_n - sum_{k=1..ell} Z_k J_{n-k}  (Eq. 3, J_j = 0 for j < 0)."""

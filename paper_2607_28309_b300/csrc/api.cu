@@ -923,10 +923,12 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_FAIL(MOT_EUNSUPPORTED, "fused solver epilogue needs the plane passes");
     } else {
         if (!plain) MOT_FAIL(MOT_EUNSUPPORTED, "row-pass product needs a stored input vector");
+        if (timed) p->kt.begin(st, MOT_K_ROW_FWD);
         if (x_forward_r<TI, T>(plain, A, nrows, Nx, Ny, tx, st)) MOT_CHECK_LAUNCH();
         else MOT_TRY(launch_x_forward<TI, T>(plain, A, nrows, Nx, H, tx, st));
         if (col_r<T, -1>(A, Bf, ty, H, Ny, My, planes, (long)Ny * H, (long)My * H, st)) MOT_CHECK_LAUNCH();
         else MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, planes, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+        if (timed) p->kt.end(st);
     }
     if (launch_z_green_r<T>(p, Bf, tz, nrhs, st)) {
         MOT_CHECK_LAUNCH();
@@ -947,10 +949,12 @@ mot_status z0_product_src(mot_problem *p, Src src, const TI *plain, int nrhs, vo
         MOT_TRY(launch_xy_inverse<T, Epi>(Bf, planes, Nx, Ny, Nz, H, tx, ty, epi, st));
         if (timed) p->kt.end(st);
     } else if constexpr (!Epi::kPlaneOnly) {
+        if (timed) p->kt.begin(st, MOT_K_ROW_INV);
         if (col_r<T, +1>(Bf, A, ty, H, My, Ny, planes, (long)My * H, (long)Ny * H, st)) MOT_CHECK_LAUNCH();
         else MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, planes, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
         if (x_inverse_r<T, Epi>(A, nrows, Nx, Ny, Nz, tx, epi, st)) MOT_CHECK_LAUNCH();
         else MOT_TRY((launch_x_inverse<T, Epi>(A, nrows, Nx, H, tx, epi, st)));
+        if (timed) p->kt.end(st);
     }
     return MOT_OK;
 }
@@ -1757,9 +1761,11 @@ template <typename V> mot_status mvp_y1(mot_run *r, cudaStream_t st) {
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     KrylovView<V> k = kview<V>(r);
     if (!z0_planes_fit<V>(p)) {
+        if (!p->capturing) p->kt.begin(st, MOT_K_VEC);
         count_launch();
         k_tfqmr_y1<V><<<dim3(grid_for(L), r->B), 256, 0, st>>>(k.v[kY1], k.v[kW], k.v[kY2], k.sc, L);
         MOT_CHECK_LAUNCH();
+        if (!p->capturing) p->kt.end(st);
         return mvp<V>(r, k.v[kY1], k.v[kAY1], st);
     }
     SrcY1<V> src = {k.v[kY1], k.v[kW], k.v[kY2], k.sc, L};
@@ -1790,20 +1796,27 @@ mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st, cudaGraphConditionalHan
         MOT_TRY((z0_product_src<SrcY1<V>, V, V>(p, s1, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, ev, st)));
         return MOT_OK;
     }
+    const bool timed = !p->capturing;
+    if (timed) p->kt.begin(st, MOT_K_VEC);
     count_launch();
     k_tfqmr_half_a<V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kY1], k.v[kAY1], k.v[kV], k.sc,
                                                    L, k.p1, ctr);
     MOT_CHECK_LAUNCH();
+    if (timed) p->kt.end(st);
     MOT_TRY(mvp<V>(r, k.v[kY2], k.v[kAY2], st));
+    if (timed) p->kt.begin(st, MOT_K_VEC);
     count_launch();
     k_tfqmr_half_b<V><<<gr, kRedThreads, 0, st>>>(x, k.v[kW], k.v[kD], k.v[kY2], k.v[kAY2], k.v[kRS], k.sc, L, k.p1,
                                                    k.p2, ctr + 1);
     MOT_CHECK_LAUNCH();
+    if (timed) p->kt.end(st);
     MOT_TRY(mvp_y1<V>(r, st));
+    if (timed) p->kt.begin(st, MOT_K_VEC);
     count_launch();
     k_tfqmr_v<V><<<gr, kRedThreads, 0, st>>>(k.v[kV], k.v[kAY1], k.v[kAY2], k.v[kRS], k.sc, L, k.p3, ctr + 2,
                                               (int *)r->ctl.p, h, use_h);
     MOT_CHECK_LAUNCH();
+    if (timed) p->kt.end(st);
     return MOT_OK;
 }
 
@@ -2000,8 +2013,10 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
                                                          Ny, H, tx, ty, st)));
         if (!p->capturing) p->kt.end(st);
     } else {
+        if (!p->capturing) p->kt.begin(st, MOT_K_FWD_RING);
         MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
         MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+        if (!p->capturing) p->kt.end(st);
     }
     const long slot_elems = (long)r->B * 3 * Mz * My * H;
     C *slot = nptr ? (C *)r->ring.p : (C *)ring_slot<T>(r, r->n % p->ell);
@@ -2164,8 +2179,10 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
         MOT_TRY((launch_xy_inverse<T, EpiHistory>(Bf, r->B * 3 * Nz, Nx, Ny, Nz, H, tx, ty, e, st)));
         if (!p->capturing) p->kt.end(st);
     } else {
+        if (!p->capturing) p->kt.begin(st, MOT_K_INV_HISTORY);
         MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
         MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
+        if (!p->capturing) p->kt.end(st);
     }
     return MOT_OK;
 }
