@@ -210,7 +210,8 @@ def oracle_sample(w, mvps_per_step: float, rows: int = 2048, seed: int = 0):
 # ---------------------------------------------------------------- roofline bookkeeping
 KERNEL_NAMES = {
     "z_green": "k_z_green_r (present-time z pass)",
-    "z_history": "k_hist_acc + k_col_r (history sum and its inverse z pass)",
+    "z_history": "k_hist_acc + k_col_r (lag 1 onto the step's partial history sum, inverse z pass)",
+    "hist_side": "k_hist_block + k_hist_acc (time-blocked history: block pass at a block start, near lags 2..)",
     "fwd_half": "k_xy_forward_r<SrcHalfA> (forward xy pass of Z0 y2 + first TFQMR half step)",
     "fwd_y1": "k_xy_forward_r<SrcY1> (forward xy pass of Z0 y1)",
     "fwd_plain": "k_xy_forward_r<SrcPlain> (forward xy pass, stored input)",
@@ -226,10 +227,14 @@ KERNEL_NAMES = {
 }
 
 
-def kernel_bytes(info, N, B, prec, lags):
+def kernel_bytes(info, N, B, prec, steps, TB=None):
     """Algorithmic bytes of one launch of each timed kernel class: every array
-    the kernel must read or write once, nothing for re-reads.  lags: the
-    history lag count of each timed step (for the history z pass)."""
+    the kernel must read or write once, nothing for re-reads.  steps: the
+    indices of the timed steps (the history classes depend on them); TB: the
+    time block of the history (8 in the mixed path, 4 in FP64)."""
+    if TB is None:
+        TB = 8 if prec == 1 else 4
+    ell = info.ell
     nv = N[0] * N[1] * N[2]
     cs = 8 if prec == 1 else 16          # complex element of the FFT precision (MOT_MIXED = 1)
     rs = cs // 2                         # real element of the solve precision
@@ -244,10 +249,30 @@ def kernel_bytes(info, N, B, prec, lags):
     eps = nv * rs
     slot = B * 3 * Mh[2] * Mh[1] * Hh * cs
     lam_h = 6 * Kh[2] * Kh[1] * Hh * rs
-    zh = sum(L * (slot + lam_h) + plh for L in lags) / max(len(lags), 1)
+
+    def side(m):
+        """the time-blocked history work that prepares step m: the block pass at a
+        block start (ring slots read once for the block's TB steps, Lambda_2.. read
+        once, TB partial sums written) and the near accumulation of lags 2..t+1
+        onto the step's partial sum (read and written)"""
+        t = m % TB
+        b = 0
+        if t == 0:
+            U = max(0, min(ell - 1, m - 1))
+            b += U * slot + min(ell - 1, U + TB) * lam_h + TB * slot
+        near = max(0, min(t + 1, m, ell) - 1)
+        if near:
+            b += near * (slot + lam_h) + 2 * slot
+        return b
+
+    nsteps = max(len(steps), 1)
+    # the critical path: lag 1 onto the step's partial sum, inverse z pass of the Nz kept planes
+    zh = sum((2 * slot + lam_h if m >= 1 else slot) + plh for m in steps) / nsteps
+    hside = sum(side(m) for m in steps) / nsteps
     return {
         "z_green": 2 * pl0 + 6 * K0[2] * K0[1] * H0 * rs,
         "z_history": zh,
+        "hist_side": hside,
         "fwd_half": 10 * vec + pl0,      # read d, y1, w, Ay1, v, x; write x, w, d, y2; write planes
         "fwd_y1": 3 * vec + pl0,         # read w, y2; write y1; write planes
         "fwd_plain": vec64 + pl0,        # the FP64 J of the residual product
@@ -394,7 +419,7 @@ def native(args, ws, rank, local):
     mot.mot_run_step(krun, max(args.warmup, ell + 1), None, None, allow_notconv=True)
     kstats = []
     ktimes = {}  # class -> [launches, total ms] over the timed steps
-    for _ in range(5):
+    for _ in range(8):  # one whole time block of the history
         mot.mot_run_step(krun, 1, None, kst, allow_notconv=True)
         s = kst[0]
         kstats.append((s.iters, s.sweeps, s.relres, s.mvps))
@@ -405,8 +430,9 @@ def native(args, ws, rank, local):
     k_n0 = mot.mot_run_step_index(krun) - len(kstats)
     # the mixed march's currents at a step past the history length, for its
     # relative L2 error against the FP64 march below
-    n_cmp = mot.mot_run_step_index(krun) + 3
-    mot.mot_run_step(krun, 3, None, None, allow_notconv=True)
+    n_cmp = ell + 1 + 10 + 3  # past the FP64 run's timed steps below
+    if mot.mot_run_step_index(krun) < n_cmp:
+        mot.mot_run_step(krun, n_cmp - mot.mot_run_step_index(krun), None, None, allow_notconv=True)
     J_mixed = None
     if prec == mot.MOT_MIXED:
         J_mixed = torch.empty(B * 3 * nv, dtype=torch.float64, device=dev)
@@ -419,7 +445,7 @@ def native(args, ws, rank, local):
     # ---- roofline of the dominant kernel class (algorithmic bytes / event time)
     peak, peak_kind = _peaks()
     nsteps_k = len(kstats)
-    kb = kernel_bytes(info, N, B, prec, [min(n, ell) for n in range(k_n0, k_n0 + nsteps_k)])
+    kb = kernel_bytes(info, N, B, prec, list(range(k_n0, k_n0 + nsteps_k)))
     per_kernel = {}
     for name, (n, tot) in ktimes.items():
         if n == 0:

@@ -353,7 +353,7 @@ void mot_server_destroy(mot_server *s);
  * counterpart in the paper.                                                    */
 typedef enum {
     MOT_K_Z_GREEN = 0,      /* present-time z pass: FFT z, Lambda0 multiply, IFFT z (Eq. 11) */
-    MOT_K_Z_HISTORY = 1,    /* history z pass: sum_k Lambda_k Jhat_{n-k} and IFFT z (Eq. 3)  */
+    MOT_K_Z_HISTORY = 1,    /* history z pass: lag 1 onto the step's lags 2.. sum, IFFT z (Eq. 3) */
     MOT_K_FWD_HALF = 2,     /* forward xy pass of Z0 y2 with the first TFQMR half step     */
     MOT_K_FWD_Y1 = 3,       /* forward xy pass of Z0 y1 forming y1 = w + beta y2           */
     MOT_K_FWD_PLAIN = 4,    /* forward xy pass of a stored vector (other Z0 products)     */
@@ -369,7 +369,10 @@ typedef enum {
                                with the product's epilogue                                 */
     MOT_K_VEC = 13,         /* the TFQMR vector kernels of the path whose planes do not
                                fit in shared memory (half steps, y1, v updates)            */
-    MOT_K_CLASSES = 14
+    MOT_K_HIST_SIDE = 14,   /* time-blocked history: the block pass over the ring at a
+                               block start and the near accumulation of lags 2.. of the
+                               step (in graph mode they run beside the previous step)     */
+    MOT_K_CLASSES = 15
 } mot_kernel_class;
 
 /* Timing-option results of the latest step of run r: the number of launches

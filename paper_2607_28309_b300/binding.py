@@ -54,7 +54,7 @@ EXPORTED = [
 
 # mot_kernel_class values, in order
 KERNEL_CLASSES = ["z_green", "z_history", "fwd_half", "fwd_y1", "fwd_plain", "fwd_ring", "inv_half", "inv_v",
-                  "inv_z0", "inv_residual", "inv_history", "row_fwd", "row_inv", "vec"]
+                  "inv_z0", "inv_residual", "inv_history", "row_fwd", "row_inv", "vec", "hist_side"]
 
 
 class MotError(RuntimeError):

@@ -451,8 +451,12 @@ struct mot_run {
     DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
     DBuf ring, wsAh, wsBh;
     DBuf hacc;  // history accumulation on the full Mh grid [B][3][Mhz][Mhy][Hh]
-    DBuf hpart;  // the lags 2.. part of a step's history sum (same layout as hacc)
-    bool hpart_ok = false;  // hpart holds the lags 2.. sum of step n (the step graph leaves it so)
+    // time-blocked history: the lags 2.. partial sums of the steps of the current
+    // time block, hTB + 1 rotating slots of hacc's layout (slot m mod (hTB + 1))
+    DBuf hpart;
+    int hTB = 8;
+    bool hpart_ok = false;  // the slot of step n holds its whole lags 2.. sum (the step graph leaves it so)
+    bool q_stale = false;   // the slots hold nothing usable (a loaded checkpoint): rebuild from the block start
     cudaStream_t hside = nullptr;  // step graph: low-priority branch of the next step's partial sum
     cudaEvent_t hfork = nullptr, hjoin = nullptr;
     bool hjoin_open = false;  // capture: the branch still has to join the step's stream
@@ -2056,39 +2060,86 @@ int hist_side_threads() {
     return (f == 64 || f == 128 || f == 256) ? f : 256;
 }
 
-// hpart = sum over lags 2..min(m, ell) of Lambda_k Jhat_{m-k}, m = r->n (or *nptr + dm)
+// the near accumulation's load mode: 0 plain loads + L2 prefetch, 1 evict-first +
+// prefetch (default beside the solve), 2 evict-first only
 int hist_side_mode() {
     static const int f = getenv("MOTJVIE_HIST_SIDE_MODE") ? atoi(getenv("MOTJVIE_HIST_SIDE_MODE")) : 1;
     return (f >= 0 && f <= 2) ? f : 1;
 }
 
+template <typename T> QSlots<T> qslots(mot_run *r, int flags) {
+    const mot_problem *p = r->p;
+    const long slot = (long)r->B * 3 * p->Mh[2] * p->Mh[1] * p->Hh;
+    return QSlots<T>{(cplx<T> *)r->hpart.p, slot, r->hTB, flags};
+}
+
+// the time-blocked pass over the ring for the block starting at m0 (outputs
+// t >= tlo); with nptr the kernel reads m0 = *nptr + dm and runs only at a
+// block start
 template <typename T>
-mot_status hist_partial(mot_run *r, cudaStream_t st, const long long *nptr, int dm, unsigned blocks, int bt = 256,
-                        int mode = 0) {
+mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const long long *nptr, int dm) {
     mot_problem *p = r->p;
     const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
     Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
-    const auto *ring = (const cplx<T> *)r->ring.p;
-    auto *out = (cplx<T> *)r->hpart.p;
+    const QSlots<T> q = qslots<T>(r, 0);
+    const long points = (long)r->B * (Mz / 2 + 1) * (My / 2 + 1) * H;
+    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, 32L * p->ctx->sms));
+    // TH outputs per thread: 4 in FP32, 2 in FP64 (registers); TB / TH thread groups
+    constexpr int TH = sizeof(T) == 4 ? 4 : 2;
     count_launch();
-    if (mode == 1)
-        k_hist_acc<T, 1><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
-                                                p->ell, nptr, dm);
-    else if (mode == 2)
-        k_hist_acc<T, 2><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
-                                                p->ell, nptr, dm);
+    if (r->hTB == 8)
+        k_hist_block<T, 8, TH><<<grid, dim3(32, 4, 8 / TH), 0, st>>>((const cplx<T> *)r->ring.p, Lh_of<T>(p), q.buf,
+                                                                     q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo,
+                                                                     nptr, dm);
     else
-        k_hist_acc<T, 0><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, out, Mz, My, H, oc, r->B, p->ell, r->n, 2,
-                                                p->ell, nptr, dm);
+        k_hist_block<T, 4, TH><<<grid, dim3(32, 4, 4 / TH), 0, st>>>((const cplx<T> *)r->ring.p, Lh_of<T>(p), q.buf,
+                                                                     q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo,
+                                                                     nptr, dm);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
 
-// before a step-graph launch: the graph expects the partial sum of step n in hpart
+// the near accumulation of step m (lags 2 .. (m mod hTB) + 1, onto its slot)
+template <typename T>
+mot_status hist_near(mot_run *r, cudaStream_t st, long m, const long long *nptr, int dm, unsigned blocks, int bt,
+                     int mode) {
+    mot_problem *p = r->p;
+    const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
+    Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
+    const auto *ring = (const cplx<T> *)r->ring.p;
+    const QSlots<T> q = qslots<T>(r, kQBase | kQAcc | kQNear);
+    count_launch();
+    if (mode == 1)
+        k_hist_acc<T, 1><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, nullptr, Mz, My, H, oc, r->B, p->ell, m, 2,
+                                                p->ell, nptr, dm, q);
+    else if (mode == 2)
+        k_hist_acc<T, 2><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, nullptr, Mz, My, H, oc, r->B, p->ell, m, 2,
+                                                p->ell, nptr, dm, q);
+    else
+        k_hist_acc<T, 0><<<blocks, bt, 0, st>>>(ring, Lh_of<T>(p), nullptr, nullptr, Mz, My, H, oc, r->B, p->ell, m, 2,
+                                                p->ell, nptr, dm, q);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+
+// the lags 2.. sum of step m = r->n into its slot, host-driven: the block pass
+// at a block start (or from the block start onwards when the slots are stale),
+// then the near accumulation -- the kernels the step graph runs beside step m-1
+template <typename T> mot_status hist_side_host(mot_run *r, cudaStream_t st, unsigned blocks, int bt, int mode) {
+    const long m = r->n;
+    const int t = (int)(m % r->hTB);
+    if (t == 0 || r->q_stale) {
+        MOT_TRY(hist_block_pass<T>(r, st, m - t, t, nullptr, 0));
+        r->q_stale = false;
+    }
+    return hist_near<T>(r, st, m, nullptr, 0, blocks, bt, mode);
+}
+
+// before a step-graph launch: the graph expects the lags 2.. sum of step n in its slot
 mot_status hist_prime(mot_run *r, cudaStream_t st) {
     if (!hist_streaming(r) || r->hpart_ok) return MOT_OK;
-    if (r->prec == MOT_MIXED) MOT_TRY(hist_partial<float>(r, st, nullptr, 0, hist_blocks(r, 32)));
-    else MOT_TRY(hist_partial<double>(r, st, nullptr, 0, hist_blocks(r, 32)));
+    if (r->prec == MOT_MIXED) MOT_TRY(hist_side_host<float>(r, st, hist_blocks(r, 32), 256, 0));
+    else MOT_TRY(hist_side_host<double>(r, st, hist_blocks(r, 32), 256, 0));
     r->hpart_ok = true;
     return MOT_OK;
 }
@@ -2128,20 +2179,25 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
         Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
         C *acc = (C *)r->hacc.p;
         const unsigned blocks = hist_blocks(r, 32);
-        if (!p->capturing) p->kt.begin(st, MOT_K_Z_HISTORY);
         if (!nptr) {
-            MOT_TRY(hist_partial<T>(r, st, nullptr, 0, blocks));
-            r->hpart_ok = false;  // hpart now holds this step's partial sum, not the next one's
+            if (!p->capturing) p->kt.begin(st, MOT_K_HIST_SIDE);
+            MOT_TRY(hist_side_host<T>(r, st, blocks, 256, 0));
+            if (!p->capturing) p->kt.end(st);
+            r->hpart_ok = false;  // the slots now serve this step, not the next one
         }
+        if (!p->capturing) p->kt.begin(st, MOT_K_Z_HISTORY);
         count_launch();
-        k_hist_acc<T><<<blocks, 256, 0, st>>>((const C *)r->ring.p, Lh_of<T>(p), (const C *)r->hpart.p, acc, Mz, My, H,
-                                              oc, r->B, p->ell, r->n, 1, 1, nptr, 0);
+        k_hist_acc<T><<<blocks, 256, 0, st>>>((const C *)r->ring.p, Lh_of<T>(p), nullptr, acc, Mz, My, H, oc, r->B,
+                                              p->ell, r->n, 1, 1, nptr, 0, qslots<T>(r, kQBase));
         MOT_CHECK_LAUNCH();
         if (nptr) {
+            // beside the solve: the next step's block pass (at a block start) and near accumulation
             MOT_CUDA_TRY(cudaEventRecord(r->hfork, st));
             MOT_CUDA_TRY(cudaStreamWaitEvent(r->hside, r->hfork, 0));
             const int bt = hist_side_threads();
-            MOT_TRY(hist_partial<T>(r, r->hside, nptr, 1, hist_blocks(r, hist_side_per_sm_x2(), bt), bt, hist_side_mode()));
+            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, nptr, 1));
+            MOT_TRY(hist_near<T>(r, r->hside, 0, nptr, 1, hist_blocks(r, hist_side_per_sm_x2(), bt), bt,
+                                 hist_side_mode()));
             MOT_CUDA_TRY(cudaEventRecord(r->hjoin, r->hside));
             r->hjoin_open = true;
         }
@@ -2705,7 +2761,9 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
     if ((s = dalloc(r->ring, ring_bytes)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->hacc, ring_bytes / p->ell)) != MOT_OK) return fail(s);
-    if ((s = dalloc(r->hpart, ring_bytes / p->ell)) != MOT_OK) return fail(s);
+    // time block: 8 steps in FP32, 4 in FP64 (the block pass holds that many outputs in registers)
+    r->hTB = mixed ? 8 : 4;
+    if ((s = dalloc(r->hpart, ring_bytes / p->ell * (r->hTB + 1))) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     for (int i = 0; i < 10; ++i)
@@ -2743,6 +2801,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(p->wsB, bb)) != MOT_OK) return fail(s);
     cudaStream_t st = p->ctx->stream;
     cudaMemsetAsync(r->ring.p, 0, ring_bytes, st);
+    cudaMemsetAsync(r->hpart.p, 0, r->hpart.bytes, st);
     cudaMemsetAsync(r->J.p, 0, sizeof(double) * n, st);
     cudaMemsetAsync(r->J2.p, 0, sizeof(double) * n, st);
     for (int i = 0; i < 4; ++i)
@@ -2971,6 +3030,8 @@ mot_status mot_run_load(mot_problem *p, const char *path, mot_run **out) {
         return s;
     }
     r->n = hd.n;
+    r->q_stale = true;  // the time-block slots are rebuilt from the ring before the next step
+    r->hpart_ok = false;
     *out = r;
     return MOT_OK;
 }

@@ -822,12 +822,33 @@ template <int Mode, typename V> __device__ __forceinline__ V hist_ld(const V *p)
     else return __ldcs(p);
 }
 
+// Time-blocked history (see k_hist_block): the lags 2.. partial sums of the
+// steps of one time block live in TB + 1 rotating slots, slot m mod (TB + 1) for
+// step m.  QSlots tells the accumulation which of its operands is such a slot.
+template <typename T> struct QSlots {
+    cplx<T> *buf;   // TB + 1 slots of the full half spectrum (nullptr: not used)
+    long slot;      // elements per slot
+    int TB;         // steps per time block
+    int flags;      // kQBase: base = slot of step m; kQAcc: acc = that slot; kQNear: lags 2..(m mod TB)+1
+};
+constexpr int kQBase = 1, kQAcc = 2, kQNear = 4;
+
 template <typename T, int Mode = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
-                                                  const cplx<T> *__restrict__ base, cplx<T> *__restrict__ acc, int Mz,
+                                                  const cplx<T> *base, cplx<T> *acc, int Mz,
                                                   int My, int H, Octant oc, int nrhs, int ell, long m, int klo,
-                                                  int kcap, const long long *__restrict__ nptr, int dm) {
+                                                  int kcap, const long long *__restrict__ nptr, int dm,
+                                                  QSlots<T> qs = QSlots<T>{nullptr, 0, 0, 0}) {
     if (nptr) m = (long)*nptr + dm;  // graph mode: step index from device memory
+    if (qs.buf) {
+        cplx<T> *q = qs.buf + (m % (qs.TB + 1)) * qs.slot;
+        if (qs.flags & kQBase) base = q;
+        if (qs.flags & kQAcc) acc = q;
+        if (qs.flags & kQNear) {
+            kcap = (int)(m % qs.TB) + 1;  // lags 2 .. t+1 of the step's place t in its block
+            if (kcap < klo) return;       // first step of a block: the block pass covered every lag >= 2
+        }
+    }
     int kend = (int)(m < ell ? m : ell);
     if (kend > kcap) kend = kcap;
     using C = cplx<T>;
@@ -899,6 +920,115 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
             if (!on) continue;
 #pragma unroll
             for (int q = 0; q < 3; ++q) acc[off[r] + q * slot_comp] = a[r][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// time-blocked history (Eq. 3): the lags >= 2 part of the history sums of the
+// TB steps m0 .. m0 + TB - 1 of one time block, computed in one pass.  Output t
+// (step m0 + t) gets the lags k >= t + 2, whose currents J_{m0+t-k} are all
+// older than m0 - 1; the lags 2 .. t + 1 are added before step m0 + t (kQNear
+// accumulation) and lag 1 in the step itself, so each step's sum is the same
+// lags 2.. partial sum in a different order of terms:
+//   Q[(m0 + t) mod (TB+1)] = sum_{k = t+2 .. min(ell, m0 + t)} Lambda_k Jhat_{m0+t-k},  t in [tlo, TB).
+// The pass walks the ring once from the newest slot (m0 - 2) back, each slot
+// read once for all TB outputs; the TB Lambda_k a slot needs (k = u + 2 + t,
+// u its age) slide one lag per slot, kept in a register window rotated by
+// unrolling.  One thread per (octant point, mirror row): block (32, 4), the four
+// mirror rows of 32 consecutive octant points, so the four threads reading the
+// same Lambda value sit in one block (L1) and each warp reads 32 consecutive kx
+// of one row; the block's TB outputs are split over TB / TH thread groups of TH
+// outputs each (the z index), which read the same ring values (L1) and keep
+// TH accumulators and a TH-lag window each.  With nptr: m0 = *nptr + dm, and the
+// pass runs only when m0 is the first step of a block (m0 mod TB == 0).
+// ---------------------------------------------------------------------------
+template <typename T, int TB, int TH>
+__global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hist_block(const cplx<T> *__restrict__ ring,
+                                                                  const T *__restrict__ Lh, cplx<T> *__restrict__ qbuf,
+                                                                  long qslot, int Mz, int My, int H, Octant oc,
+                                                                  int nrhs, int ell, long m0, int tlo,
+                                                                  const long long *__restrict__ nptr, int dm) {
+    static_assert(TB % TH == 0, "outputs per thread divide the block");
+    if (nptr) {
+        m0 = (long)*nptr + dm;
+        if (m0 % TB != 0) return;
+        tlo = 0;
+    }
+    using C = cplx<T>;
+    const int hz = Mz / 2 + 1, hy = My / 2 + 1;
+    const unsigned total = (unsigned)nrhs * hz * hy * H;
+    const long plane = (long)My * H;
+    const long slot_comp = (long)Mz * plane;
+    const long slot_size = (long)nrhs * 3 * slot_comp;
+    const long cs = (long)oc.Kz * oc.Ky * oc.H;
+    const FastDiv fH = make_fastdiv((unsigned)H), fy = make_fastdiv((unsigned)hy), fz_ = make_fastdiv((unsigned)hz);
+    const int r = threadIdx.y;        // mirror row: bit 0 -> ky = My - j, bit 1 -> kz = Mz - fz
+    const int t0 = threadIdx.z * TH;  // this thread's outputs t0 .. t0 + TH - 1
+    const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1), syz = sy * sz;
+    // inputs J_j for j = m0 - 2 - u, u in [0, U): every j >= 0 and within ell of step m0
+    const long U = (m0 - 1 < (long)ell - 1) ? m0 - 1 : (long)ell - 1;
+    for (unsigned idx = blockIdx.x * 32 + threadIdx.x; idx < total; idx += gridDim.x * 32) {
+        unsigned t_ = fdiv(idx, fH);
+        const int kx = (int)(idx - t_ * H);
+        unsigned t2 = fdiv(t_, fy);
+        const int j = (int)(t_ - t2 * hy);
+        const unsigned b = fdiv(t2, fz_);
+        const int fz = (int)(t2 - b * hz);
+        const bool twoy = j != 0 && 2 * j != My;
+        const bool twoz = fz != 0 && 2 * fz != Mz;
+        if (((r & 1) && !twoy) || ((r & 2) && !twoz)) continue;  // self-mirrored row: mirror 0 holds it
+        long off = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
+        if (r & 1) off += (long)(My - 2 * j) * H;
+        if (r & 2) off += (long)(Mz - 2 * fz) * plane;
+        const T *Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
+        C a[TH][3];
+#pragma unroll
+        for (int t = 0; t < TH; ++t)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a[t][q] = cmake<C>(T(0), T(0));
+        // window: at walk position u, output t0 + i needs lag k = u + 2 + t0 + i, held in
+        // lw[(u + i) mod TH]; before the walk lw[i] holds lag 2 + t0 + i
+        T lw[TH][6];
+#pragma unroll
+        for (int i = 0; i < TH; ++i) {
+            const long k = 2 + t0 + i;
+#pragma unroll
+            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = k <= ell ? Lp[k * 6 * cs + c6 * cs] : T(0);
+        }
+        for (long u0 = 0; u0 < U; u0 += TH) {
+#pragma unroll
+            for (int uu = 0; uu < TH; ++uu) {
+                const long u = u0 + uu;
+                if (u >= U) break;
+                const C *R = ring + ((m0 - 2 - u) % ell) * slot_size + off;
+                const C u0v = R[0], u1v = R[slot_comp], u2v = R[2 * slot_comp];
+#pragma unroll
+                for (int i = 0; i < TH; ++i) {
+                    const long k = u + 2 + t0 + i;
+                    if (t0 + i >= tlo && k <= ell) {
+                        const T *g = lw[(uu + i) % TH];
+                        const T gxx = g[0], gyy = g[1], gzz = g[2], exy = sy * g[3], exz = sz * g[4], eyz = syz * g[5];
+                        a[i][0] = cmake<C>(a[i][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
+                                           a[i][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
+                        a[i][1] = cmake<C>(a[i][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
+                                           a[i][1].y + exy * u0v.y + gyy * u1v.y + eyz * u2v.y);
+                        a[i][2] = cmake<C>(a[i][2].x + exz * u0v.x + eyz * u1v.x + gzz * u2v.x,
+                                           a[i][2].y + exz * u0v.y + eyz * u1v.y + gzz * u2v.y);
+                    }
+                }
+                // lw[uu] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
+                const long kn = u + 2 + t0 + TH;
+#pragma unroll
+                for (int c6 = 0; c6 < 6; ++c6) lw[uu][c6] = kn <= ell ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TH; ++i) {
+            if (t0 + i < tlo) continue;
+            C *Q = qbuf + ((m0 + t0 + i) % (TB + 1)) * qslot + off;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Q[q * slot_comp] = a[i][q];
         }
     }
 }

@@ -10,19 +10,31 @@ import types
 import bench
 from paper_2607_28309_b300 import mvp_bench
 
-INFO = types.SimpleNamespace(M0=(72, 72, 72), Mh=(128, 128, 128))
+INFO = types.SimpleNamespace(M0=(72, 72, 72), Mh=(128, 128, 128), ell=26)
 N = (64, 64, 64)
 
 
 def test_z_pass_and_history_bytes_cube64_a8():
-    kb = bench.kernel_bytes(INFO, N, 1, 1, [26])
+    kb = bench.kernel_bytes(INFO, N, 1, 1, [40])
     planes = 3 * 64 * 72 * 37 * 8          # (component, z, ky, kx) complex FP32
     lam0 = 6 * 37 * 37 * 37 * 4            # Lambda0 octant, six components, FP32
     assert kb["z_green"] == 2 * planes + lam0 == 9_399_480
     slot = 3 * 128 * 128 * 65 * 8          # one history-ring slot
     lam_h = 6 * 65 ** 3 * 4                # one Lambda_k octant
     out = 3 * 64 * 128 * 65 * 8            # the Nz kept planes of the inverse z pass
-    assert kb["z_history"] == 26 * (slot + lam_h) + out == 848_680_560
+    # critical path: the step's partial sum + the lag-1 slot + Lambda_1 in, the kept planes out
+    assert kb["z_history"] == 2 * slot + lam_h + out
+    # step 40 is the first of a time block (40 mod 8 = 0): the block pass reads the
+    # 25 ring slots within ell of it and Lambda_2..Lambda_26 once, writes 8 partial sums
+    assert kb["hist_side"] == 25 * slot + 25 * lam_h + 8 * slot
+    # step 43 (t = 3): near lags 2..4 onto its partial sum
+    assert bench.kernel_bytes(INFO, N, 1, 1, [43])["hist_side"] == 3 * (slot + lam_h) + 2 * slot
+    # averaged over a whole block (steps 40..47): one block pass, near lags 1+2+...+7 = 28,
+    # seven near read-modify-writes of a partial sum; less than half the direct sum's
+    # 26 (slot + Lambda) per step
+    kb8 = bench.kernel_bytes(INFO, N, 1, 1, list(range(40, 48)))
+    assert kb8["hist_side"] * 8 == 25 * slot + 25 * lam_h + 8 * slot + 28 * (slot + lam_h) + 7 * 2 * slot
+    assert kb8["hist_side"] + kb8["z_history"] - out < 26 * (slot + lam_h) / 2
 
 
 def test_fused_solver_pass_bytes_cube64_a8():
@@ -37,8 +49,8 @@ def test_fused_solver_pass_bytes_cube64_a8():
 
 
 def test_fp64_doubles_the_real_element():
-    k32 = bench.kernel_bytes(INFO, N, 1, 1, [26])
-    k64 = bench.kernel_bytes(INFO, N, 1, 0, [26])
+    k32 = bench.kernel_bytes(INFO, N, 1, 1, [41], TB=8)
+    k64 = bench.kernel_bytes(INFO, N, 1, 0, [41], TB=8)
     assert k64["z_green"] == 2 * k32["z_green"]
     assert k64["z_history"] == 2 * k32["z_history"]
 
