@@ -217,6 +217,19 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
  * Errors: MOT_EINVAL, MOT_ECUDA.                                              */
 mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
 
+/* y = Z0 x by direct summation over the nonzero entries of the present-time
+ * matrix (the paper's "direct" product, Sec. IV and V-A, here on the GPU):
+ * (Z0 x)_p(m) = eps(m) T(0) x_p(m) - (eps(m) - 1) sum_d sum_q g0(d)_pq x_q(m - d)
+ * over the offsets d of the lag-0 support (x = 0 outside the grid).  Same
+ * arguments, layout and precision choice as mot_apply_Z0, same result up to
+ * rounding; its cost grows with nnz(Z0) (the number of offsets grows as
+ * alpha^3), the FFT product's does not, so it is the faster of the two at small
+ * alpha only.  One kernel launch, shared-memory tiles of the input with a halo
+ * of the table's reach.  Allocates the offset list on its first call (per
+ * precision).  Errors: MOT_EINVAL, MOT_EUNSUPPORTED (reach too large for a
+ * tile), MOT_ENOMEM, MOT_ECUDA.                                                 */
+mot_status mot_apply_Z0_direct(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
+
 /* The library's own Galerkin table of lag `lag` (0 <= lag <= ell):
  * g_out[6][2Rz+1][2Ry+1][2Rx+1] doubles, components (xx, yy, zz, xy, xz, yz),
  * offset d = (dx, dy, dz) at index (dz+Rz, dy+Ry, dx+Rx); R_out receives

@@ -39,7 +39,7 @@ __all__ = [
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
     "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED", "mot_request", "mot_result",
     "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
-    "mot_schedule", "mot_problem_schedule",
+    "mot_schedule", "mot_problem_schedule", "mot_apply_Z0_direct",
 ]
 
 # every symbol include/motjvie.h declares
@@ -49,7 +49,7 @@ EXPORTED = [
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "mot_kernel_launches", "mot_apply_Z0_static", "mot_run_kernel_times", "mot_run_save", "mot_run_load",
     "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",
-    "mot_problem_schedule",
+    "mot_problem_schedule", "mot_apply_Z0_direct",
 ]
 
 # mot_kernel_class values, in order
@@ -128,6 +128,7 @@ def lib():
         L.mot_problem_destroy.restype = None
         L.mot_apply_Z0.argtypes = [P, P, P, I, I]
         L.mot_apply_Z0_static.argtypes = [P, P, P, I, I]
+        L.mot_apply_Z0_direct.argtypes = [P, P, P, I, I]
         L.mot_kernel_table.argtypes = [P, I, P, P]
         L.mot_set_kernel_table.argtypes = [P, I, P, P]
         L.mot_table_host.argtypes = [D, I, P, P]
@@ -223,6 +224,11 @@ def mot_apply_Z0(prob, x_dev, y_dev, nrhs: int, dtype: int):
 def mot_apply_Z0_static(prob, x_dev, y_dev, nrhs: int, dtype: int):
     """y = Z0 x using the library's static device scratch (no allocation)."""
     _check(lib().mot_apply_Z0_static(prob, _ptr(x_dev), _ptr(y_dev), int(nrhs), int(dtype)))
+
+
+def mot_apply_Z0_direct(prob, x_dev, y_dev, nrhs: int, dtype: int):
+    """y = Z0 x by direct summation over the lag-0 support (the paper's direct product)."""
+    _check(lib().mot_apply_Z0_direct(prob, _ptr(x_dev), _ptr(y_dev), int(nrhs), int(dtype)))
 
 
 def mot_kernel_table(prob, lag: int):

@@ -20,6 +20,7 @@
 #include "spectral.cuh"
 #include "tables.cuh"
 #include "peak.cuh"
+#include "direct.cuh"
 
 #include <atomic>
 #include <mutex>
@@ -421,6 +422,11 @@ struct mot_problem {
         mot_schedule info;
     };
     std::vector<Tuned> tuned;
+    // the direct product's offset list of the lag-0 support (per precision and tile)
+    struct DirectList {
+        int fp32 = -1, SX = 0, SY = 0, nd = 0;
+        DBuf d, g;
+    } direct;
     const Sched *sched_for(int nrhs, bool fp32) const {
         for (auto &t : tuned)
             if (t.nrhs == nrhs && t.fp32 == (int)fp32) return &t.s;
@@ -1435,6 +1441,82 @@ bool finite_all(const double *a, long n) {
 // ============================================================================
 // C ABI
 // ============================================================================
+namespace {
+// tile of the direct product: the largest of 8x8x8 .. 4x4x2 whose haloed
+// three-component input fits in shared memory
+bool direct_tile(const mot_problem *p, size_t es, int *t) {
+    const int R[3] = {p->lags[0].R[0], p->lags[0].R[1], p->lags[0].R[2]};
+    const int cand[][3] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 2}, {4, 2, 2}, {2, 2, 2}};
+    for (auto &c : cand) {
+        const size_t smem = 3 * es * (size_t)(c[0] + 2 * R[0]) * (c[1] + 2 * R[1]) * (c[2] + 2 * R[2]);
+        if (smem <= kSmemMax) {
+            t[0] = c[0];
+            t[1] = c[1];
+            t[2] = c[2];
+            return true;
+        }
+    }
+    return false;
+}
+
+// the nonzero offsets of the lag-0 table with their signed values, as the
+// direct kernel reads them (tile offsets for the haloed tile SX x SY)
+template <typename T> mot_status direct_list(mot_problem *p, int SX, int SY) {
+    auto &D = p->direct;
+    const int fp32 = sizeof(T) == 4;
+    if (D.fp32 == fp32 && D.SX == SX && D.SY == SY) return MOT_OK;
+    const LagTable &L = p->lags[0];
+    const int R[3] = {L.R[0], L.R[1], L.R[2]};
+    const long on = (long)(R[0] + 1) * (R[1] + 1) * (R[2] + 1);
+    std::vector<double> oct(6 * on);
+    MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+    MOT_CUDA_TRY(cudaMemcpy(oct.data(), L.oct.p, sizeof(double) * 6 * on, cudaMemcpyDeviceToHost));
+    std::vector<int4> dl;
+    std::vector<T> gv;
+    for (int dz = -R[2]; dz <= R[2]; ++dz)
+        for (int dy = -R[1]; dy <= R[1]; ++dy)
+            for (int dx = -R[0]; dx <= R[0]; ++dx) {
+                const long oi = ((long)std::abs(dz) * (R[1] + 1) + std::abs(dy)) * (R[0] + 1) + std::abs(dx);
+                const double sx = dx < 0 ? -1.0 : 1.0, sy = dy < 0 ? -1.0 : 1.0, sz = dz < 0 ? -1.0 : 1.0;
+                double g[6] = {oct[oi], oct[on + oi], oct[2 * on + oi], sx * sy * oct[3 * on + oi],
+                               sx * sz * oct[4 * on + oi], sy * sz * oct[5 * on + oi]};
+                bool any = false;
+                for (double v : g) any = any || v != 0.0;
+                if (!any) continue;
+                dl.push_back(make_int4(dx, dy, dz, (dz * SY + dy) * SX + dx));
+                for (double v : g) gv.push_back((T)v);
+            }
+    MOT_TRY(dalloc(D.d, sizeof(int4) * std::max<size_t>(1, dl.size())));
+    MOT_TRY(dalloc(D.g, sizeof(T) * std::max<size_t>(1, gv.size())));
+    if (!dl.empty()) {
+        MOT_CUDA_TRY(cudaMemcpy(D.d.p, dl.data(), sizeof(int4) * dl.size(), cudaMemcpyHostToDevice));
+        MOT_CUDA_TRY(cudaMemcpy(D.g.p, gv.data(), sizeof(T) * gv.size(), cudaMemcpyHostToDevice));
+    }
+    D.fp32 = fp32;
+    D.SX = SX;
+    D.SY = SY;
+    D.nd = (int)dl.size();
+    return MOT_OK;
+}
+
+template <typename T> mot_status z0_direct(mot_problem *p, const T *x, T *y, int nrhs, cudaStream_t st) {
+    int t[3];
+    if (!direct_tile(p, sizeof(T), t)) MOT_FAIL(MOT_EUNSUPPORTED, "lag-0 reach too large for the direct product's tile");
+    const int R[3] = {p->lags[0].R[0], p->lags[0].R[1], p->lags[0].R[2]};
+    const int SX = t[0] + 2 * R[0], SY = t[1] + 2 * R[1], SZ = t[2] + 2 * R[2];
+    MOT_TRY(direct_list<T>(p, SX, SY));
+    const size_t smem = 3 * sizeof(T) * (size_t)SX * SY * SZ;
+    MOT_TRY(allow_smem<k_z0_direct<T>>());
+    const int tiles = ((p->N[0] + t[0] - 1) / t[0]) * ((p->N[1] + t[1] - 1) / t[1]) * ((p->N[2] + t[2] - 1) / t[2]);
+    count_launch();
+    k_z0_direct<T><<<dim3(tiles, nrhs), dim3(t[0], t[1], t[2]), smem, st>>>(
+        x, y, eps_of<T>(p), (const int4 *)p->direct.d.p, (const T *)p->direct.g.p, p->direct.nd, R[0], R[1], R[2],
+        p->N[0], p->N[1], p->N[2]);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *mot_last_error(void) { return get_error(); }
@@ -1608,6 +1690,8 @@ void mot_problem_destroy(mot_problem *p) {
     cudaStreamSynchronize(p->ctx->stream);
     dfree(p->eps);
     dfree(p->eps32);
+    dfree(p->direct.d);
+    dfree(p->direct.g);
     for (auto *t : p->tws) {
         dfree(t->tw64);
         dfree(t->tw32);
@@ -1649,6 +1733,16 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
     SchedScope scope(sc);
     EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+}
+
+mot_status mot_apply_Z0_direct(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
+    if (!p || !x_dev || !y_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
+    if (nrhs < 1 || nrhs > 65535) MOT_FAIL(MOT_EINVAL, "nrhs out of range [1, 65535]");
+    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
+    MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    if (dtype == MOT_F64) return z0_direct<double>(p, (const double *)x_dev, (double *)y_dev, nrhs, p->ctx->stream);
+    return z0_direct<float>(p, (const float *)x_dev, (float *)y_dev, nrhs, p->ctx->stream);
 }
 
 mot_status mot_problem_schedule(const mot_problem *p, int nrhs, int dtype, mot_schedule *out) {
@@ -2083,18 +2177,29 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const 
     Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
     const QSlots<T> q = qslots<T>(r, 0);
     const long points = (long)r->B * (Mz / 2 + 1) * (My / 2 + 1) * H;
-    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, 32L * p->ctx->sms));
-    // TH outputs per thread: 4 in FP32, 2 in FP64 (registers); TB / TH thread groups
-    constexpr int TH = sizeof(T) == 4 ? 4 : 2;
+    // blocks per SM (MOTJVIE_HIST_BLOCK_BPS overrides, for sweeps)
+    static const long bps = getenv("MOTJVIE_HIST_BLOCK_BPS") ? std::max(1, atoi(getenv("MOTJVIE_HIST_BLOCK_BPS"))) : 32;
+    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, bps * p->ctx->sms));
+    // TH outputs per thread: 4 in FP32, 2 in FP64 (registers); TB / TH thread groups.
+    // MOTJVIE_HIST_TH = 2 forces two outputs per thread in FP32 (sweeps)
+    static const int th_env = getenv("MOTJVIE_HIST_TH") ? atoi(getenv("MOTJVIE_HIST_TH")) : 0;
+    const auto *ring = (const cplx<T> *)r->ring.p;
     count_launch();
-    if (r->hTB == 8)
-        k_hist_block<T, 8, TH><<<grid, dim3(32, 4, 8 / TH), 0, st>>>((const cplx<T> *)r->ring.p, Lh_of<T>(p), q.buf,
-                                                                     q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo,
-                                                                     nptr, dm);
-    else
-        k_hist_block<T, 4, TH><<<grid, dim3(32, 4, 4 / TH), 0, st>>>((const cplx<T> *)r->ring.p, Lh_of<T>(p), q.buf,
-                                                                     q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo,
-                                                                     nptr, dm);
+    if (r->hTB == 8) {
+        if (sizeof(T) == 4 && th_env != 2)
+            k_hist_block<T, 8, 4><<<grid, dim3(32, 4, 2), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
+                                                                  r->B, p->ell, m0, tlo, nptr, dm);
+        else
+            k_hist_block<T, 8, 2><<<grid, dim3(32, 4, 4), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
+                                                                  r->B, p->ell, m0, tlo, nptr, dm);
+    } else {
+        if (sizeof(T) == 4 && th_env != 2)
+            k_hist_block<T, 4, 4><<<grid, dim3(32, 4, 1), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
+                                                                  r->B, p->ell, m0, tlo, nptr, dm);
+        else
+            k_hist_block<T, 4, 2><<<grid, dim3(32, 4, 2), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
+                                                                  r->B, p->ell, m0, tlo, nptr, dm);
+    }
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }

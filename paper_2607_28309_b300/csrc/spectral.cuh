@@ -943,6 +943,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // TH accumulators and a TH-lag window each.  With nptr: m0 = *nptr + dm, and the
 // pass runs only when m0 is the first step of a block (m0 mod TB == 0).
 // ---------------------------------------------------------------------------
+constexpr int kHistBlockAhead = 4;  // ring slots prefetched ahead by the block pass
+
 template <typename T, int TB, int TH>
 __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hist_block(const cplx<T> *__restrict__ ring,
                                                                   const T *__restrict__ Lh, cplx<T> *__restrict__ qbuf,
@@ -1001,6 +1003,16 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
             for (int uu = 0; uu < TH; ++uu) {
                 const long u = u0 + uu;
                 if (u >= U) break;
+                if (u + kHistBlockAhead < U) {  // L2 prefetch kHistBlockAhead slots ahead: more loads in flight
+                    const C *Rp = ring + ((m0 - 2 - u - kHistBlockAhead) % ell) * slot_size + off;
+                    prefetch_l2(Rp);
+                    prefetch_l2(Rp + slot_comp);
+                    prefetch_l2(Rp + 2 * slot_comp);
+                    const long kp = u + 2 + t0 + TH + kHistBlockAhead;
+                    if (kp <= ell && r == 0)
+#pragma unroll
+                        for (int c6 = 0; c6 < 6; ++c6) prefetch_l2(Lp + kp * 6 * cs + c6 * cs);
+                }
                 const C *R = ring + ((m0 - 2 - u) % ell) * slot_size + off;
                 const C u0v = R[0], u1v = R[slot_comp], u2v = R[2 * slot_comp];
 #pragma unroll
