@@ -563,6 +563,36 @@ def native(args, ws, rank, local):
             except Exception as e:  # reported, not fatal
                 extra[label] = {"error": str(e)[:200]}
 
+    # ---- direct product (sum over the lag-0 support) against the FFT product, by
+    # time-step size: the alpha crossover on the 64^3 cube (FP32, L2 flushed)
+    crossover = {}
+    if not args.no_extra:
+        try:
+            from paper_2607_28309_b300 import synthetic as syn
+
+            for a in (1.0, 2.0, 4.0, 8.0, 16.0):
+                wc = syn.cube64(a)
+                pc = mot.mot_problem_create(ctx, wc["N"], wc["h"], wc["eps"], wc["alpha"], gopt)
+                nvc = int(np.prod(wc["N"]))
+                xc = torch.randn(1, 3, nvc, dtype=torch.float32, device=dev)
+                yf, yd = torch.empty_like(xc), torch.empty_like(xc)
+                row = {}
+                for nm, fn in (("fft_us", lambda: mot.mot_apply_Z0(pc, xc, yf, 1, mot.MOT_F32)),
+                               ("direct_us", lambda: mot.mot_apply_Z0_direct(pc, xc, yd, 1, mot.MOT_F32))):
+                    for _ in range(3):
+                        fn()
+                    tt = []
+                    for _ in range(10):
+                        flush.zero_()
+                        tt.append(_events_ms(stream, fn))
+                    row[nm] = statistics.median(tt) * 1e3
+                row["rel_l2_direct_vs_fft"] = float(torch.linalg.vector_norm(yd - yf) / torch.linalg.vector_norm(yf))
+                row["r0"] = mot.mot_problem_info_get(pc).r0
+                crossover[f"alpha{int(a)}"] = row
+                mot.mot_problem_destroy(pc)
+        except Exception as e:  # reported, not fatal
+            crossover["error"] = str(e)[:200]
+
     # ---- the Z0 product alone on the 60%-of-HBM target workloads
     targets = {}
     if not args.no_targets:
@@ -576,6 +606,14 @@ def native(args, ws, rank, local):
                                                      "pass_frac", "M0", "nrhs") if k in r_}
             except Exception as e:  # reported, not fatal
                 targets[label] = {"error": str(e)[:200]}
+
+    # ---- serving: a Poisson stream of runs of mixed size through the server
+    serving = {}
+    if args.serve_runs > 0:
+        try:
+            serving = serve_stream(mot, ctx, args.serve_runs, args.serve_steps_scale, args.serve_slots)
+        except Exception as e:  # reported, not fatal
+            serving = {"error": str(e)[:300]}
 
     mot.mot_ctx_destroy(ctx)
 
@@ -601,10 +639,120 @@ def native(args, ws, rank, local):
         "relres_max": max(s[2] for s in stats),
         "steady_state": steady, "setup_s": t_setup, "schedule": schedule,
         "same_gpu": compare, "other_workloads": extra, "fma_peak": fma,
-        "z0_mvp": mvp, "z0_mvp_targets": targets, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
+        "z0_mvp": mvp, "z0_mvp_targets": targets, "z0_crossover": crossover, "serving": serving,
+        "roofline": roofline, "e2e": e2e,
+        "gpu_launches": int(launches),
         "clocks": clocks,
     }
     return res, w, mvps / K
+
+
+def serve_requests(nruns: int, steps_scale: float, seed: int = 5):
+    """The serving recipe: 50 % cubes with edge in {24, 32, ..., 96} (eps_r U[1.5, 6] per
+    4^3 block), 50 % n x n pillar arrays, n in {2, 3, 4} (32n x 32n x 80, layer eps_r
+    U[1.5, 6] per pillar); alpha in {4, 8, 16}; steps U{100..300} times steps_scale;
+    mixed precision; one plane wave along +z (cubes) or -z (pillars)."""
+    import numpy as np
+
+    from paper_2607_28309_b300 import synthetic
+
+    u = synthetic.splitmix64(seed, 8 * nruns)
+    out = []
+    for i in range(nruns):
+        a = u[8 * i: 8 * i + 8]
+        alpha = (4.0, 8.0, 16.0)[int(a[1] * 3)]
+        steps = max(3, int(round((100 + int(a[2] * 201)) * steps_scale)))
+        if a[0] < 0.5:
+            edge = 24 + 8 * int(a[3] * 10)
+            N = (edge, edge, edge)
+            eps = synthetic.block_eps(N, 4, 1.5, 6.0, seed * 100003 + i)
+            exc = [synthetic.pulse(steps, alpha)]
+            kind = f"cube{edge}"
+        else:
+            n = 2 + int(a[3] * 3)
+            le = synthetic.splitmix64(seed * 7919 + i, 2 * n * n)
+            layers = [(1.5 + 4.5 * le[2 * k], 1.5 + 4.5 * le[2 * k + 1]) for k in range(n * n)]
+            eps = synthetic.pillar_eps(n, n, layer_eps=layers)
+            N = (32 * n, 32 * n, 80)
+            exc = [synthetic.pulse(steps, alpha, khat=(0.0, 0.0, -1.0))]
+            kind = f"pillars{n}x{n}"
+        out.append({"N": N, "eps": np.ascontiguousarray(eps), "alpha": alpha, "steps": steps, "exc": exc,
+                    "kind": kind, "t_gap": float(-math.log(max(a[4], 1e-12)))})
+    return out
+
+
+def serve_stream(mot, ctx, nruns: int, steps_scale: float, slots: int):
+    """Serve the recipe's runs through mot_server_*: calibrate the sustainable rate
+    (runs served one at a time), then submit the stream with Poisson arrivals at
+    0.8 x that rate into a server with `slots` slots; per-run and per-step latency
+    percentiles and the aggregate MOT steps/s."""
+    import threading
+
+    reqs = serve_requests(nruns, steps_scale)
+    h = 10e-9
+    # calibration: the first few requests alone, one after the other
+    ncal = min(6, nruns)
+    srv = mot.mot_server_create(ctx, 0, 1)
+    t0 = time.perf_counter()
+    cal = []
+    for q in reqs[:ncal]:
+        tk = mot.mot_server_submit(srv, q["N"], h, q["eps"], q["alpha"], q["exc"], q["steps"])
+        cal.append(mot.mot_server_wait(srv, tk, 600.0))
+    cal_s = time.perf_counter() - t0
+    mot.mot_server_destroy(srv)
+    mean_run_s = statistics.mean(r.run_ms for r in cal) / 1e3
+    rate = 0.8 / max(mean_run_s, 1e-6)  # runs per second
+    srv = mot.mot_server_create(ctx, 0, slots)
+    tickets = [None] * nruns
+    sub_err = []
+
+    def submitter():
+        t = time.perf_counter()
+        for i, q in enumerate(reqs):
+            t += q["t_gap"] / rate
+            dt = t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            try:
+                tickets[i] = mot.mot_server_submit(srv, q["N"], h, q["eps"], q["alpha"], q["exc"], q["steps"])
+            except Exception as e:  # recorded
+                sub_err.append(str(e)[:100])
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    res = []
+    for i in range(nruns):
+        while tickets[i] is None and th.is_alive():
+            time.sleep(0.001)
+        if tickets[i] is None:
+            continue
+        res.append((reqs[i], mot.mot_server_wait(srv, tickets[i], 3600.0)))
+    th.join()
+    wall = time.perf_counter() - t_start
+    mot.mot_server_destroy(srv)
+    ok = [(q, r) for q, r in res if r.status == 0]
+    steps = sum(r.steps for _, r in ok)
+    run_lat = sorted((r.queue_ms + r.run_ms) for _, r in ok)
+    step50 = sorted(r.step_p50_ms for _, r in ok)
+    step99 = sorted(r.step_p99_ms for _, r in ok)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+    kinds = {}
+    for q, _ in ok:
+        kinds[q["kind"]] = kinds.get(q["kind"], 0) + 1
+    return {"runs": nruns, "completed": len(ok), "failed": len(res) - len(ok), "submit_errors": sub_err[:3],
+            "slots": slots, "steps_scale": steps_scale, "arrival_rate_runs_per_s": rate,
+            "calibration": {"runs": ncal, "mean_run_s": mean_run_s, "wall_s": cal_s},
+            "aggregate_steps_per_s": steps / wall, "steps": steps, "wall_s": wall,
+            "run_latency_ms": {"p50": pct(run_lat, 0.5), "p99": pct(run_lat, 0.99)},
+            "step_latency_ms": {"p50_of_run_p50": pct(step50, 0.5), "p99_of_run_p99": pct(step99, 0.99)},
+            "mix": kinds,
+            "recipe": "cubes 24^3..96^3 (eps U[1.5,6] per 4^3) and 2x2..4x4 pillar arrays (32n x 32n x 80, layer eps "
+                      "U[1.5,6] per pillar), alpha in {4,8,16}, steps U{100..300} x steps_scale, mixed; Poisson "
+                      "arrivals at 0.8 x the rate of runs served one at a time (seed 5)"}
 
 
 def _dev_view(ptr, n, dev):
@@ -821,6 +969,10 @@ def main():
     ap.add_argument("--no-targets", action="store_true", help="skip the Z0 product timings on cube64_b16 and pillars8x8")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 form of the workload")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (cube64_a8, cube64_b16)")
+    ap.add_argument("--serve-runs", type=int, default=48, help="runs of the serving stream (0: skip; recipe: 256)")
+    ap.add_argument("--serve-steps-scale", type=float, default=0.25,
+                    help="fraction of the recipe's 100..300 steps per run (recipe: 1)")
+    ap.add_argument("--serve-slots", type=int, default=8, help="server slots (runs on the GPU at once)")
     ap.add_argument("--graph-mode", default="step", choices=list(GRAPH_MODES),
                     help="step: one CUDA graph per MOT step (default); loop: host-driven steps, one graph per TFQMR "
                          "loop; none: no CUDA graphs (for per-kernel profilers)")

@@ -23,6 +23,7 @@
 #include "direct.cuh"
 
 #include <atomic>
+#include <memory>
 #include <mutex>
 
 namespace mot {
@@ -394,6 +395,22 @@ struct SchedScope {
     ~SchedScope() { t_sched = prev; }
 };
 
+// device memory shared by problems (the history spectra of problems with the
+// same step, grid and precision): freed with the last problem holding it
+struct SharedDev {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int device = 0;
+    ~SharedDev() {
+        if (!p) return;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        cudaFree(p);
+        cudaSetDevice(cur);
+    }
+};
+
 struct mot_problem {
     mot_ctx *ctx = nullptr;
     KTimer kt;
@@ -410,6 +427,7 @@ struct mot_problem {
     std::vector<LagTable> lags;
     DBuf L0_64, L0_32;  // [6][K0z][K0y][H0]
     DBuf Lh_64, Lh_32;  // [ell+1][6][Khz][Khy][Hh]
+    std::shared_ptr<SharedDev> lh_hold[2];  // set when Lh_64 / Lh_32 is shared (not owned)
     bool hist64 = false, hist32 = false;
     DBuf glx, glw;
     // Z0 product workspace
@@ -1375,8 +1393,80 @@ mot_status build_Z0_spectrum(mot_problem *p) {
     return MOT_OK;
 }
 
+// process-wide registry of history spectra on the device: problems with the
+// same device, step (rho), grid, history grid and precision and no caller-
+// supplied lag tables share one copy (their spectra do not depend on eps_r)
+struct SpecKey {
+    int device;
+    double rho;
+    int N[3], Mh[3], ell, fp32;
+    bool operator==(const SpecKey &o) const {
+        return device == o.device && rho == o.rho && !memcmp(N, o.N, sizeof N) && !memcmp(Mh, o.Mh, sizeof Mh) &&
+               ell == o.ell && fp32 == o.fp32;
+    }
+};
+std::mutex g_spec_mu;
+std::vector<std::pair<SpecKey, std::weak_ptr<SharedDev>>> g_spec;
+
+SpecKey spec_key(const mot_problem *p, bool fp32) {
+    SpecKey k;
+    k.device = p->ctx->device;
+    k.rho = p->rho;
+    for (int i = 0; i < 3; ++i) {
+        k.N[i] = p->N[i];
+        k.Mh[i] = p->Mh[i];
+    }
+    k.ell = p->ell;
+    k.fp32 = fp32;
+    return k;
+}
+
+std::shared_ptr<SharedDev> spec_lookup(const SpecKey &k) {
+    std::lock_guard<std::mutex> lk(g_spec_mu);
+    for (auto it = g_spec.begin(); it != g_spec.end();) {
+        if (it->second.expired()) {
+            it = g_spec.erase(it);
+            continue;
+        }
+        if (it->first == k) return it->second.lock();
+        ++it;
+    }
+    return nullptr;
+}
+
+// hand the problem's own spectra buffer over to a shared holder and register it
+void spec_share(mot_problem *p, DBuf &buf, int slot, bool fp32) {
+    auto h = std::make_shared<SharedDev>();
+    h->p = buf.p;
+    h->bytes = buf.bytes;
+    h->device = p->ctx->device;
+    p->lh_hold[slot] = h;
+    std::lock_guard<std::mutex> lk(g_spec_mu);
+    g_spec.emplace_back(spec_key(p, fp32), h);
+}
+
 mot_status build_history_spectra(mot_problem *p, bool want64, bool want32) {
     if ((!want64 || p->hist64) && (!want32 || p->hist32)) return MOT_OK;
+    bool shareable = true;  // no caller-supplied table among the history lags
+    for (int k = 1; k <= p->ell; ++k)
+        if (p->lags[k].override_) shareable = false;
+    if (shareable) {
+        for (int f = 0; f < 2; ++f) {
+            const bool want = f ? want32 : want64;
+            bool &have = f ? p->hist32 : p->hist64;
+            if (!want || have) continue;
+            if (auto h = spec_lookup(spec_key(p, f == 1))) {
+                DBuf &b = f ? p->Lh_32 : p->Lh_64;
+                dfree(b);
+                b.p = h->p;
+                b.bytes = h->bytes;
+                p->lh_hold[f] = h;
+                have = true;
+            }
+        }
+        if ((!want64 || p->hist64) && (!want32 || p->hist32)) return MOT_OK;
+    }
+    const bool new64 = want64 && !p->hist64, new32 = want32 && !p->hist32;
     bool need_oct = false;
     for (int k = 1; k <= p->ell; ++k)
         if (!p->lags[k].ready) need_oct = true;
@@ -1407,6 +1497,10 @@ mot_status build_history_spectra(mot_problem *p, bool want64, bool want32) {
     dfree(tmp);
     if (want64) p->hist64 = true;
     if (want32) p->hist32 = true;
+    if (shareable) {
+        if (new64) spec_share(p, p->Lh_64, 0, false);
+        if (new32) spec_share(p, p->Lh_32, 1, true);
+    }
     return MOT_OK;
 }
 
@@ -1700,6 +1794,11 @@ void mot_problem_destroy(mot_problem *p) {
     for (auto &L : p->lags) dfree(L.oct);
     dfree(p->L0_64);
     dfree(p->L0_32);
+    // shared spectra are released with the holder, not freed here
+    if (p->lh_hold[0]) p->Lh_64.p = nullptr;
+    if (p->lh_hold[1]) p->Lh_32.p = nullptr;
+    p->lh_hold[0].reset();
+    p->lh_hold[1].reset();
     dfree(p->Lh_64);
     dfree(p->Lh_32);
     dfree(p->glx);

@@ -38,6 +38,12 @@ struct ServeJob {
     int done_steps = 0;
     bool inflight = false;
     bool graph_started = false;
+    // set-up (context, problem incl. quadrature, run) on a thread of its own, so
+    // the worker keeps stepping the other runs meanwhile
+    std::thread setup;
+    std::atomic<int> setup_state{0};  // 0 running, 1 done, 2 failed
+    mot_status setup_status = MOT_OK;
+    std::string setup_error;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<float> step_ms;
     int32_t status = MOT_OK;
@@ -55,6 +61,7 @@ struct mot_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ServeJob *> pending;
+    std::vector<ServeJob *> starting;  // admitted, set-up thread running
     std::vector<ServeJob *> active;
     std::map<uint64_t, ServeJob *> jobs;  // every ticket not yet collected
     bool stop = false;
@@ -85,7 +92,8 @@ size_t serve_estimate(const ServeJob &j) {
     b += (size_t)(ell + 1) * 6 * (Mh[2] / 2 + 1) * (Mh[1] / 2 + 1) * Hh * (mixed ? 4 : 8);  // history spectra
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + M0[1]) * H0 * 16;                        // product workspace
     b += 5 * n3 * 8 + 10 * n3 * (mixed ? 4 : 8) + (mixed ? 2 * n3 * 4 : 0);               // J, b, r, Krylov
-    b += (size_t)(ell + 2) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum and partial sum
+    const long tb = mixed ? 8 : 4;  // time block of the history: tb + 1 partial sums
+    b += (size_t)(ell + 1 + tb + 1) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum, partial sums
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + Mh[1]) * Hh * cs;                       // history workspace
     return b + b / 10 + ((size_t)64 << 20);
 }
@@ -192,7 +200,7 @@ void serve_worker(mot_server *s) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop) break;
-            if (s->active.empty() && s->pending.empty())
+            if (s->active.empty() && s->pending.empty() && s->starting.empty())
                 s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
             if (s->stop) break;
             // admission in arrival order; a request that does not fit waits
@@ -200,7 +208,8 @@ void serve_worker(mot_server *s) {
             cudaMemGetInfo(&free_b, &total_b);
             size_t head = free_b > ((size_t)256 << 20) ? free_b - ((size_t)256 << 20) : 0;
             for (auto it = s->pending.begin();
-                 it != s->pending.end() && (int)s->active.size() + (int)admit.size() < s->max_slots;) {
+                 it != s->pending.end() &&
+                 (int)s->active.size() + (int)s->starting.size() + (int)admit.size() < s->max_slots;) {
                 ServeJob *j = *it;
                 if (j->est_bytes > s->budget) {  // can never fit
                     j->status = MOT_ENOMEM;
@@ -217,8 +226,8 @@ void serve_worker(mot_server *s) {
                     ++it;
                 }
             }
-            // nothing running and the oldest request does not fit in free memory: it never will
-            if (s->active.empty() && admit.empty() && !s->pending.empty()) {
+            // nothing running or starting and the oldest request does not fit in free memory: it never will
+            if (s->active.empty() && s->starting.empty() && admit.empty() && !s->pending.empty()) {
                 ServeJob *j = s->pending.front();
                 s->pending.pop_front();
                 j->status = MOT_ENOMEM;
@@ -236,16 +245,40 @@ void serve_worker(mot_server *s) {
                 serve_finish(s, j, MOT_ENOMEM);
                 continue;
             }
-            mot_status st = serve_start(s, j);
-            if (st != MOT_OK) {
-                serve_finish(s, j, st);
-                continue;
-            }
+            j->setup = std::thread([s, j] {
+                cudaSetDevice(s->device);
+                const mot_status st = serve_start(s, j);
+                j->setup_status = st;
+                if (st != MOT_OK) j->setup_error = get_error();
+                j->setup_state.store(st == MOT_OK ? 1 : 2);
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->cv_work.notify_all();
+            });
             std::lock_guard<std::mutex> lk(s->mu);
-            s->active.push_back(j);
+            s->starting.push_back(j);
+        }
+        // runs whose set-up has finished join the active ones
+        bool progressed = false;
+        {
+            std::vector<ServeJob *> ready, still;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (ServeJob *j : s->starting) (j->setup_state.load() ? ready : still).push_back(j);
+                s->starting = still;
+            }
+            for (ServeJob *j : ready) {
+                j->setup.join();
+                progressed = true;
+                if (j->setup_state.load() == 2) {
+                    set_error(j->setup_error);
+                    serve_finish(s, j, j->setup_status);
+                    continue;
+                }
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->active.push_back(j);
+            }
         }
         // one pass over the active runs: collect finished steps, launch the next ones
-        bool progressed = false;
         std::vector<ServeJob *> keep, act;
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -378,6 +411,13 @@ void mot_server_destroy(mot_server *s) {
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    // set-ups in flight finish first; their runs are then cancelled with the active ones
+    for (ServeJob *j : s->starting) {
+        if (j->setup.joinable()) j->setup.join();
+        if (j->setup_state.load() == 1) s->active.push_back(j);
+        else serve_finish(s, j, MOT_ECANCELLED);
+    }
+    s->starting.clear();
     // runs on the GPU finish their current step and are abandoned; waiting ones are cancelled
     for (ServeJob *j : s->active) {
         if (j->ctx) cudaStreamSynchronize(j->ctx->stream);

@@ -116,3 +116,49 @@ def test_admission_budget_and_bounded_wait(ctx):
         assert e.value.status == mot.MOT_EINVAL
     finally:
         mot.mot_server_destroy(srv)
+
+
+def test_problems_of_one_step_and_grid_share_history_spectra(ctx):
+    """Two problems with the same grid and time step (different eps_r) hold one
+    copy of the history spectra Lambda_k on the device (they do not depend on
+    eps_r): the second run costs less device memory by about that size, and
+    each run's currents equal the run alone."""
+    N, alpha, steps = (20, 18, 16), 8.0, 12
+    exc = [synthetic.pulse(steps, alpha)]
+    eps_a = synthetic.block_eps(N, 4, 1.5, 6.0, 91)
+    eps_b = synthetic.block_eps(N, 4, 1.5, 6.0, 92)
+    alone_b = _alone(ctx, N, eps_b, alpha, exc, mot.MOT_MIXED, steps)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    pa = mot.mot_problem_create(ctx, N, 10e-9, eps_a, alpha)
+    ra = mot.mot_run_create(pa, exc, mot.MOT_MIXED)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    pb = mot.mot_problem_create(ctx, N, 10e-9, eps_b, alpha)
+    rb = mot.mot_run_create(pb, exc, mot.MOT_MIXED)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    try:
+        info = mot.mot_problem_info_get(pb)
+        Kh = [m // 2 + 1 for m in info.Mh]
+        spectra = (info.ell + 1) * 6 * Kh[0] * Kh[1] * Kh[2] * 4
+        used_a, used_b = free0 - free1, free1 - free2
+        assert used_a - used_b >= 0.9 * spectra, (used_a, used_b, spectra)
+        nv = int(np.prod(N))
+        J = np.zeros((steps, 1, 3, nv))
+        mot.mot_run_step(rb, steps, J)
+        assert np.abs(J[-1] - alone_b).max() <= 1e-12 * np.abs(alone_b).max()
+        # the first problem goes; the second keeps the shared spectra
+        mot.mot_run_destroy(ra)
+        mot.mot_problem_destroy(pa)
+        ra = pa = None
+        J2 = np.zeros((2, 1, 3, nv))
+        mot.mot_run_step(rb, 2, J2)
+        assert np.isfinite(J2).all() and np.abs(J2).max() > 0
+    finally:
+        if ra is not None:
+            mot.mot_run_destroy(ra)
+        if pa is not None:
+            mot.mot_problem_destroy(pa)
+        mot.mot_run_destroy(rb)
+        mot.mot_problem_destroy(pb)
