@@ -224,10 +224,10 @@ mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, i
  * arguments, layout and precision choice as mot_apply_Z0, same result up to
  * rounding; its cost grows with nnz(Z0) (the number of offsets grows as
  * alpha^3), the FFT product's does not, so it is the faster of the two at small
- * alpha only.  One kernel launch, shared-memory tiles of the input with a halo
- * of the table's reach.  Allocates the offset list on its first call (per
- * precision).  Errors: MOT_EINVAL, MOT_EUNSUPPORTED (reach too large for a
- * tile), MOT_ENOMEM, MOT_ECUDA.                                                 */
+ * alpha only.  One kernel launch: shared-memory tiles of the input with a halo
+ * of the table's reach, or neighbour reads through the caches where such a tile
+ * does not fit.  Allocates the offset list on its first call (per precision).
+ * Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA.                                    */
 mot_status mot_apply_Z0_direct(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype);
 
 /* The library's own Galerkin table of lag `lag` (0 <= lag <= ell):

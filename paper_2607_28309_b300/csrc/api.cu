@@ -1595,8 +1595,17 @@ template <typename T> mot_status direct_list(mot_problem *p, int SX, int SY) {
 
 template <typename T> mot_status z0_direct(mot_problem *p, const T *x, T *y, int nrhs, cudaStream_t st) {
     int t[3];
-    if (!direct_tile(p, sizeof(T), t)) MOT_FAIL(MOT_EUNSUPPORTED, "lag-0 reach too large for the direct product's tile");
     const int R[3] = {p->lags[0].R[0], p->lags[0].R[1], p->lags[0].R[2]};
+    if (!direct_tile(p, sizeof(T), t)) {  // haloed tile too large for shared memory: unstaged kernel
+        MOT_TRY(direct_list<T>(p, 0, 0));
+        const long nv = (long)p->N[0] * p->N[1] * p->N[2];
+        count_launch();
+        k_z0_direct_g<T><<<dim3((unsigned)std::min<long>((nv + 255) / 256, 16L * p->ctx->sms), nrhs), 256, 0, st>>>(
+            x, y, eps_of<T>(p), (const int4 *)p->direct.d.p, (const T *)p->direct.g.p, p->direct.nd, p->N[0],
+            p->N[1], p->N[2]);
+        MOT_CHECK_LAUNCH();
+        return MOT_OK;
+    }
     const int SX = t[0] + 2 * R[0], SY = t[1] + 2 * R[1], SZ = t[2] + 2 * R[2];
     MOT_TRY(direct_list<T>(p, SX, SY));
     const size_t smem = 3 * sizeof(T) * (size_t)SX * SY * SZ;
@@ -2279,20 +2288,20 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const 
     // blocks per SM (MOTJVIE_HIST_BLOCK_BPS overrides, for sweeps)
     static const long bps = getenv("MOTJVIE_HIST_BLOCK_BPS") ? std::max(1, atoi(getenv("MOTJVIE_HIST_BLOCK_BPS"))) : 32;
     const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, bps * p->ctx->sms));
-    // TH outputs per thread: 4 in FP32, 2 in FP64 (registers); TB / TH thread groups.
-    // MOTJVIE_HIST_TH = 2 forces two outputs per thread in FP32 (sweeps)
+    // TH = 2 outputs per thread (TB / TH thread groups): with four, the window and the
+    // outputs spill at the 128-register bound.  MOTJVIE_HIST_TH = 4 forces four in FP32 (sweeps)
     static const int th_env = getenv("MOTJVIE_HIST_TH") ? atoi(getenv("MOTJVIE_HIST_TH")) : 0;
     const auto *ring = (const cplx<T> *)r->ring.p;
     count_launch();
     if (r->hTB == 8) {
-        if (sizeof(T) == 4 && th_env != 2)
+        if (sizeof(T) == 4 && th_env == 4)
             k_hist_block<T, 8, 4><<<grid, dim3(32, 4, 2), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
                                                                   r->B, p->ell, m0, tlo, nptr, dm);
         else
             k_hist_block<T, 8, 2><<<grid, dim3(32, 4, 4), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
                                                                   r->B, p->ell, m0, tlo, nptr, dm);
     } else {
-        if (sizeof(T) == 4 && th_env != 2)
+        if (sizeof(T) == 4 && th_env == 4)
             k_hist_block<T, 4, 4><<<grid, dim3(32, 4, 1), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
                                                                   r->B, p->ell, m0, tlo, nptr, dm);
         else

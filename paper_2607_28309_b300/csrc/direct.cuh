@@ -68,4 +68,36 @@ __global__ void __launch_bounds__(512) k_z0_direct(const T *__restrict__ x, T *_
     yb[2 * nv + m] = e * T(0.5) * tile[2 * sn + c0] - (e - T(1)) * g2;
 }
 
+// the same sum without staging, for reaches whose haloed tile does not fit in
+// shared memory (large alpha, FP64): neighbours are read from global memory
+// (L1 / L2), one thread per voxel of one right-hand side
+template <typename T>
+__global__ void __launch_bounds__(256) k_z0_direct_g(const T *__restrict__ x, T *__restrict__ y,
+                                                     const T *__restrict__ eps, const int4 *__restrict__ dlist,
+                                                     const T *__restrict__ gval, int nd, int Nx, int Ny, int Nz) {
+    const long nv = (long)Nx * Ny * Nz;
+    const int b = blockIdx.y;
+    const T *xb = x + (long)b * 3 * nv;
+    for (long m = (long)blockIdx.x * blockDim.x + threadIdx.x; m < nv; m += (long)gridDim.x * blockDim.x) {
+        const int ox = (int)(m % Nx), oy = (int)((m / Nx) % Ny), oz = (int)(m / ((long)Nx * Ny));
+        T g0 = T(0), g1 = T(0), g2 = T(0);
+        for (int i = 0; i < nd; ++i) {
+            const int4 d = dlist[i];
+            const int sx = ox - d.x, sy = oy - d.y, sz = oz - d.z;
+            if (sx < 0 || sx >= Nx || sy < 0 || sy >= Ny || sz < 0 || sz >= Nz) continue;
+            const long s = ((long)sz * Ny + sy) * Nx + sx;
+            const T *gv = gval + 6 * (long)i;
+            const T u0 = xb[s], u1 = xb[nv + s], u2 = xb[2 * nv + s];
+            g0 += gv[0] * u0 + gv[3] * u1 + gv[4] * u2;
+            g1 += gv[3] * u0 + gv[1] * u1 + gv[5] * u2;
+            g2 += gv[4] * u0 + gv[5] * u1 + gv[2] * u2;
+        }
+        const T e = eps[m];
+        T *yb = y + (long)b * 3 * nv;
+        yb[m] = e * T(0.5) * xb[m] - (e - T(1)) * g0;
+        yb[nv + m] = e * T(0.5) * xb[nv + m] - (e - T(1)) * g1;
+        yb[2 * nv + m] = e * T(0.5) * xb[2 * nv + m] - (e - T(1)) * g2;
+    }
+}
+
 }  // namespace mot

@@ -998,13 +998,18 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
 #pragma unroll
             for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = k <= ell ? Lp[k * 6 * cs + c6 * cs] : T(0);
         }
+        long sl = (m0 - 2) % ell;  // ring slot of input u (decremented, wrapping)
         for (long u0 = 0; u0 < U; u0 += TH) {
+            // fully unrolled with a guard rather than a break: the window index (uu + i) % TH
+            // stays a compile-time constant, so lw and a stay in registers
 #pragma unroll
             for (int uu = 0; uu < TH; ++uu) {
                 const long u = u0 + uu;
-                if (u >= U) break;
+                if (u < U) {
                 if (u + kHistBlockAhead < U) {  // L2 prefetch kHistBlockAhead slots ahead: more loads in flight
-                    const C *Rp = ring + ((m0 - 2 - u - kHistBlockAhead) % ell) * slot_size + off;
+                    long sp = sl - kHistBlockAhead;
+                    if (sp < 0) sp += ell;
+                    const C *Rp = ring + sp * slot_size + off;
                     prefetch_l2(Rp);
                     prefetch_l2(Rp + slot_comp);
                     prefetch_l2(Rp + 2 * slot_comp);
@@ -1013,7 +1018,8 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
 #pragma unroll
                         for (int c6 = 0; c6 < 6; ++c6) prefetch_l2(Lp + kp * 6 * cs + c6 * cs);
                 }
-                const C *R = ring + ((m0 - 2 - u) % ell) * slot_size + off;
+                const C *R = ring + sl * slot_size + off;
+                sl = sl == 0 ? ell - 1 : sl - 1;
                 const C u0v = R[0], u1v = R[slot_comp], u2v = R[2 * slot_comp];
 #pragma unroll
                 for (int i = 0; i < TH; ++i) {
@@ -1033,6 +1039,7 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
                 const long kn = u + 2 + t0 + TH;
 #pragma unroll
                 for (int c6 = 0; c6 < 6; ++c6) lw[uu][c6] = kn <= ell ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+                }
             }
         }
 #pragma unroll
