@@ -169,6 +169,7 @@ typedef struct {
     int32_t pdl;         /* programmatic dependent launch on (1) / off (0)      */
     int32_t gen_pairs;   /* generic row passes: row pairs per block             */
     int32_t gen_tile;    /* generic column passes: columns per block            */
+    int32_t z_tma;       /* 1: the z pass stages its column tiles with TMA      */
     int32_t candidates;  /* candidates timed                                    */
     int32_t rejected;    /* candidates whose product differed (discarded)       */
     int32_t cached;      /* 1: taken from this process's cache, not re-timed    */

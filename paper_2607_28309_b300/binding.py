@@ -77,7 +77,8 @@ class mot_options(ctypes.Structure):
 class mot_schedule(ctypes.Structure):
     _fields_ = [("z_cols", ctypes.c_int32), ("x_rows", ctypes.c_int32), ("xy_fwd", ctypes.c_int32),
                 ("xy_inv", ctypes.c_int32), ("pdl", ctypes.c_int32), ("gen_pairs", ctypes.c_int32),
-                ("gen_tile", ctypes.c_int32), ("candidates", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("gen_tile", ctypes.c_int32), ("z_tma", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("rejected", ctypes.c_int32),
                 ("cached", ctypes.c_int32), ("ms_default", ctypes.c_float), ("ms_tuned", ctypes.c_float),
                 ("max_rel_diff", ctypes.c_double)]
 

@@ -383,6 +383,7 @@ struct Sched {
     int pdl = 1;        // programmatic dependent launch of the chain kernels
     int gen_pairs = 0;  // generic x passes: row pairs per block, 1..8
     int gen_tile = 0;   // generic axis passes: columns per block, power of two
+    int z_tma = 0;      // z pass: stage the column tiles with TMA (cp.async.bulk.tensor) when 1
 };
 thread_local const Sched *t_sched = nullptr;
 inline const Sched &cur_sched() {
@@ -440,6 +441,14 @@ struct mot_problem {
         mot_schedule info;
     };
     std::vector<Tuned> tuned;
+    // TMA descriptors of the z pass, per planes buffer and shape
+    struct ZMap {
+        const void *ptr;
+        long rows, ncols;
+        int Nz, TC, es;
+        CUtensorMap map;
+    };
+    std::vector<ZMap> zmaps;
     // the direct product's offset list of the lag-0 support (per precision and tile)
     struct DirectList {
         int fp32 = -1, SX = 0, SY = 0, nd = 0;
@@ -844,6 +853,59 @@ template <typename T> const T *L0_of(mot_problem *p);
 
 // specialised z pass when M0z = R1 * R2 is one of the compiled shapes;
 // returns false to fall back to the generic pass
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+using TmapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeFn tmap_encoder() {
+    static TmapEncodeFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<TmapEncodeFn>(f);
+    }();
+    return fn;
+}
+
+// the z pass's descriptor over the planes buffer [rows = nrhs 3 Nz][ncols] of
+// complex T, viewed as rows of 2 ncols scalars; box 2 TC scalars x Nz rows.
+// nullptr where TMA cannot address it (row pitch off the 16-byte grid, box too tall)
+template <typename T> const CUtensorMap *z_tmap(mot_problem *p, const cplx<T> *buf, long rows, long ncols, int Nz, int TC) {
+    for (auto &z : p->zmaps)
+        if (z.ptr == buf && z.rows == rows && z.ncols == ncols && z.Nz == Nz && z.TC == TC && z.es == (int)sizeof(T))
+            return &z.map;
+    TmapEncodeFn enc = tmap_encoder();
+    if (!enc || Nz > 256 || (ncols * (long)sizeof(cplx<T>)) % 16 != 0 || ((uintptr_t)buf & 15) != 0) return nullptr;
+    mot_problem::ZMap z;
+    z.ptr = buf;
+    z.rows = rows;
+    z.ncols = ncols;
+    z.Nz = Nz;
+    z.TC = TC;
+    z.es = (int)sizeof(T);
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ncols), (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ncols * sizeof(cplx<T>))};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * TC), (cuuint32_t)Nz};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&z.map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                           (void *)buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    p->zmaps.push_back(z);
+    return &p->zmaps.back().map;
+}
+
+inline bool z_tma_wanted() {
+    static const int f = getenv("MOTJVIE_Z_TMA") ? atoi(getenv("MOTJVIE_Z_TMA")) : -1;
+    return f >= 0 ? f != 0 : cur_sched().z_tma != 0;
+}
+
 template <typename T, int R1, int R2, int TC>
 bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_t st) {
     const int My = p->M0[1], H = p->H0, Nz = p->N[2];
@@ -851,10 +913,21 @@ bool z_green_r_tc(mot_problem *p, cplx<T> *Bf, AxisTw *tz, int nrhs, cudaStream_
     if (smem > kSmemMax || allow_smem<k_z_green_r<T, R1, R2, TC>>() != MOT_OK) return false;
     Octant oc = {p->M0[2], My, p->K0[2], p->K0[1], H};
     dim3 grid((My * H + TC - 1) / TC, (unsigned)nrhs);
+    constexpr size_t smem_t = z_green_r_smem_tma<T, R1, R2, TC>();
+    const CUtensorMap *tm = nullptr;
+    if (z_tma_wanted() && smem_t <= kSmemMax && allow_smem<k_z_green_r<T, R1, R2, TC, true>>() == MOT_OK)
+        tm = z_tmap<T>(p, Bf, (long)nrhs * 3 * Nz, (long)My * H, Nz, TC);
     if (!p->capturing) p->kt.begin(st, MOT_K_Z_GREEN);
     count_launch();
-    launch_chain(k_z_green_r<T, R1, R2, TC>, grid, dim3(3 * TC * R2), smem, st, Bf, L0_of<T>(p), twp<T>(tz), Nz, My, H,
-                 oc);
+    if (tm)
+        launch_chain(k_z_green_r<T, R1, R2, TC, true>, grid, dim3(3 * TC * R2), smem_t, st, Bf, L0_of<T>(p),
+                     twp<T>(tz), Nz, My, H, oc, *tm);
+    else {
+        CUtensorMap none;
+        memset(&none, 0, sizeof none);
+        launch_chain(k_z_green_r<T, R1, R2, TC, false>, grid, dim3(3 * TC * R2), smem, st, Bf, L0_of<T>(p),
+                     twp<T>(tz), Nz, My, H, oc, none);
+    }
     if (!p->capturing) p->kt.end(st);
     return true;
 }
@@ -1167,6 +1240,7 @@ mot_status tune_product(mot_problem *p, int nrhs, Sched &best, mot_schedule &inf
             for (int c : {4, 8, 16, 32})
                 if (z_cols_valid<T>(p->M0[2], c)) v.push_back(c);
             dims.push_back({&Sched::z_cols, v});
+            dims.push_back({&Sched::z_tma, {1}});
         }
         if (rows270) {
             std::vector<int> v;
@@ -1216,6 +1290,7 @@ mot_status tune_product(mot_problem *p, int nrhs, Sched &best, mot_schedule &inf
     info.pdl = best.pdl;
     info.gen_pairs = best.gen_pairs;
     info.gen_tile = best.gen_tile;
+    info.z_tma = best.z_tma;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         TuneCacheEntry e;

@@ -16,6 +16,8 @@
 
 #include <type_traits>
 #include <utility>
+#include <cuda.h>  // CUtensorMap (descriptors are encoded on the host)
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -678,15 +680,52 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // stage A' thread (q, t, c): inverse R1-point DFT over k1, rows z < Nz to HBM.
 // grid = (ceil(My*H/TC), B); smem = (M + 3*TC*(M+1)) complex + 6*(M/2+1)*TC real
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) staging: a 2-D tensor map over the planes buffer
+// viewed as rows of scalars (row = one (b, q, z) plane, 2 * My * H scalars),
+// box = 2 TC scalars x Nz rows (the TC columns of one component's Nz planes);
+// the copy completes on an mbarrier.  The wait is bounded: past the limit the
+// kernel records the fact in g_tma_timeouts and goes on (its output is then
+// wrong and the parity checks catch it) rather than hang.
+// ---------------------------------------------------------------------------
+__device__ unsigned g_tma_timeouts = 0;
+constexpr unsigned kTmaWaitLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase) {
+    for (unsigned it = 0; it < kTmaWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <typename T, int R1, int R2, int TC>
 __host__ __device__ constexpr size_t z_green_r_smem() {
     return (size_t)(R1 * R2 + 3 * TC * (R1 * R2 + 1)) * sizeof(cplx<T>) + (size_t)6 * (R1 * R2 / 2 + 1) * TC * sizeof(T);
 }
-
+// with TMA staging: plus the [3][Nz <= M][TC] landing tile (each component on a
+// 128-byte boundary) and the mbarrier
 template <typename T, int R1, int R2, int TC>
+__host__ __device__ constexpr size_t z_green_r_smem_tma() {
+    return z_green_r_smem<T, R1, R2, TC>() + 128 + 3 * (((size_t)R1 * R2 * TC * sizeof(cplx<T>) + 127) / 128 * 128) + 16;
+}
+
+template <typename T, int R1, int R2, int TC, bool TMA = false>
 __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__ buf, const T *__restrict__ L,
                                                            const cplx<T> *__restrict__ tw_g, int Nz, int My, int H,
-                                                           Octant oc) {
+                                                           Octant oc, const __grid_constant__ CUtensorMap tmap) {
     using C = cplx<T>;
     constexpr int M = R1 * R2, RS = M + 1, KZ = M / 2 + 1;  // RS: padded row stride in shared memory
     constexpr int NT = 3 * TC * R2;
@@ -694,6 +733,12 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *S = tw + M;                                   // [q][c][RS]
     T *sL = reinterpret_cast<T *>(S + 3 * TC * RS);  // [6][KZ][TC]
+    // TMA landing tile [q][z][c] (component stride tstride elements, 128-byte aligned) and its mbarrier
+    unsigned char *tp = smem_raw + z_green_r_smem<T, R1, R2, TC>();
+    tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 127) & ~(uintptr_t)127);
+    C *Tt = reinterpret_cast<C *>(tp);
+    const int tstride = (int)(((size_t)Nz * TC * sizeof(C) + 127) / 128 * 128 / sizeof(C));
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tp + 3 * (size_t)tstride * sizeof(C));
     const int ncols = My * H;
     const int col0 = blockIdx.x * TC;
     const long plane = ncols;                 // z stride
@@ -714,15 +759,33 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
         }
     }
     load_twiddles(tw, tw_g, M);
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     chain_wait_prev();  // the planes come from the previous kernel (Lambda0 and the twiddles do not)
     __syncthreads();
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            const unsigned bytes = 3u * (unsigned)Nz * TC * (unsigned)sizeof(C);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
+                         : "memory");
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq)
+                tma_load_2d(Tt + qq * tstride, &tmap, 2 * col0, (int)((blockIdx.y * 3 + qq) * Nz), bar);
+        }
+        if (!mbar_wait_bounded(bar, 0) && threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1u);
+    }
     // ---- stage A
     {
         C v[R1];
 #pragma unroll
         for (int m = 0; m < R1; ++m) {
             const int z = t + R2 * m;
-            v[m] = (live && z < Nz) ? base[q * comp + (long)z * plane + col0 + c] : cmake<C>(T(0), T(0));
+            if constexpr (TMA) v[m] = z < Nz ? Tt[q * tstride + z * TC + c] : cmake<C>(T(0), T(0));
+            else v[m] = (live && z < Nz) ? base[q * comp + (long)z * plane + col0 + c] : cmake<C>(T(0), T(0));
         }
         dft_small<R1, -1>(v);
         C *row = S + (q * TC + c) * RS;
