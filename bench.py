@@ -576,20 +576,21 @@ def native(args, ws, rank, local):
                 wc = syn.cube64(a)
                 pc = mot.mot_problem_create(ctx, wc["N"], wc["h"], wc["eps"], wc["alpha"], gopt)
                 nvc = int(np.prod(wc["N"]))
-                xc = torch.randn(1, 3, nvc, dtype=torch.float32, device=dev)
-                yf, yd = torch.empty_like(xc), torch.empty_like(xc)
-                row = {}
-                for nm, fn in (("fft_us", lambda: mot.mot_apply_Z0(pc, xc, yf, 1, mot.MOT_F32)),
-                               ("direct_us", lambda: mot.mot_apply_Z0_direct(pc, xc, yd, 1, mot.MOT_F32))):
-                    for _ in range(3):
-                        fn()
-                    tt = []
-                    for _ in range(10):
-                        flush.zero_()
-                        tt.append(_events_ms(stream, fn))
-                    row[nm] = statistics.median(tt) * 1e3
-                row["rel_l2_direct_vs_fft"] = float(torch.linalg.vector_norm(yd - yf) / torch.linalg.vector_norm(yf))
-                row["r0"] = mot.mot_problem_info_get(pc).r0
+                row = {"r0": mot.mot_problem_info_get(pc).r0}
+                for pn, dtc, tdt in (("fp32", mot.MOT_F32, torch.float32), ("fp64", mot.MOT_F64, torch.float64)):
+                    xc = torch.randn(1, 3, nvc, dtype=tdt, device=dev)
+                    yf, yd = torch.empty_like(xc), torch.empty_like(xc)
+                    for nm, fn in (("fft_us", lambda: mot.mot_apply_Z0(pc, xc, yf, 1, dtc)),
+                                   ("direct_us", lambda: mot.mot_apply_Z0_direct(pc, xc, yd, 1, dtc))):
+                        for _ in range(3):
+                            fn()
+                        tt = []
+                        for _ in range(10 if (nm == "fft_us" or a <= 8) else 3):
+                            flush.zero_()
+                            tt.append(_events_ms(stream, fn))
+                        row[f"{pn}_{nm}"] = statistics.median(tt) * 1e3
+                    row[f"{pn}_rel_l2_direct_vs_fft"] = float(torch.linalg.vector_norm(yd - yf) /
+                                                              torch.linalg.vector_norm(yf))
                 crossover[f"alpha{int(a)}"] = row
                 mot.mot_problem_destroy(pc)
         except Exception as e:  # reported, not fatal

@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
             for (int uu = 0; uu < TH; ++uu) {
                 const long u = u0 + uu;
                 if (u < U) {
-                if (u + kHistBlockAhead < U) {  // L2 prefetch kHistBlockAhead slots ahead: more loads in flight
+                if (threadIdx.z == 0 && u + kHistBlockAhead < U) {  // L2 prefetch kHistBlockAhead slots ahead (one group)
                     long sp = sl - kHistBlockAhead;
                     if (sp < 0) sp += ell;
                     const C *Rp = ring + sp * slot_size + off;

@@ -123,7 +123,7 @@ def test_problems_of_one_step_and_grid_share_history_spectra(ctx):
     copy of the history spectra Lambda_k on the device (they do not depend on
     eps_r): the second run costs less device memory by about that size, and
     each run's currents equal the run alone."""
-    N, alpha, steps = (20, 18, 16), 8.0, 12
+    N, alpha, steps = (64, 64, 48), 8.0, 12  # spectra ~130 MB: well above the allocation granularity
     exc = [synthetic.pulse(steps, alpha)]
     eps_a = synthetic.block_eps(N, 4, 1.5, 6.0, 91)
     eps_b = synthetic.block_eps(N, 4, 1.5, 6.0, 92)
