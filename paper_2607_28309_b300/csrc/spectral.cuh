@@ -998,22 +998,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // The pass walks the ring once from the newest slot (m0 - 2) back, each slot
 // read once for all TB outputs; the TB Lambda_k a slot needs (k = u + 2 + t,
 // u its age) slide one lag per slot, kept in a register window rotated by
-// unrolling.  One thread per (octant point, mirror row): block (32, 4), the four
-// mirror rows of 32 consecutive octant points, so the four threads reading the
-// same Lambda value sit in one block (L1) and each warp reads 32 consecutive kx
-// of one row; the block's TB outputs are split over TB / TH thread groups of TH
-// outputs each (the z index), which read the same ring values (L1) and keep
-// TH accumulators and a TH-lag window each.  With nptr: m0 = *nptr + dm, and the
-// pass runs only when m0 is the first step of a block (m0 mod TB == 0).
+// unrolling.  One thread per octant point, holding its four mirrored rows (they
+// share the octant's Lambda values, sign-flipped): twelve ring loads in flight
+// per slot and every Lambda value read once per thread; a warp reads 32
+// consecutive kx of each row.  The block's TB outputs are split over TB / TH
+// thread groups of TH outputs each (block (32, TB / TH)), which read the same
+// ring values (L1).  With nptr: m0 = *nptr + dm, and the pass runs only when m0
+// is the first step of a block (m0 mod TB == 0).
 // ---------------------------------------------------------------------------
 constexpr int kHistBlockAhead = 4;  // ring slots prefetched ahead by the block pass
 
 template <typename T, int TB, int TH>
-__global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hist_block(const cplx<T> *__restrict__ ring,
-                                                                  const T *__restrict__ Lh, cplx<T> *__restrict__ qbuf,
-                                                                  long qslot, int Mz, int My, int H, Octant oc,
-                                                                  int nrhs, int ell, long m0, int tlo,
-                                                                  const long long *__restrict__ nptr, int dm) {
+__global__ void __launch_bounds__(32 * (TB / TH), 384 / (32 * (TB / TH))) k_hist_block(const cplx<T> *__restrict__ ring,
+                                                                 const T *__restrict__ Lh, cplx<T> *__restrict__ qbuf,
+                                                                 long qslot, int Mz, int My, int H, Octant oc,
+                                                                 int nrhs, int ell, long m0, int tlo,
+                                                                 const long long *__restrict__ nptr, int dm) {
     static_assert(TB % TH == 0, "outputs per thread divide the block");
     if (nptr) {
         m0 = (long)*nptr + dm;
@@ -1028,9 +1028,7 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
     const long slot_size = (long)nrhs * 3 * slot_comp;
     const long cs = (long)oc.Kz * oc.Ky * oc.H;
     const FastDiv fH = make_fastdiv((unsigned)H), fy = make_fastdiv((unsigned)hy), fz_ = make_fastdiv((unsigned)hz);
-    const int r = threadIdx.y;        // mirror row: bit 0 -> ky = My - j, bit 1 -> kz = Mz - fz
-    const int t0 = threadIdx.z * TH;  // this thread's outputs t0 .. t0 + TH - 1
-    const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1), syz = sy * sz;
+    const int t0 = threadIdx.y * TH;  // this thread's outputs t0 .. t0 + TH - 1
     // inputs J_j for j = m0 - 2 - u, u in [0, U): every j >= 0 and within ell of step m0
     const long U = (m0 - 1 < (long)ell - 1) ? m0 - 1 : (long)ell - 1;
     for (unsigned idx = blockIdx.x * 32 + threadIdx.x; idx < total; idx += gridDim.x * 32) {
@@ -1042,16 +1040,21 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
         const int fz = (int)(t2 - b * hz);
         const bool twoy = j != 0 && 2 * j != My;
         const bool twoz = fz != 0 && 2 * fz != Mz;
-        if (((r & 1) && !twoy) || ((r & 2) && !twoz)) continue;  // self-mirrored row: mirror 0 holds it
-        long off = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
-        if (r & 1) off += (long)(My - 2 * j) * H;
-        if (r & 2) off += (long)(Mz - 2 * fz) * plane;
+        // the up to four mirrored rows (kz, ky) in {fz, Mz - fz} x {j, My - j}; rows that do not
+        // exist (self-mirrored folds) read row 0 again and are not stored
+        long off[4];
+        off[0] = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
+        off[1] = twoy ? off[0] + (long)(My - 2 * j) * H : off[0];
+        off[2] = twoz ? off[0] + (long)(Mz - 2 * fz) * plane : off[0];
+        off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];
         const T *Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
-        C a[TH][3];
+        C a[TH][4][3];
 #pragma unroll
-        for (int t = 0; t < TH; ++t)
+        for (int i = 0; i < TH; ++i)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) a[t][q] = cmake<C>(T(0), T(0));
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a[i][r][q] = cmake<C>(T(0), T(0));
         // window: at walk position u, output t0 + i needs lag k = u + 2 + t0 + i, held in
         // lw[(u + i) mod TH]; before the walk lw[i] holds lag 2 + t0 + i
         T lw[TH][6];
@@ -1069,48 +1072,60 @@ __global__ void __launch_bounds__(32 * 4 * (TB / TH), 256 / (TB / TH) / 64) k_hi
             for (int uu = 0; uu < TH; ++uu) {
                 const long u = u0 + uu;
                 if (u < U) {
-                if (threadIdx.z == 0 && u + kHistBlockAhead < U) {  // L2 prefetch kHistBlockAhead slots ahead (one group)
-                    long sp = sl - kHistBlockAhead;
-                    if (sp < 0) sp += ell;
-                    const C *Rp = ring + sp * slot_size + off;
-                    prefetch_l2(Rp);
-                    prefetch_l2(Rp + slot_comp);
-                    prefetch_l2(Rp + 2 * slot_comp);
-                    const long kp = u + 2 + t0 + TH + kHistBlockAhead;
-                    if (kp <= ell && r == 0)
+                    if (threadIdx.y == 0 && u + kHistBlockAhead < U) {  // L2 prefetch ahead (one group)
+                        long sp = sl - kHistBlockAhead;
+                        if (sp < 0) sp += ell;
+                        const C *Rp = ring + sp * slot_size;
 #pragma unroll
-                        for (int c6 = 0; c6 < 6; ++c6) prefetch_l2(Lp + kp * 6 * cs + c6 * cs);
-                }
-                const C *R = ring + sl * slot_size + off;
-                sl = sl == 0 ? ell - 1 : sl - 1;
-                const C u0v = R[0], u1v = R[slot_comp], u2v = R[2 * slot_comp];
+                        for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int i = 0; i < TH; ++i) {
-                    const long k = u + 2 + t0 + i;
-                    if (t0 + i >= tlo && k <= ell) {
-                        const T *g = lw[(uu + i) % TH];
-                        const T gxx = g[0], gyy = g[1], gzz = g[2], exy = sy * g[3], exz = sz * g[4], eyz = syz * g[5];
-                        a[i][0] = cmake<C>(a[i][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
-                                           a[i][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
-                        a[i][1] = cmake<C>(a[i][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
-                                           a[i][1].y + exy * u0v.y + gyy * u1v.y + eyz * u2v.y);
-                        a[i][2] = cmake<C>(a[i][2].x + exz * u0v.x + eyz * u1v.x + gzz * u2v.x,
-                                           a[i][2].y + exz * u0v.y + eyz * u1v.y + gzz * u2v.y);
+                            for (int q = 0; q < 3; ++q) prefetch_l2(Rp + off[r] + q * slot_comp);
                     }
-                }
-                // lw[uu] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
-                const long kn = u + 2 + t0 + TH;
+                    const C *R = ring + sl * slot_size;
+                    sl = sl == 0 ? ell - 1 : sl - 1;
+                    C uv[4][3];
 #pragma unroll
-                for (int c6 = 0; c6 < 6; ++c6) lw[uu][c6] = kn <= ell ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) uv[r][q] = R[off[r] + q * slot_comp];
+#pragma unroll
+                    for (int i = 0; i < TH; ++i) {
+                        const long k = u + 2 + t0 + i;
+                        if (t0 + i >= tlo && k <= ell) {
+                            const T *g = lw[(uu + i) % TH];
+                            const T gxx = g[0], gyy = g[1], gzz = g[2];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
+                                const T exy = sy * g[3], exz = sz * g[4], eyz = sy * sz * g[5];
+                                const C u0v = uv[r][0], u1v = uv[r][1], u2v = uv[r][2];
+                                a[i][r][0] = cmake<C>(a[i][r][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
+                                                      a[i][r][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
+                                a[i][r][1] = cmake<C>(a[i][r][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
+                                                      a[i][r][1].y + exy * u0v.y + gyy * u1v.y + eyz * u2v.y);
+                                a[i][r][2] = cmake<C>(a[i][r][2].x + exz * u0v.x + eyz * u1v.x + gzz * u2v.x,
+                                                      a[i][r][2].y + exz * u0v.y + eyz * u1v.y + gzz * u2v.y);
+                            }
+                        }
+                    }
+                    // lw[uu] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
+                    const long kn = u + 2 + t0 + TH;
+#pragma unroll
+                    for (int c6 = 0; c6 < 6; ++c6) lw[uu][c6] = kn <= ell ? Lp[kn * 6 * cs + c6 * cs] : T(0);
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
             if (t0 + i < tlo) continue;
-            C *Q = qbuf + ((m0 + t0 + i) % (TB + 1)) * qslot + off;
+            C *Q = qbuf + ((m0 + t0 + i) % (TB + 1)) * qslot;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) Q[q * slot_comp] = a[i][q];
+            for (int r = 0; r < 4; ++r) {
+                const bool on = (r == 0) || (r == 1 && twoy) || (r == 2 && twoz) || (r == 3 && twoy && twoz);
+                if (!on) continue;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Q[off[r] + q * slot_comp] = a[i][r][q];
+            }
         }
     }
 }
