@@ -2363,27 +2363,15 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const 
     // blocks per SM (MOTJVIE_HIST_BLOCK_BPS overrides, for sweeps)
     static const long bps = getenv("MOTJVIE_HIST_BLOCK_BPS") ? std::max(1, atoi(getenv("MOTJVIE_HIST_BLOCK_BPS"))) : 32;
     const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, bps * p->ctx->sms));
-    // TH outputs per thread (TB / TH thread groups): 2 in FP32, 1 in FP64 -- more spill
-    // past the register bound.  MOTJVIE_HIST_TH = 4 (FP32) / 2 (FP64) forces more (sweeps)
-    static const int th_env = getenv("MOTJVIE_HIST_TH") ? atoi(getenv("MOTJVIE_HIST_TH")) : 0;
     const auto *ring = (const cplx<T> *)r->ring.p;
     if (r->hTB != (sizeof(T) == 4 ? 8 : 4)) MOT_FAIL(MOT_EINVAL, "time block does not match the history precision");
+    // time block 8 (FP32) with two outputs per thread, 4 (FP64) with one: four thread groups
+    constexpr int TB = sizeof(T) == 4 ? 8 : 4, TH = TB / 4;
+    constexpr size_t smem = hist_block_smem<T>();
+    MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
     count_launch();
-    if constexpr (sizeof(T) == 4) {  // time block 8: two outputs per thread, four groups
-        if (th_env == 4)
-            k_hist_block<T, 8, 4><<<grid, dim3(32, 2), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
-                                                               p->ell, m0, tlo, nptr, dm);
-        else
-            k_hist_block<T, 8, 2><<<grid, dim3(32, 4), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
-                                                               p->ell, m0, tlo, nptr, dm);
-    } else {  // time block 4: one output per thread (FP64 registers), four groups
-        if (th_env == 2)
-            k_hist_block<T, 4, 2><<<grid, dim3(32, 2), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
-                                                               p->ell, m0, tlo, nptr, dm);
-        else
-            k_hist_block<T, 4, 1><<<grid, dim3(32, 4), 0, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
-                                                               p->ell, m0, tlo, nptr, dm);
-    }
+    k_hist_block<T, TB, TH><<<grid, dim3(32, 4), smem, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
+                                                            p->ell, m0, tlo, nptr, dm);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }

@@ -651,14 +651,15 @@ __global__ void __launch_bounds__(256) k_z_history(const cplx<T> *__restrict__ r
 }
 
 // ---------------------------------------------------------------------------
-// asynchronous global -> shared copy of one element (4 or 8 bytes), waited for
+// asynchronous global -> shared copy of one element (4, 8 or 16 bytes), waited for
 // with cp_async_wait_all() before the data is read
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src) {
-    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "4-, 8- or 16-byte elements");
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+    else if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::);
@@ -998,29 +999,36 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // The pass walks the ring once from the newest slot (m0 - 2) back, each slot
 // read once for all TB outputs; the TB Lambda_k a slot needs (k = u + 2 + t,
 // u its age) slide one lag per slot, kept in a register window rotated by
-// unrolling.  One thread per octant point, holding its four mirrored rows (they
-// share the octant's Lambda values, sign-flipped): twelve ring loads in flight
-// per slot and every Lambda value read once per thread; a warp reads 32
-// consecutive kx of each row.  The block's TB outputs are split over TB / TH
-// thread groups of TH outputs each (block (32, TB / TH)), which read the same
-// ring values (L1).  With nptr: m0 = *nptr + dm, and the pass runs only when m0
-// is the first step of a block (m0 mod TB == 0).
+// unrolling.  One thread per octant point and group, holding the point's four
+// mirrored rows (they share the octant's Lambda values, sign-flipped); the
+// block's TB outputs are split over four thread groups of TH outputs (block
+// (32, 4)).  The ring values of the block's 32 points stream through a shared-
+// memory pipeline of kHistBlockDepth slots (cp.async, thread group y loading
+// mirror row y), so many slots are in flight without registers and the four
+// groups read each value once from HBM.  With nptr: m0 = *nptr + dm, and the
+// pass runs only when m0 is the first step of a block (m0 mod TB == 0).
 // ---------------------------------------------------------------------------
-constexpr int kHistBlockAhead = 4;  // ring slots prefetched ahead by the block pass
+constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
+
+template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
+    return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
+}
 
 template <typename T, int TB, int TH>
-__global__ void __launch_bounds__(32 * (TB / TH), 384 / (32 * (TB / TH))) k_hist_block(const cplx<T> *__restrict__ ring,
-                                                                 const T *__restrict__ Lh, cplx<T> *__restrict__ qbuf,
-                                                                 long qslot, int Mz, int My, int H, Octant oc,
-                                                                 int nrhs, int ell, long m0, int tlo,
-                                                                 const long long *__restrict__ nptr, int dm) {
-    static_assert(TB % TH == 0, "outputs per thread divide the block");
+__global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
+                                                    cplx<T> *__restrict__ qbuf, long qslot, int Mz, int My, int H,
+                                                    Octant oc, int nrhs, int ell, long m0, int tlo,
+                                                    const long long *__restrict__ nptr, int dm) {
+    static_assert(TB / TH == 4, "four thread groups: group y also loads mirror row y");
+    constexpr int D = kHistBlockDepth;
     if (nptr) {
         m0 = (long)*nptr + dm;
         if (m0 % TB != 0) return;
         tlo = 0;
     }
     using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);  // [D][row 4][component 3][point 32]
     const int hz = Mz / 2 + 1, hy = My / 2 + 1;
     const unsigned total = (unsigned)nrhs * hz * hy * H;
     const long plane = (long)My * H;
@@ -1028,26 +1036,50 @@ __global__ void __launch_bounds__(32 * (TB / TH), 384 / (32 * (TB / TH))) k_hist
     const long slot_size = (long)nrhs * 3 * slot_comp;
     const long cs = (long)oc.Kz * oc.Ky * oc.H;
     const FastDiv fH = make_fastdiv((unsigned)H), fy = make_fastdiv((unsigned)hy), fz_ = make_fastdiv((unsigned)hz);
-    const int t0 = threadIdx.y * TH;  // this thread's outputs t0 .. t0 + TH - 1
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int t0 = y * TH;  // this thread's outputs t0 .. t0 + TH - 1
     // inputs J_j for j = m0 - 2 - u, u in [0, U): every j >= 0 and within ell of step m0
     const long U = (m0 - 1 < (long)ell - 1) ? m0 - 1 : (long)ell - 1;
-    for (unsigned idx = blockIdx.x * 32 + threadIdx.x; idx < total; idx += gridDim.x * 32) {
-        unsigned t_ = fdiv(idx, fH);
-        const int kx = (int)(idx - t_ * H);
-        unsigned t2 = fdiv(t_, fy);
-        const int j = (int)(t_ - t2 * hy);
-        const unsigned b = fdiv(t2, fz_);
-        const int fz = (int)(t2 - b * hz);
-        const bool twoy = j != 0 && 2 * j != My;
-        const bool twoz = fz != 0 && 2 * fz != Mz;
-        // the up to four mirrored rows (kz, ky) in {fz, Mz - fz} x {j, My - j}; rows that do not
-        // exist (self-mirrored folds) read row 0 again and are not stored
-        long off[4];
-        off[0] = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
-        off[1] = twoy ? off[0] + (long)(My - 2 * j) * H : off[0];
-        off[2] = twoz ? off[0] + (long)(Mz - 2 * fz) * plane : off[0];
-        off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];
-        const T *Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
+    for (unsigned base = blockIdx.x * 32; base < total; base += gridDim.x * 32) {
+        const unsigned idx = base + x;
+        const bool valid = idx < total;
+        long off[4] = {0, 0, 0, 0};
+        bool twoy = false, twoz = false;
+        const T *Lp = Lh;
+        if (valid) {
+            unsigned t_ = fdiv(idx, fH);
+            const int kx = (int)(idx - t_ * H);
+            unsigned t2 = fdiv(t_, fy);
+            const int j = (int)(t_ - t2 * hy);
+            const unsigned b = fdiv(t2, fz_);
+            const int fz = (int)(t2 - b * hz);
+            twoy = j != 0 && 2 * j != My;
+            twoz = fz != 0 && 2 * fz != Mz;
+            // the up to four mirrored rows (kz, ky) in {fz, Mz - fz} x {j, My - j}; rows that do
+            // not exist (self-mirrored folds) read row 0 again and are not stored
+            off[0] = (long)b * 3 * slot_comp + (long)fz * plane + (long)j * H + kx;
+            off[1] = twoy ? off[0] + (long)(My - 2 * j) * H : off[0];
+            off[2] = twoz ? off[0] + (long)(Mz - 2 * fz) * plane : off[0];
+            off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];
+            Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
+        }
+        // loader: thread (x, y) copies mirror row y of point x, three components, per slot
+        const long my_off = y == 0 ? off[0] : y == 1 ? off[1] : y == 2 ? off[2] : off[3];
+        long s_issue = (m0 - 2) % ell;  // ring slot of the next slot to load (decremented, wrapping)
+        auto issue = [&](int bslot) {
+            if (valid) {
+                const C *R = ring + s_issue * slot_size + my_off;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) cp_async_elem(buf + ((bslot * 4 + y) * 3 + q) * 32 + x, R + q * slot_comp);
+            }
+            asm volatile("cp.async.commit_group;\n" ::);
+            s_issue = s_issue == 0 ? ell - 1 : s_issue - 1;
+        };
+#pragma unroll 1
+        for (int i = 0; i < D - 1; ++i) {
+            if (i < U) issue(i);
+            else asm volatile("cp.async.commit_group;\n" ::);
+        }
         C a[TH][4][3];
 #pragma unroll
         for (int i = 0; i < TH; ++i)
@@ -1062,32 +1094,25 @@ __global__ void __launch_bounds__(32 * (TB / TH), 384 / (32 * (TB / TH))) k_hist
         for (int i = 0; i < TH; ++i) {
             const long k = 2 + t0 + i;
 #pragma unroll
-            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = k <= ell ? Lp[k * 6 * cs + c6 * cs] : T(0);
+            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = (valid && k <= ell) ? Lp[k * 6 * cs + c6 * cs] : T(0);
         }
-        long sl = (m0 - 2) % ell;  // ring slot of input u (decremented, wrapping)
         for (long u0 = 0; u0 < U; u0 += TH) {
-            // fully unrolled with a guard rather than a break: the window index (uu + i) % TH
-            // stays a compile-time constant, so lw and a stay in registers
+            // fully unrolled with a guard (uniform over the block) rather than a break: the
+            // window index (uu + i) % TH stays a compile-time constant, lw and a in registers
 #pragma unroll
             for (int uu = 0; uu < TH; ++uu) {
                 const long u = u0 + uu;
                 if (u < U) {
-                    if (threadIdx.y == 0 && u + kHistBlockAhead < U) {  // L2 prefetch ahead (one group)
-                        long sp = sl - kHistBlockAhead;
-                        if (sp < 0) sp += ell;
-                        const C *Rp = ring + sp * slot_size;
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) prefetch_l2(Rp + off[r] + q * slot_comp);
-                    }
-                    const C *R = ring + sl * slot_size;
-                    sl = sl == 0 ? ell - 1 : sl - 1;
+                    asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot u landed
+                    __syncthreads();  // ... for every thread; and slot u - 1's buffer is free again
+                    const int bs = (int)(u % D);
                     C uv[4][3];
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) uv[r][q] = R[off[r] + q * slot_comp];
+                        for (int q = 0; q < 3; ++q) uv[r][q] = buf[((bs * 4 + r) * 3 + q) * 32 + x];
+                    if (u + D - 1 < U) issue((int)((u + D - 1) % D));
+                    else asm volatile("cp.async.commit_group;\n" ::);
 #pragma unroll
                     for (int i = 0; i < TH; ++i) {
                         const long k = u + 2 + t0 + i;
@@ -1111,10 +1136,14 @@ __global__ void __launch_bounds__(32 * (TB / TH), 384 / (32 * (TB / TH))) k_hist
                     // lw[uu] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
                     const long kn = u + 2 + t0 + TH;
 #pragma unroll
-                    for (int c6 = 0; c6 < 6; ++c6) lw[uu][c6] = kn <= ell ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+                    for (int c6 = 0; c6 < 6; ++c6)
+                        lw[uu][c6] = (valid && kn <= ell) ? Lp[kn * 6 * cs + c6 * cs] : T(0);
                 }
             }
         }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();  // the buffers are reused by the next chunk of points
+        if (!valid) continue;
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
             if (t0 + i < tlo) continue;
