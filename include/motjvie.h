@@ -80,9 +80,11 @@ typedef struct {
     int maxit;        /* TFQMR iteration cap per solve (default 500)             */
     double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-6)      */
     int max_refine;   /* MOT_MIXED refinement sweeps cap (default 6)              */
-    double delta;     /* diagonal shift of the delta-regularised MOT,
-                         Z_n + delta I (Sec. II; the paper uses 0).  Only 0 is
-                         supported (MOT_EUNSUPPORTED otherwise)                   */
+    double delta;     /* diagonal shift of the delta-regularised MOT (Sec. II,
+                         Z^delta_n = Z_n + delta_n I): here delta_0 = delta for the
+                         present-time matrix (every Z0 product and the solve) and
+                         delta_n = 0 for the history lags n >= 1.  The paper uses
+                         0 (the default); any finite value is accepted           */
     int timing;       /* 1: time the history z-pass and the Z0 spectral z-pass
                          kernels of every step with CUDA events (fills
                          ms_zhist / ms_zgreen of mot_step_stats; adds event

@@ -275,9 +275,13 @@ def assemble_Zk(k, N, eps, R, g, dense: bool = False):
 
 # ---------------------------------------------------------------- the march (Eq. 3)
 class Problem:
-    """Geometry, permittivity, time step and the lag tables of one MOT-JVIE problem."""
+    """Geometry, permittivity, time step and the lag tables of one MOT-JVIE problem.
 
-    def __init__(self, N, h, eps, alpha, tables=None):
+    delta: the diagonal shift of the delta-regularised MOT (Sec. II, Z^delta_n =
+    Z_n + delta_n I), applied to the present-time matrix only (delta_0 = delta,
+    delta_n = 0 for n >= 1); the paper uses 0."""
+
+    def __init__(self, N, h, eps, alpha, tables=None, delta=0.0):
         self.N = tuple(int(v) for v in N)
         self.h = float(h)
         self.eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(self.N[2], self.N[1], self.N[0])
@@ -286,11 +290,15 @@ class Problem:
         self.dt = alpha * dt_cfl(h)
         self.ell = history_length(self.N, self.rho)
         self.tables = tables if tables is not None else lag_tables(self.N, self.rho, self.ell)
+        self.delta = float(delta)
         self._lu = None
 
     def apply(self, k, x):
         R, g = self.tables[k]
-        return Zk_apply(k, self.N, self.eps, R, g, x)
+        y = Zk_apply(k, self.N, self.eps, R, g, x)
+        if k == 0 and self.delta != 0.0:
+            y = y + self.delta * np.asarray(x, dtype=np.float64).reshape(y.shape)
+        return y
 
     def solve_Z0(self, b):
         """J = Z0^-1 b exactly (up to rounding): dense LU with partial pivoting
@@ -302,6 +310,10 @@ class Problem:
         if self._lu is None:
             R, g = self.tables[0]
             Z = assemble_Zk(0, self.N, self.eps, R, g)
+            if self.delta != 0.0:
+                import scipy.sparse as sp
+
+                Z = (Z + self.delta * sp.identity(Z.shape[0], format="csc")).tocsc()
             if Z.shape[0] <= 12288:
                 self._lu = ("dense", sla.lu_factor(Z.toarray(), check_finite=False))
             else:

@@ -1178,7 +1178,7 @@ mot_status tune_product(mot_problem *p, int nrhs, Sched &best, mot_schedule &inf
     p->capturing = true;  // no kernel-timing events while tuning
     auto run = [&](const Sched &s, T *out) -> mot_status {
         SchedScope sc(&s);
-        EpiZ0<T, T> e = {(const T *)x.p, out, eps_of<T>(p), pr, p->N[0]};
+        EpiZ0<T, T> e = {(const T *)x.p, out, eps_of<T>(p), pr, p->N[0], (T)p->opt.delta};
         return z0_product<T, T>(p, (const T *)x.p, nrhs, wa.p, wb.p, e, st);
     };
     int reps = 3;
@@ -1677,7 +1677,7 @@ template <typename T> mot_status z0_direct(mot_problem *p, const T *x, T *y, int
         count_launch();
         k_z0_direct_g<T><<<dim3((unsigned)std::min<long>((nv + 255) / 256, 16L * p->ctx->sms), nrhs), 256, 0, st>>>(
             x, y, eps_of<T>(p), (const int4 *)p->direct.d.p, (const T *)p->direct.g.p, p->direct.nd, p->N[0],
-            p->N[1], p->N[2]);
+            p->N[1], p->N[2], (T)p->opt.delta);
         MOT_CHECK_LAUNCH();
         return MOT_OK;
     }
@@ -1689,7 +1689,7 @@ template <typename T> mot_status z0_direct(mot_problem *p, const T *x, T *y, int
     count_launch();
     k_z0_direct<T><<<dim3(tiles, nrhs), dim3(t[0], t[1], t[2]), smem, st>>>(
         x, y, eps_of<T>(p), (const int4 *)p->direct.d.p, (const T *)p->direct.g.p, p->direct.nd, R[0], R[1], R[2],
-        p->N[0], p->N[1], p->N[2]);
+        p->N[0], p->N[1], p->N[2], (T)p->opt.delta);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
@@ -1788,7 +1788,7 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
     mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 0, 1, 1};
     if (opt) o = *opt;
-    if (o.delta != 0.0) MOT_FAIL(MOT_EUNSUPPORTED, "delta-regularisation (delta != 0) is not supported");
+    if (!std::isfinite(o.delta)) MOT_FAIL(MOT_EINVAL, "delta must be finite");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
     if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
     if (o.graph < 0 || o.graph > 2) MOT_FAIL(MOT_EINVAL, "graph must be 0, 1 or 2");
@@ -1909,12 +1909,14 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
     if (dtype == MOT_F64) {
         MOT_TRY(schedule_for<double>(p, nrhs, &sc));
         SchedScope scope(sc);
-        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0],
+                                   p->opt.delta};
         return z0_product<double, double>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
     }
     MOT_TRY(schedule_for<float>(p, nrhs, &sc));
     SchedScope scope(sc);
-    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
+    EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0],
+                             (float)p->opt.delta};
     return z0_product<float, float>(p, (const float *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
 }
 
@@ -2017,7 +2019,7 @@ template <typename V> KrylovView<V> kview(mot_run *r) {
 
 template <typename V> mot_status mvp(mot_run *r, const V *x, V *y, cudaStream_t st) {
     mot_problem *p = r->p;
-    EpiZ0<V, V> e = {x, y, eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0]};
+    EpiZ0<V, V> e = {x, y, eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0], (V)p->opt.delta};
     return z0_product<V, V>(p, x, r->B, p->wsA.p, p->wsB.p, e, st);
 }
 
@@ -2050,7 +2052,7 @@ template <typename V> mot_status mvp_y1(mot_run *r, cudaStream_t st) {
         return mvp<V>(r, k.v[kY1], k.v[kAY1], st);
     }
     SrcY1<V> src = {k.v[kY1], k.v[kW], k.v[kY2], k.sc, L};
-    EpiZ0<V, V> e = {k.v[kY1], k.v[kAY1], eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0]};
+    EpiZ0<V, V> e = {k.v[kY1], k.v[kAY1], eps_of<V>(p), (long)p->N[2] * p->N[1], p->N[0], (V)p->opt.delta};
     return z0_product_src<SrcY1<V>, V, V>(p, src, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, e, st);
 }
 
@@ -2069,11 +2071,12 @@ mot_status tfqmr_body(mot_run *r, V *x, cudaStream_t st, cudaGraphConditionalHan
         const int P = 3 * p->N[2];
         const V *eps = eps_of<V>(p);
         SrcHalfA<V> sa = {x, k.v[kW], k.v[kD], k.v[kY2], k.v[kY1], k.v[kAY1], k.v[kV], k.sc, L, k.p1, P, ctr};
-        EpiHalfB<V> eb = {k.v[kY2], k.v[kAY2], eps, x, k.v[kW], k.v[kD], k.v[kRS], k.sc, k.p1, k.p2, P, ctr + 1};
+        EpiHalfB<V> eb = {k.v[kY2], k.v[kAY2], eps, x, k.v[kW], k.v[kD], k.v[kRS], k.sc, k.p1, k.p2, P, ctr + 1,
+                          (V)p->opt.delta};
         MOT_TRY((z0_product_src<SrcHalfA<V>, V, V>(p, sa, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, eb, st)));
         SrcY1<V> s1 = {k.v[kY1], k.v[kW], k.v[kY2], k.sc, L};
         EpiV<V> ev = {k.v[kY1], k.v[kAY1], eps, k.v[kV], k.v[kAY2], k.v[kRS], k.sc, k.p3, P, ctr + 2,
-                      (int *)r->ctl.p, h, use_h};
+                      (int *)r->ctl.p, h, use_h, 0, (V)p->opt.delta};
         MOT_TRY((z0_product_src<SrcY1<V>, V, V>(p, s1, (const V *)nullptr, r->B, p->wsA.p, p->wsB.p, ev, st)));
         return MOT_OK;
     }
@@ -2176,7 +2179,7 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
                                                                  L, k.p1, k.sc, tol, stag, ctr + 3);
         MOT_CHECK_LAUNCH();
         EpiV<V> ev = {k.v[kY1], k.v[kAY1], eps_of<V>(p), k.v[kV], k.v[kAY2], k.v[kRS], k.sc, k.p3, 3 * p->N[2],
-                      ctr + 2, (int *)r->ctl.p, cudaGraphConditionalHandle{}, 0, 1};
+                      ctr + 2, (int *)r->ctl.p, cudaGraphConditionalHandle{}, 0, 1, (V)p->opt.delta};
         return z0_product<V, V>(p, (const V *)k.v[kY1], B, p->wsA.p, p->wsB.p, ev, st);
     }
     if (zero_x0) {
@@ -2570,7 +2573,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         conv = c;
         sweeps = 1;
         EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p, (const double *)p->eps.p, pr,
-                         p->N[0]};
+                         p->N[0], p->opt.delta};
         MOT_TRY((z0_product<double, double>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
         ++mvps;
         MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
@@ -2580,7 +2583,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         float *c32 = r32 + n;
         for (sweeps = 0; sweeps <= p->opt.max_refine; ++sweeps) {
             EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
-                             (const double *)p->eps.p, pr, p->N[0]};
+                             (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
             MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
             ++mvps;
             MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
@@ -2871,7 +2874,7 @@ mot_status build_step_graph(mot_run *r) {
             MOT_TRY(tfqmr_capture<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, st,
                                           r->cap2, 1));
             EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
-                             (const double *)p->eps.p, pr, p->N[0]};
+                             (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
             MOT_TRY((z0_product<double, double>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
             MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, st));
             count_launch();
@@ -2883,7 +2886,7 @@ mot_status build_step_graph(mot_run *r) {
             float *r32 = (float *)r->r32.p;
             float *c32 = r32 + n;
             EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
-                             (const double *)p->eps.p, pr, p->N[0]};
+                             (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
             // residual of the initial guess, then sweeps while it misses tol
             MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
             MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, st));
@@ -3497,10 +3500,12 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
     SchedScope scope(p->sched_for(nrhs, dtype == MOT_F32));
     mot_status st;
     if (dtype == MOT_F64) {
-        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0]};
+        EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0],
+                                   p->opt.delta};
         st = z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
     } else {
-        EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0]};
+        EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0],
+                             (float)p->opt.delta};
         st = z0_product<float, float>(p, (const float *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
     }
     p->capturing = was;

@@ -5,6 +5,8 @@
 //
 //   (Z0 x)_p(m) = eps(m) T(0) x_p(m) - (eps(m) - 1) sum_d sum_q g0(d)_pq x_q(m - d)   (Eq. 10, 12)
 //
+// (+ delta x_p(m) for the regularised Z0 + delta I, Sec. II; delta = 0 in the paper)
+//
 // with x = 0 outside the grid.  The offsets d with a nonzero entry (the causal
 // support of lag 0, |d_i| <= R_i) come as a list with their six table values
 // (xx yy zz xy xz yz), signs of the mixed entries already applied.  One CTA per
@@ -22,7 +24,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_z0_direct(const T *__restrict__ x, T *__restrict__ y,
                                                    const T *__restrict__ eps, const int4 *__restrict__ dlist,
                                                    const T *__restrict__ gval, int nd, int Rx, int Ry, int Rz,
-                                                   int Nx, int Ny, int Nz) {
+                                                   int Nx, int Ny, int Nz, T dl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
     const int TX = blockDim.x, TY = blockDim.y, TZ = blockDim.z;
@@ -63,9 +65,10 @@ __global__ void __launch_bounds__(512) k_z0_direct(const T *__restrict__ x, T *_
     const long m = ((long)oz * Ny + oy) * Nx + ox;
     const T e = eps[m];
     T *yb = y + (long)b * 3 * nv;
-    yb[m] = e * T(0.5) * tile[c0] - (e - T(1)) * g0;
-    yb[nv + m] = e * T(0.5) * tile[sn + c0] - (e - T(1)) * g1;
-    yb[2 * nv + m] = e * T(0.5) * tile[2 * sn + c0] - (e - T(1)) * g2;
+    const T dg = e * T(0.5) + dl;  // the diagonal D (+ delta of Z0 + delta I)
+    yb[m] = dg * tile[c0] - (e - T(1)) * g0;
+    yb[nv + m] = dg * tile[sn + c0] - (e - T(1)) * g1;
+    yb[2 * nv + m] = dg * tile[2 * sn + c0] - (e - T(1)) * g2;
 }
 
 // the same sum without staging, for reaches whose haloed tile does not fit in
@@ -74,7 +77,8 @@ __global__ void __launch_bounds__(512) k_z0_direct(const T *__restrict__ x, T *_
 template <typename T>
 __global__ void __launch_bounds__(256) k_z0_direct_g(const T *__restrict__ x, T *__restrict__ y,
                                                      const T *__restrict__ eps, const int4 *__restrict__ dlist,
-                                                     const T *__restrict__ gval, int nd, int Nx, int Ny, int Nz) {
+                                                     const T *__restrict__ gval, int nd, int Nx, int Ny, int Nz,
+                                                     T dl) {
     const long nv = (long)Nx * Ny * Nz;
     const int b = blockIdx.y;
     const T *xb = x + (long)b * 3 * nv;
@@ -94,9 +98,10 @@ __global__ void __launch_bounds__(256) k_z0_direct_g(const T *__restrict__ x, T 
         }
         const T e = eps[m];
         T *yb = y + (long)b * 3 * nv;
-        yb[m] = e * T(0.5) * xb[m] - (e - T(1)) * g0;
-        yb[nv + m] = e * T(0.5) * xb[nv + m] - (e - T(1)) * g1;
-        yb[2 * nv + m] = e * T(0.5) * xb[2 * nv + m] - (e - T(1)) * g2;
+        const T dg = e * T(0.5) + dl;
+        yb[m] = dg * xb[m] - (e - T(1)) * g0;
+        yb[nv + m] = dg * xb[nv + m] - (e - T(1)) * g1;
+        yb[2 * nv + m] = dg * xb[2 * nv + m] - (e - T(1)) * g2;
     }
 }
 

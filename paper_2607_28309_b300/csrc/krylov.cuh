@@ -581,6 +581,7 @@ template <typename V> struct EpiHalfB {
     double *part_w2, *part_rw;  // [B][P]
     int P;
     unsigned *ctr;
+    V dl = V(0);  // delta of Z0 + delta I
     struct Plane {
         const V *y2;
         V *Ay2;
@@ -590,9 +591,10 @@ template <typename V> struct EpiHalfB {
         V al, coef, ep;
         int pending, skip;
         typename AccOf<V>::type w2, rw;
+        V dl = V(0);
         __device__ __forceinline__ void operator()(int i, V g) {
             const V e = eps[i], yv = y2[i];
-            const V ay = e * V(0.5) * yv - (e - V(1)) * g;
+            const V ay = (e * V(0.5) + dl) * yv - (e - V(1)) * g;
             Ay2[i] = ay;
             if (skip) return;
             const V dold = d[i];
@@ -608,7 +610,7 @@ template <typename V> struct EpiHalfB {
             ldv<W>(e, eps + i);
             ldv<W>(yv, y2 + i);
 #pragma unroll
-            for (int k = 0; k < W; ++k) ay[k] = e[k] * V(0.5) * yv[k] - (e[k] - V(1)) * g[k];
+            for (int k = 0; k < W; ++k) ay[k] = (e[k] * V(0.5) + dl) * yv[k] - (e[k] - V(1)) * g[k];
             stv<W>(Ay2 + i, ay);
             if (skip) return;
             V dd[W], ww[W], rr[W], xx[W];
@@ -633,7 +635,7 @@ template <typename V> struct EpiHalfB {
         const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
         const TfqmrScal s = sc[(int)(plane / P)];
         Plane p{y2 + off, Ay2 + off, eps + zoff, x + off, w + off, d + off, rs + off, V(0), V(0), V(0),
-                s.pending, s.conv != 0, 0, 0};
+                s.pending, s.conv != 0, 0, 0, dl};
         if (!p.skip) {
             p.al = Coefs<V>::al(s);
             p.coef = Coefs<V>::coef(s);
@@ -686,6 +688,7 @@ template <typename V> struct EpiV {
     cudaGraphConditionalHandle h;
     int use_h;
     int start;  // the solve's first product: v = Ay1, alpha from (r*, v), no loop test
+    V dl = V(0);  // delta of Z0 + delta I
     struct Plane {
         const V *y1;
         V *Ay1;
@@ -696,9 +699,10 @@ template <typename V> struct EpiV {
         int skip;
         typename AccOf<V>::type acc;
         int start;
+        V dl = V(0);
         __device__ __forceinline__ void operator()(int i, V g) {
             const V e = eps[i];
-            const V ay = e * V(0.5) * y1[i] - (e - V(1)) * g;
+            const V ay = (e * V(0.5) + dl) * y1[i] - (e - V(1)) * g;
             Ay1[i] = ay;
             if (skip) return;
             const V vn = start ? ay : ay + be * (Ay2[i] + be * v[i]);
@@ -710,7 +714,7 @@ template <typename V> struct EpiV {
             ldv<W>(e, eps + i);
             ldv<W>(yv, y1 + i);
 #pragma unroll
-            for (int k = 0; k < W; ++k) ay[k] = e[k] * V(0.5) * yv[k] - (e[k] - V(1)) * g[k];
+            for (int k = 0; k < W; ++k) ay[k] = (e[k] * V(0.5) + dl) * yv[k] - (e[k] - V(1)) * g[k];
             stv<W>(Ay1 + i, ay);
             if (skip) return;
             V vv[W], rr[W];
@@ -733,7 +737,8 @@ template <typename V> struct EpiV {
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         const long off = plane * (long)NyNx, zoff = (plane % Nz) * (long)NyNx;
         const TfqmrScal s = sc[(int)(plane / P)];
-        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, Coefs<V>::be(s), s.conv != 0, 0, start};
+        return Plane{y1 + off, Ay1 + off, eps + zoff, v + off, Ay2 + off, rs + off, Coefs<V>::be(s), s.conv != 0, 0, start,
+                     dl};
     }
     __device__ __forceinline__ void finish(const Plane &pl, long plane) const {
         __shared__ int active;

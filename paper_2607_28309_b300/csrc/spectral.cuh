@@ -1591,19 +1591,21 @@ struct EpiZ0 {
     const TY *eps;
     long plane_rows;  // Nz * Ny
     int Nx;
+    TY dl = TY(0);  // delta of the regularised present-time matrix Z0 + delta I (0: the paper's)
     __device__ __forceinline__ void operator()(long row, int e, double g) const {
         long idx = row * Nx + e;
         long m = (row % plane_rows) * Nx + e;
         TY ep = eps[m];
-        y[idx] = ep * TY(0.5) * (TY)x[idx] - (ep - TY(1)) * (TY)g;
+        y[idx] = (ep * TY(0.5) + dl) * (TY)x[idx] - (ep - TY(1)) * (TY)g;
     }
     struct Plane {
         const TX *x;
         TY *y;
         const TY *eps;
+        TY dl = TY(0);
         __device__ __forceinline__ void operator()(int i, TY g) const {
             TY ep = eps[i];
-            y[i] = ep * TY(0.5) * (TY)x[i] - (ep - TY(1)) * g;
+            y[i] = (ep * TY(0.5) + dl) * (TY)x[i] - (ep - TY(1)) * g;
         }
         __device__ __forceinline__ void prefetch(int i) const {
             prefetch_l2(eps + i);
@@ -1615,7 +1617,7 @@ struct EpiZ0 {
             ldv<W>(e, eps + i);
             ldv<W>(xv, x + i);
 #pragma unroll
-            for (int k = 0; k < W; ++k) r[k] = e[k] * TY(0.5) * (TY)xv[k] - (e[k] - TY(1)) * g[k];
+            for (int k = 0; k < W; ++k) r[k] = (e[k] * TY(0.5) + dl) * (TY)xv[k] - (e[k] - TY(1)) * g[k];
             stv<W>(y + i, r);
         }
     };
@@ -1623,7 +1625,7 @@ struct EpiZ0 {
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         long off = plane * (long)NyNx;
         long zoff = (plane % Nz) * (long)NyNx;
-        return Plane{x + off, y + off, eps + zoff};
+        return Plane{x + off, y + off, eps + zoff, dl};
     }
     __device__ __forceinline__ void finish(const Plane &, long) const {}  // end-of-block hook
 };
@@ -1636,19 +1638,21 @@ struct EpiResidual {
     const double *eps;
     long plane_rows;
     int Nx;
+    double dl = 0.0;  // delta of Z0 + delta I
     __device__ __forceinline__ void operator()(long row, int e, double g) const {
         long idx = row * Nx + e;
         long m = (row % plane_rows) * Nx + e;
         double ep = eps[m];
-        r[idx] = b[idx] - (ep * 0.5 * x[idx] - (ep - 1.0) * g);
+        r[idx] = b[idx] - ((ep * 0.5 + dl) * x[idx] - (ep - 1.0) * g);
     }
     struct Plane {
         const double *x, *b;
         double *r;
         const double *eps;
+        double dl = 0.0;
         __device__ __forceinline__ void operator()(int i, double g) const {
             double ep = eps[i];
-            r[i] = b[i] - (ep * 0.5 * x[i] - (ep - 1.0) * g);
+            r[i] = b[i] - ((ep * 0.5 + dl) * x[i] - (ep - 1.0) * g);
         }
         __device__ __forceinline__ void prefetch(int i) const {
             prefetch_l2(eps + i);
@@ -1661,14 +1665,14 @@ struct EpiResidual {
             ldv<W>(xv, x + i);
             ldv<W>(bv, b + i);
 #pragma unroll
-            for (int k = 0; k < W; ++k) rv[k] = bv[k] - (e[k] * 0.5 * xv[k] - (e[k] - 1.0) * (double)g[k]);
+            for (int k = 0; k < W; ++k) rv[k] = bv[k] - ((e[k] * 0.5 + dl) * xv[k] - (e[k] - 1.0) * (double)g[k]);
             stv<W>(r + i, rv);
         }
     };
     __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
         long off = plane * (long)NyNx;
         long zoff = (plane % Nz) * (long)NyNx;
-        return Plane{x + off, b + off, r + off, eps + zoff};
+        return Plane{x + off, b + off, r + off, eps + zoff, dl};
     }
     __device__ __forceinline__ void finish(const Plane &, long) const {}
 };

@@ -51,6 +51,14 @@ def test_problem_rejects_bad_step_or_spacing(ctx, h, alpha):
     assert _status(mot.mot_problem_create, ctx, N, h, np.full(N[::-1], 2.0), alpha) == mot.MOT_EINVAL
 
 
+@pytest.mark.parametrize("delta", [float("nan"), float("inf")])
+def test_problem_rejects_non_finite_delta(ctx, delta):
+    N = (4, 3, 5)
+    opt = mot.default_options(delta=delta)
+    assert _status(mot.mot_problem_create, ctx, N, 10e-9, np.full(N[::-1], 2.0), 4.0, opt) == mot.MOT_EINVAL
+    assert "delta" in mot.mot_last_error()
+
+
 def test_run_rejects_bad_plane_waves(ctx):
     N = (5, 4, 3)
     prob = mot.mot_problem_create(ctx, N, 10e-9, np.full(N[::-1], 3.0), 4.0)

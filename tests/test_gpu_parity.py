@@ -263,3 +263,37 @@ def test_direct_product_matches_oracle(ctx, orc, N, alpha):
                 assert _rel(got, yf.double().cpu().numpy()) <= (1e-10 if dt == mot.MOT_F64 else 2e-5)
     finally:
         mot.mot_problem_destroy(prob)
+
+
+def test_delta_regularised_product_and_march(ctx, orc):
+    """The delta-regularised MOT (Sec. II; the shift on the present-time matrix
+    only): the FFT and direct Z0 products against the oracle's Z0 + delta I, and
+    the FP64 and mixed marches against the oracle's march with the same shift
+    (tolerances as for delta = 0)."""
+    N, alpha, delta, steps = (7, 6, 5), 4.0, 0.35, 24
+    eps = synthetic.block_eps(N, 2, 2.0, 5.0, 9)
+    P = orc.Problem(N, 10e-9, eps, alpha, delta=delta)
+    opt = mot.default_options(delta=delta)
+    prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha, opt)
+    try:
+        rng = np.random.default_rng(11)
+        x = rng.standard_normal((2, 3) + N[::-1])
+        ref = np.stack([P.apply(0, x[b]) for b in range(2)])
+        for dt, tdt, tol in ((mot.MOT_F64, torch.float64, 1e-10), (mot.MOT_F32, torch.float32, 1e-5)):
+            assert _rel(_apply(prob, x, 2, dt), ref) <= tol
+            xt = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", tdt)
+            yd = torch.empty_like(xt)
+            mot.mot_apply_Z0_direct(prob, xt, yd, 2, dt)
+            torch.cuda.synchronize()
+            assert _rel(yd.double().cpu().numpy(), ref) <= tol
+    finally:
+        mot.mot_problem_destroy(prob)
+    exc = [synthetic.pulse(steps, alpha)]
+    Jo = P.march(exc, steps)
+    e64 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64, opt), Jo)
+    assert e64.max() <= 1e-9, e64.max()
+    e32 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_MIXED, opt), Jo)
+    assert e32.max() <= 1e-5, e32.max()
+    # the shift is not dropped: the unshifted march differs
+    J0 = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
+    assert _mot_errors(J0, Jo).max() > 1e-3

@@ -144,3 +144,31 @@ def test_time_step_refinement_converges(orc):
     e42 = np.abs(traces[4] - traces[2]).max()
     e21 = np.abs(traces[2] - traces[1]).max()
     assert e84 > e42 > e21
+
+
+@pytest.mark.parametrize("alpha,delta", [(2.0, 0.3), (8.0, 0.05), (4.0, 5.0)])
+def test_delta_regularised_single_voxel_recursion(orc, alpha, delta):
+    """Sec. II's delta-regularised MOT with the shift on the present-time matrix
+    only (Z0 + delta I, no shift on the history lags): on one voxel the march is a
+    scalar recursion (Z_0 + delta) J_n = b_n - sum_k Z_k J_{n-k}, with Z_k =
+    eps T(k) - (eps - 1) g_k(0)_xx written out here from the temporal and kernel
+    entries, independently of the oracle's product and solve."""
+    h, eps, nsteps = 10e-9, 4.0, 60
+    pw = synthetic.pulse(nsteps, alpha, h)
+    P = orc.Problem((1, 1, 1), h, np.full((1, 1, 1), eps), alpha, delta=delta)
+    J = P.march([pw], nsteps)[:, 0, 0, 0, 0, 0]
+    rho = orc.rho_of_alpha(alpha)
+    Z = []
+    k = 0
+    while k < 2 or orc.in_support(k, rho, (0, 0, 0)):
+        Z.append(eps * orc.temporal(k) - (eps - 1) * orc.g_raw(k, rho, (0, 0, 0))[0])
+        k += 1
+    ref = np.zeros(nsteps)
+    for n in range(nsteps):
+        b = orc.incident((1, 1, 1), h, np.full((1, 1, 1), eps), pw, n * P.dt)[0, 0, 0, 0]
+        hist = sum(Z[k] * ref[n - k] for k in range(1, min(n, len(Z) - 1) + 1))
+        ref[n] = (b - hist) / (Z[0] + delta)
+    assert np.abs(J - ref).max() <= 1e-12 * np.abs(ref).max()
+    # the shift changes the answer (it is not silently dropped)
+    J0 = orc.Problem((1, 1, 1), h, np.full((1, 1, 1), eps), alpha).march([pw], nsteps)[:, 0, 0, 0, 0, 0]
+    assert np.abs(J - J0).max() > 1e-3 * np.abs(J0).max()
