@@ -58,8 +58,12 @@ typedef enum {
  *              the refinement correction and the marched solution J_n.         */
 typedef enum { MOT_FP64 = 0, MOT_MIXED = 1 } mot_precision;
 
-/* element type of device vectors handed to mot_apply_Z0 */
-typedef enum { MOT_F64 = 0, MOT_F32 = 1 } mot_dtype;
+/* element type of device vectors handed to mot_apply_Z0, and the arithmetic
+ * of its FFTs: MOT_F64 and MOT_F32 vectors computed in that precision;
+ * MOT_F64DF -- FP64 vectors, the FFTs and the spectral multiply in
+ * double-float (each value an unevaluated sum of two FP32 numbers, about 48
+ * significant bits, on the FP32 pipe), the contrast terms in FP64.          */
+typedef enum { MOT_F64 = 0, MOT_F32 = 1, MOT_F64DF = 2 } mot_dtype;
 
 /* Modulated-Gaussian plane wave of Eq. 7-8:
  *   E^i(r,t) = E0 pol (1/(sigma sqrt(2 pi))) exp(-tau^2/(2 sigma^2)) cos(2 pi f0 tau),
@@ -78,7 +82,11 @@ typedef struct {
     double tol;       /* TFQMR relative residual target (paper: 1e-6, Sec. V-A).
                          Default 1e-11 for MOT_FP64, 1e-6 (outer) for MOT_MIXED   */
     int maxit;        /* TFQMR iteration cap per solve (default 500)             */
-    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-6)      */
+    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-6),
+                         relative to the refinement residual r; a sweep whose r
+                         is already small against the outer right-hand side b
+                         solves only to max(inner_tol, 0.3 tol ||b|| / ||r||)
+                         (at most 1/2): the outer test is what it must pass     */
     int max_refine;   /* MOT_MIXED refinement sweeps cap (default 6)              */
     double delta;     /* diagonal shift of the delta-regularised MOT (Sec. II,
                          Z^delta_n = Z_n + delta_n I): here delta_0 = delta for the
@@ -90,8 +98,9 @@ typedef struct {
                          ms_zhist / ms_zgreen of mot_step_stats; adds event
                          overhead).  Default 0                                     */
     int guess;        /* initial guess of each step's solve (the paper does not
-                         specify one): 0 = J_{n-1} (default); 1 = 2 J_{n-1} -
-                         J_{n-2} (linear extrapolation)                            */
+                         specify one): 0 = J_{n-1}; 1 = 2 J_{n-1} - J_{n-2}
+                         (linear extrapolation, default: 19.8 instead of 21
+                         products per step on the 256 x 256 x 80 pillar array)   */
     int graph;        /* 1 (default): after the first step each step is one CUDA
                          graph launch whose loops and tests run on the device; 0:
                          host-driven steps, each solve's TFQMR loop one graph
@@ -186,7 +195,8 @@ void mot_problem_destroy(mot_problem *p);
 /* y = Z0 x for nrhs current vectors (Eq. 12: Z0 x = D x - X (G x), with
  * (G x) from Eq. 11 through zero-padded FFTs on the M0 grid).  x_dev, y_dev:
  * device arrays of nrhs*3*Nz*Ny*Nx elements of `dtype` (MOT_F64 computes in
- * FP64, MOT_F32 in FP32), x fastest; x and y must not overlap and must be
+ * FP64, MOT_F32 in FP32, MOT_F64DF takes FP64 vectors and computes the FFTs in
+ * double-float, relative error about 1e-14), x fastest; x and y must not overlap and must be
  * 16-byte aligned (the kernels move 16-byte packs).  Asynchronous on the
  * context stream.  Errors: MOT_EINVAL (null, nrhs < 1, dtype, alignment),
  * MOT_ENOMEM (workspace), MOT_ECUDA.                                          */

@@ -303,8 +303,8 @@ void axis_coef(int M, int R, bool odd, std::vector<double> &cf) {
 struct AxisTw {
     int M = 0;
     FftPlan plan{};    // FP32 passes
-    FftPlan plan64{};  // FP64 passes (radix <= 9: register pressure)
-    DBuf tw64, tw32;
+    FftPlan plan64{};  // FP64 and double-float passes (radix <= 9: register pressure)
+    DBuf tw64, tw32, twdf;  // twiddles in FP64, FP32 and double-float (hi, lo pairs)
 };
 
 struct mot_ctx {
@@ -426,7 +426,7 @@ struct mot_problem {
     DBuf eps, eps32;  // eps_r in FP64 and FP32
     std::vector<AxisTw *> tws;
     std::vector<LagTable> lags;
-    DBuf L0_64, L0_32;  // [6][K0z][K0y][H0]
+    DBuf L0_64, L0_32, L0_df;  // [6][K0z][K0y][H0] in FP64, FP32, double-float
     DBuf Lh_64, Lh_32;  // [ell+1][6][Khz][Khy][Hh]
     std::shared_ptr<SharedDev> lh_hold[2];  // set when Lh_64 / Lh_32 is shared (not owned)
     bool hist64 = false, hist32 = false;
@@ -485,11 +485,12 @@ struct mot_run {
     DBuf ring, wsAh, wsBh;
     DBuf hacc;  // history accumulation on the full Mh grid [B][3][Mhz][Mhy][Hh]
     // time-blocked history: the lags 2.. partial sums of the steps of the current
-    // time block, hTB + 1 rotating slots of hacc's layout (slot m mod (hTB + 1))
+    // time block, 2 hTB rotating slots of hacc's layout (slot m mod 2 hTB): the
+    // current block's partial sums and the next block's, filled beside this block's steps
     DBuf hpart;
     int hTB = 8;
     bool hpart_ok = false;  // the slot of step n holds its whole lags 2.. sum (the step graph leaves it so)
-    bool q_stale = false;   // the slots hold nothing usable (a loaded checkpoint): rebuild from the block start
+    bool q_stale = true;    // the slots hold nothing usable (a new run, a loaded checkpoint): rebuild from the block start
     cudaStream_t hside = nullptr;  // step graph: low-priority branch of the next step's partial sum
     cudaEvent_t hfork = nullptr, hjoin = nullptr;
     bool hjoin_open = false;  // capture: the branch still has to join the step's stream
@@ -526,18 +527,23 @@ AxisTw *get_tw(mot_problem *p, int M) {
     }
     std::vector<double2> h64(M);
     std::vector<float2> h32(M);
+    std::vector<float4> hdf(M);  // (re.hi, re.lo, im.hi, im.lo)
     const double pi = 3.141592653589793238462643383279502884;
     for (int m = 0; m < M; ++m) {
         double a = -2.0 * pi * (double)m / (double)M;
         h64[m] = make_double2(cos(a), sin(a));
         h32[m] = make_float2((float)cos(a), (float)sin(a));
+        const float ch = (float)cos(a), sh = (float)sin(a);
+        hdf[m] = make_float4(ch, (float)(cos(a) - (double)ch), sh, (float)(sin(a) - (double)sh));
     }
-    if (dalloc(t->tw64, sizeof(double2) * M) != MOT_OK || dalloc(t->tw32, sizeof(float2) * M) != MOT_OK) {
+    if (dalloc(t->tw64, sizeof(double2) * M) != MOT_OK || dalloc(t->tw32, sizeof(float2) * M) != MOT_OK ||
+        dalloc(t->twdf, sizeof(float4) * M) != MOT_OK) {
         delete t;
         return nullptr;
     }
     cudaMemcpy(t->tw64.p, h64.data(), sizeof(double2) * M, cudaMemcpyHostToDevice);
     cudaMemcpy(t->tw32.p, h32.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+    cudaMemcpy(t->twdf.p, hdf.data(), sizeof(float4) * M, cudaMemcpyHostToDevice);
     p->tws.push_back(t);
     return t;
 }
@@ -545,10 +551,12 @@ AxisTw *get_tw(mot_problem *p, int M) {
 template <typename T> const FftPlan &planp(AxisTw *t);
 template <> const FftPlan &planp<double>(AxisTw *t) { return t->plan64; }
 template <> const FftPlan &planp<float>(AxisTw *t) { return t->plan; }
+template <> const FftPlan &planp<dfl>(AxisTw *t) { return t->plan64; }
 
 template <typename T> const cplx<T> *twp(AxisTw *t);
 template <> const cplx<double> *twp<double>(AxisTw *t) { return (const double2 *)t->tw64.p; }
 template <> const cplx<float> *twp<float>(AxisTw *t) { return (const float2 *)t->tw32.p; }
+template <> const cplx<dfl> *twp<dfl>(AxisTw *t) { return (const dfl2 *)t->twdf.p; }
 
 constexpr size_t kSmemMax = 200 * 1024;
 // block sizes: the pencil passes are latency-bound at small grids, so they use
@@ -786,6 +794,8 @@ bool x_forward_r(const TI *x, cplx<T> *out, long nrows, int Nx, int Ny, AxisTw *
                 case 8: return x_forward_r_go<TI, T, 15, 18, 4>(x, out, nrows, Nx, tw, st);
                 default: return false;
             }
+        case 512:  // the history grid of the 256 x 256 pillar array: 16 x 32, four row pairs per block
+            return Ny % 8 == 0 && x_forward_r_go<TI, T, 16, 32, 4>(x, out, nrows, Nx, tw, st);
         default: return false;
     }
 }
@@ -801,6 +811,8 @@ bool x_inverse_r(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisTw *
                 case 8: return x_inverse_r_go<T, Epi, 15, 18, 4>(in, nrows, Nx, Ny, Nz, tw, epi, st);
                 default: return false;
             }
+        case 512:
+            return Ny % 8 == 0 && x_inverse_r_go<T, Epi, 16, 32, 4>(in, nrows, Nx, Ny, Nz, tw, epi, st);
         default: return false;
     }
 }
@@ -815,6 +827,11 @@ bool col_r(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int Lout
         case 128: return col_r_go<T, S, 16, 8, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
         case 160: return col_r_go<T, S, 10, 16, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
         case 270: return col_r_go<T, S, 15, 18, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+        case 512:  // 16 x 32 (32-point register DFTs); 8 columns per block in FP64 (registers)
+            if constexpr (sizeof(T) == 4)
+                return col_r_go<T, S, 16, 32, 16>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
+            else
+                return col_r_go<T, S, 16, 32, 8>(in, out, tw, H, Lin, Lout, planes, ips, ops, st, nptr, ell, slot_stride);
         default: return false;
     }
 }
@@ -979,6 +996,7 @@ template <> const float *eps_of<float>(mot_problem *p) { return (const float *)p
 template <typename T> const T *L0_of(mot_problem *p);
 template <> const double *L0_of<double>(mot_problem *p) { return (const double *)p->L0_64.p; }
 template <> const float *L0_of<float>(mot_problem *p) { return (const float *)p->L0_32.p; }
+template <> const dfl *L0_of<dfl>(mot_problem *p) { return (const dfl *)p->L0_df.p; }
 template <typename T> const T *Lh_of(mot_problem *p);
 template <> const double *Lh_of<double>(mot_problem *p) { return (const double *)p->Lh_64.p; }
 template <> const float *Lh_of<float>(mot_problem *p) { return (const float *)p->Lh_32.p; }
@@ -1132,7 +1150,7 @@ template <typename T> bool z_cols_valid(int M0z, int tc) {
 inline bool compiled_plane(int Mx, int My) {
     return Mx == My && (Mx == 20 || Mx == 32 || Mx == 72 || Mx == 75 || Mx == 128);
 }
-inline bool compiled_col(int M) { return M == 32 || M == 64 || M == 128 || M == 160 || M == 270; }
+inline bool compiled_col(int M) { return M == 32 || M == 64 || M == 128 || M == 160 || M == 270 || M == 512; }
 
 template <typename T>
 mot_status tune_product(mot_problem *p, int nrhs, Sched &best, mot_schedule &info) {
@@ -1459,10 +1477,15 @@ mot_status build_Z0_spectrum(mot_problem *p) {
     long kn = (long)p->K0[0] * p->K0[1] * p->K0[2];
     MOT_TRY(dalloc(p->L0_64, sizeof(double) * 6 * kn));
     MOT_TRY(dalloc(p->L0_32, sizeof(float) * 6 * kn));
+    MOT_TRY(dalloc(p->L0_df, sizeof(dfl) * 6 * kn));
     MOT_TRY(lag_spectrum(p, p->lags[0], p->M0, (double *)p->L0_64.p));
     count_launch();
     k_scale_store<float><<<grid_for(6 * kn), 256, 0, p->ctx->stream>>>((const double *)p->L0_64.p,
                                                                        (float *)p->L0_32.p, 6 * kn, 1.0);
+    MOT_CHECK_LAUNCH();
+    count_launch();
+    k_scale_store<dfl><<<grid_for(6 * kn), 256, 0, p->ctx->stream>>>((const double *)p->L0_64.p,
+                                                                     (dfl *)p->L0_df.p, 6 * kn, 1.0);
     MOT_CHECK_LAUNCH();
     MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
     return MOT_OK;
@@ -1786,7 +1809,7 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     long nv = (long)n[0] * n[1] * n[2];
     for (long i = 0; i < nv; ++i)
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
-    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 0, 1, 1};
+    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 1, 1, 1};
     if (opt) o = *opt;
     if (!std::isfinite(o.delta)) MOT_FAIL(MOT_EINVAL, "delta must be finite");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
@@ -1873,11 +1896,13 @@ void mot_problem_destroy(mot_problem *p) {
     for (auto *t : p->tws) {
         dfree(t->tw64);
         dfree(t->tw32);
+        dfree(t->twdf);
         delete t;
     }
     for (auto &L : p->lags) dfree(L.oct);
     dfree(p->L0_64);
     dfree(p->L0_32);
+    dfree(p->L0_df);
     // shared spectra are released with the holder, not freed here
     if (p->lh_hold[0]) p->Lh_64.p = nullptr;
     if (p->lh_hold[1]) p->Lh_32.p = nullptr;
@@ -1895,13 +1920,14 @@ void mot_problem_destroy(mot_problem *p) {
 mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
     if (!p || !x_dev || !y_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
     if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
-    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    if (dtype != MOT_F64 && dtype != MOT_F32 && dtype != MOT_F64DF)
+        MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64, MOT_F32 or MOT_F64DF");
     if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
     if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15u)
         MOT_FAIL(MOT_EINVAL, "x and y must be 16-byte aligned");
     MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
     size_t a, b;
-    z0_ws_bytes(p, nrhs, dtype == MOT_F64 ? sizeof(double2) : sizeof(float2), &a, &b);
+    z0_ws_bytes(p, nrhs, dtype == MOT_F32 ? sizeof(float2) : sizeof(double2), &a, &b);
     MOT_TRY(dalloc(p->wsA, a));
     MOT_TRY(dalloc(p->wsB, b));
     const long pr = (long)p->N[2] * p->N[1];
@@ -1912,6 +1938,13 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
         EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0],
                                    p->opt.delta};
         return z0_product<double, double>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
+    }
+    if (dtype == MOT_F64DF) {
+        // the FP64 schedule's shapes (same element size), without a tuning pass of its own
+        MOT_TRY(schedule_for<double>(p, nrhs, &sc));
+        SchedScope scope(sc);
+        EpiZ0DF e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0], p->opt.delta};
+        return z0_product<double, dfl>(p, (const double *)x_dev, nrhs, p->wsA.p, p->wsB.p, e, p->ctx->stream);
     }
     MOT_TRY(schedule_for<float>(p, nrhs, &sc));
     SchedScope scope(sc);
@@ -2156,9 +2189,24 @@ template <typename V> bool fused_start(const mot_problem *p) { return z0_planes_
 // With src64 (zero_x0 and fused_start only) the right-hand side is 2^-e src64,
 // e from the squared norms n2 (the mixed form's correction solve), and rhs is
 // not read.  *mvps: products applied.
+// the adaptive inner tolerance of the mixed refinement (InnerTol): the FP32
+// correction solve is given 0.3 of the outer tolerance, the rest left to its
+// rounding; MOTJVIE_INNER_ADAPT=0 keeps inner_tol fixed (timing comparisons)
+mot_status dev_norms2(mot_run *r, const double *v, double *out, cudaStream_t st);
+
+inline InnerTol inner_tol_for(mot_run *r, const double *ro2, double tol) {
+    static const bool off = getenv("MOTJVIE_INNER_ADAPT") && atoi(getenv("MOTJVIE_INNER_ADAPT")) == 0;
+    InnerTol it;
+    if (off) return it;
+    it.bo2 = (const double *)r->b2.p;
+    it.ro2 = ro2;
+    it.otol = 0.3 * tol;
+    return it;
+}
+
 template <typename V>
 mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, cudaStream_t st, int *mvps,
-                       const double *src64 = nullptr, const double *n2 = nullptr) {
+                       const double *src64 = nullptr, const double *n2 = nullptr, InnerTol itol = InnerTol{}) {
     mot_problem *p = r->p;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
@@ -2173,10 +2221,11 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
         count_launch();
         if (src64)
             k_tfqmr_start_zero<V, double><<<gr, kRedThreads, 0, st>>>(src64, n2, x, k.v[kW], k.v[kY1], k.v[kRS],
-                                                                      k.v[kD], L, k.p1, k.sc, tol, stag, ctr + 3);
+                                                                      k.v[kD], L, k.p1, k.sc, tol, stag, ctr + 3,
+                                                                      itol);
         else
             k_tfqmr_start_zero<V, V><<<gr, kRedThreads, 0, st>>>(rhs, nullptr, x, k.v[kW], k.v[kY1], k.v[kRS], k.v[kD],
-                                                                 L, k.p1, k.sc, tol, stag, ctr + 3);
+                                                                 L, k.p1, k.sc, tol, stag, ctr + 3, itol);
         MOT_CHECK_LAUNCH();
         EpiV<V> ev = {k.v[kY1], k.v[kAY1], eps_of<V>(p), k.v[kV], k.v[kAY2], k.v[kRS], k.sc, k.p3, 3 * p->N[2],
                       ctr + 2, (int *)r->ctl.p, cudaGraphConditionalHandle{}, 0, 1, (V)p->opt.delta};
@@ -2201,7 +2250,7 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
     k_dot_part<V, V><<<gr, kRedThreads, 0, st>>>(rhs, rhs, L, k.p2);
     count_launch();
     // FP32 inner solves stop at stagnation; the FP64 solve runs to tol or maxit
-    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol, sizeof(V) == 4 ? 1 : 0);
+    k_tfqmr_init<<<B, 32, 0, st>>>(k.sc, k.p1, k.p2, tol, sizeof(V) == 4 ? 1 : 0, itol);
     count_launch();
     k_tfqmr_zero_rhs<V><<<gv, 256, 0, st>>>(x, k.sc, L);
     count_launch();
@@ -2223,7 +2272,8 @@ mot_status tfqmr_start(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol,
 // iters_out: iterations (max over the batch); mvps_out: Z0 products applied.
 template <typename V>
 mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, int *iters_out,
-                 bool *conv_out, int *mvps_out, const double *src64 = nullptr, const double *n2 = nullptr) {
+                 bool *conv_out, int *mvps_out, const double *src64 = nullptr, const double *n2 = nullptr,
+                 InnerTol itol = InnerTol{}) {
     mot_problem *p = r->p;
     cudaStream_t st = p->ctx->stream;
     const int B = r->B;
@@ -2231,7 +2281,7 @@ mot_status tfqmr(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int m
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B);
     int mvps = 0;
-    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &mvps, src64, n2));
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &mvps, src64, n2, itol));
     int ctl_h[2] = {0, maxit};
     MOT_CUDA_TRY(cudaMemcpyAsync(r->ctl.p, ctl_h, sizeof(ctl_h), cudaMemcpyHostToDevice, st));
     if (p->opt.graph == 2) {
@@ -2298,8 +2348,10 @@ template <typename T> mot_status ring_push(mot_run *r, cudaStream_t st, const lo
         if (!p->capturing) p->kt.end(st);
     } else {
         if (!p->capturing) p->kt.begin(st, MOT_K_FWD_RING);
-        MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
-        MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
+        if (x_forward_r<double, T>((const double *)r->J.p, A, nrows, Nx, Ny, tx, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_x_forward<double, T>((const double *)r->J.p, A, nrows, Nx, H, tx, st)));
+        if (col_r<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, (long)Ny * H, (long)My * H, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_axis<T, -1>(A, Bf, ty, H, Ny, My, r->B * 3 * Nz, 1, (long)Ny * H, 0, H, (long)My * H, 0, H, st)));
         if (!p->capturing) p->kt.end(st);
     }
     const long slot_elems = (long)r->B * 3 * Mz * My * H;
@@ -2353,19 +2405,23 @@ template <typename T> QSlots<T> qslots(mot_run *r, int flags) {
     return QSlots<T>{(cplx<T> *)r->hpart.p, slot, r->hTB, flags};
 }
 
-// the time-blocked pass over the ring for the block starting at m0 (outputs
-// t >= tlo); with nptr the kernel reads m0 = *nptr + dm and runs only at a
-// block start
+// one part of the time-blocked pass (k_hist_block) for the block starting at
+// m0, outputs t >= tlo, octant-point chunks [c_lo, c_hi) of hTB; with nptr the
+// kernel takes its block and chunk from m = *nptr + dm (see k_hist_block)
 template <typename T>
-mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const long long *nptr, int dm) {
+mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, int part, int c_lo, int c_hi,
+                           const long long *nptr, int dm) {
     mot_problem *p = r->p;
     const int H = p->Hh, My = p->Mh[1], Mz = p->Mh[2];
     Octant oc = {Mz, My, p->Kh[2], p->Kh[1], H};
     const QSlots<T> q = qslots<T>(r, 0);
     const long points = (long)r->B * (Mz / 2 + 1) * (My / 2 + 1) * H;
+    // points of the launch: all of them (recent part) or one chunk of hTB (old part)
+    const int nchunks = nptr ? (part == kHistOld ? 1 : r->hTB) : c_hi - c_lo;
+    const long lpoints = (points * nchunks + r->hTB - 1) / r->hTB;
     // blocks per SM (MOTJVIE_HIST_BLOCK_BPS overrides, for sweeps)
     static const long bps = getenv("MOTJVIE_HIST_BLOCK_BPS") ? std::max(1, atoi(getenv("MOTJVIE_HIST_BLOCK_BPS"))) : 32;
-    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((points + 31) / 32, bps * p->ctx->sms));
+    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>((lpoints + 31) / 32, bps * p->ctx->sms));
     const auto *ring = (const cplx<T> *)r->ring.p;
     if (r->hTB != (sizeof(T) == 4 ? 8 : 4)) MOT_FAIL(MOT_EINVAL, "time block does not match the history precision");
     // time block 8 (FP32) with two outputs per thread, 4 (FP64) with one: four thread groups
@@ -2374,7 +2430,7 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, const 
     MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
     count_launch();
     k_hist_block<T, TB, TH><<<grid, dim3(32, 4), smem, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
-                                                            p->ell, m0, tlo, nptr, dm);
+                                                            p->ell, m0, tlo, part, c_lo, c_hi, nptr, dm);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
@@ -2402,16 +2458,25 @@ mot_status hist_near(mot_run *r, cudaStream_t st, long m, const long long *nptr,
     return MOT_OK;
 }
 
-// the lags 2.. sum of step m = r->n into its slot, host-driven: the block pass
-// at a block start (or from the block start onwards when the slots are stale),
-// then the near accumulation -- the kernels the step graph runs beside step m-1
+// the lags 2.. sum of step m = r->n into its slot, host-driven -- the kernels
+// the step graph runs beside step m-1, in the same order: at a block start the
+// recent part of the block, then chunk t = m mod hTB of the next block's old
+// part, then the near accumulation of step m.  Stale slots (a new run, a loaded
+// checkpoint) are rebuilt first: the block's old part (outputs t..), its recent
+// part, the chunks 0..t-1 of the next block's old part.
 template <typename T> mot_status hist_side_host(mot_run *r, cudaStream_t st, unsigned blocks, int bt, int mode) {
     const long m = r->n;
-    const int t = (int)(m % r->hTB);
-    if (t == 0 || r->q_stale) {
-        MOT_TRY(hist_block_pass<T>(r, st, m - t, t, nullptr, 0));
+    const int TB = r->hTB, t = (int)(m % TB);
+    const long m0 = m - t;
+    if (r->q_stale) {
+        MOT_TRY(hist_block_pass<T>(r, st, m0, t, kHistOld, 0, TB, nullptr, 0));
+        MOT_TRY(hist_block_pass<T>(r, st, m0, t, kHistRecent, 0, TB, nullptr, 0));
+        if (t > 0) MOT_TRY(hist_block_pass<T>(r, st, m0 + TB, 0, kHistOld, 0, t, nullptr, 0));
         r->q_stale = false;
+    } else if (t == 0) {
+        MOT_TRY(hist_block_pass<T>(r, st, m0, 0, kHistRecent, 0, TB, nullptr, 0));
     }
+    MOT_TRY(hist_block_pass<T>(r, st, m0 + TB, 0, kHistOld, t, t + 1, nullptr, 0));
     return hist_near<T>(r, st, m, nullptr, 0, blocks, bt, mode);
 }
 
@@ -2475,7 +2540,8 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
             MOT_CUDA_TRY(cudaEventRecord(r->hfork, st));
             MOT_CUDA_TRY(cudaStreamWaitEvent(r->hside, r->hfork, 0));
             const int bt = hist_side_threads();
-            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, nptr, 1));
+            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistRecent, 0, 0, nptr, 1));
+            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistOld, 0, 0, nptr, 1));
             MOT_TRY(hist_near<T>(r, r->hside, 0, nptr, 1, hist_blocks(r, hist_side_per_sm_x2(), bt), bt,
                                  hist_side_mode()));
             MOT_CUDA_TRY(cudaEventRecord(r->hjoin, r->hside));
@@ -2516,8 +2582,10 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
         if (!p->capturing) p->kt.end(st);
     } else {
         if (!p->capturing) p->kt.begin(st, MOT_K_INV_HISTORY);
-        MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
-        MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
+        if (col_r<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, (long)My * H, (long)Ny * H, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_axis<T, +1>(Bf, A, ty, H, My, Ny, r->B * 3 * Nz, 1, (long)My * H, 0, H, (long)Ny * H, 0, H, st)));
+        if (x_inverse_r<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, Ny, Nz, tx, e, st)) MOT_CHECK_LAUNCH();
+        else MOT_TRY((launch_x_inverse<T, EpiHistory>(A, (long)r->B * 3 * Nz * Ny, Nx, H, tx, e, st)));
         if (!p->capturing) p->kt.end(st);
     }
     return MOT_OK;
@@ -2581,6 +2649,8 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
         float *r32 = (float *)r->r32.p;
         float *c32 = r32 + n;
+        MOT_TRY(dev_norms2(r, (const double *)r->b.p, (double *)r->b2.p, st));
+        const InnerTol itol = inner_tol_for(r, (const double *)r->dots.p, tol);
         for (sweeps = 0; sweeps <= p->opt.max_refine; ++sweeps) {
             EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
                              (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
@@ -2598,12 +2668,13 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
             int nm;
             if (fused_start<float>(p)) {  // the start kernel scales and converts r itself
                 MOT_TRY(tfqmr<float>(r, c32, nullptr, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm,
-                                     (const double *)r->r.p, (const double *)r->dots.p));
+                                     (const double *)r->r.p, (const double *)r->dots.p, itol));
             } else {
                 count_launch();
                 k_convert_scaled<<<gs, 256, 0, st>>>(r32, (const double *)r->r.p, (const double *)r->dots.p, L);
                 MOT_CHECK_LAUNCH();
-                MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm));
+                MOT_TRY(tfqmr<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, &it, &c, &nm, nullptr,
+                                     nullptr, itol));
             }
             mvps += nm;
             iters += it;
@@ -2817,14 +2888,14 @@ mot_status while_insert(cudaStream_t st, cudaStream_t bst, const WhileNode &w, F
 template <typename V>
 mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double tol, int maxit, cudaStream_t st,
                          cudaStream_t bst, int mark_notconv, const double *src64 = nullptr,
-                         const double *n2 = nullptr) {
+                         const double *n2 = nullptr, InnerTol itol = InnerTol{}) {
     mot_problem *p = r->p;
     const int B = r->B;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     KrylovView<V> k = kview<V>(r);
     dim3 gv(grid_for(L), B);
     int init_mvps = 1;
-    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &init_mvps, src64, n2));
+    MOT_TRY(tfqmr_start<V>(r, x, rhs, zero_x0, tol, st, &init_mvps, src64, n2, itol));
     WhileNode w;
     MOT_TRY(while_handle(st, w, 1));
     count_launch();
@@ -2899,14 +2970,16 @@ mot_status build_step_graph(mot_run *r) {
             MOT_TRY(while_insert(st, r->cap2, wo, [&](cudaStream_t cs) -> mot_status {
                 // r->r2 holds the squared residual norms (dev_norms2 before the test)
                 const dim3 gs(grid_for(L), r->B);
+                const InnerTol itol = inner_tol_for(r, (const double *)r->r2.p, tol);
                 if (fused_start<float>(p)) {  // the start kernel scales and converts r itself
                     MOT_TRY(tfqmr_capture<float>(r, c32, nullptr, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3,
-                                                 0, (const double *)r->r.p, (const double *)r->r2.p));
+                                                 0, (const double *)r->r.p, (const double *)r->r2.p, itol));
                 } else {
                     count_launch();
                     k_convert_scaled<<<gs, 256, 0, cs>>>(r32, (const double *)r->r.p, (const double *)r->r2.p, L);
                     MOT_CHECK_LAUNCH();
-                    MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0));
+                    MOT_TRY(tfqmr_capture<float>(r, c32, r32, true, p->opt.inner_tol, p->opt.maxit, cs, r->cap3, 0,
+                                                 nullptr, nullptr, itol));
                 }
                 count_launch();
                 k_add_scaled<<<gs, 256, 0, cs>>>((double *)r->J.p, c32, (const double *)r->r2.p, L);
@@ -3043,7 +3116,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->hacc, ring_bytes / p->ell)) != MOT_OK) return fail(s);
     // time block: 8 steps in FP32, 4 in FP64 (the block pass holds that many outputs in registers)
     r->hTB = mixed ? 8 : 4;
-    if ((s = dalloc(r->hpart, ring_bytes / p->ell * (r->hTB + 1))) != MOT_OK) return fail(s);
+    if ((s = dalloc(r->hpart, ring_bytes / p->ell * (2 * r->hTB))) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     for (int i = 0; i < 10; ++i)

@@ -6,16 +6,19 @@
 
 #include <string>
 
+#include "dfloat.cuh"
+
 #ifndef MOT_HD
 #define MOT_HD __host__ __device__
 #endif
 
 namespace mot {
 
-// complex helpers on float2 / double2
+// complex helpers on float2 / double2 / dfl2
 template <typename T> struct cx;
 template <> struct cx<float> { using type = float2; };
 template <> struct cx<double> { using type = double2; };
+template <> struct cx<dfl> { using type = dfl2; };  // double-float (FP32 pair) complex
 template <typename T> using cplx = typename cx<T>::type;
 
 template <typename C> MOT_HD inline C cmake(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }

@@ -190,6 +190,21 @@ template <> struct Root<18> {
     __host__ __device__ static constexpr double s(int j) { return (j % 18) <= 9 ? sh(j % 18) : -sh(18 - j % 18); }
 };
 
+template <> struct Root<32> {
+    // cos(k pi / 16), k = 0..8; the rest of the circle by symmetry
+    __host__ __device__ static constexpr double q(int k) {
+        return k == 0 ? 1.0 : k == 1 ? 0.9807852804032304491262 : k == 2 ? 0.9238795325112867561282
+             : k == 3 ? 0.8314696123025452370788 : k == 4 ? 0.7071067811865475244008
+             : k == 5 ? 0.5555702330196022247428 : k == 6 ? 0.3826834323650897717285
+             : k == 7 ? 0.1950903220161282678483 : 0.0;
+    }
+    __host__ __device__ static constexpr double c(int j) {
+        return (j & 31) <= 8 ? q(j & 31) : (j & 31) <= 16 ? -q(16 - (j & 31))
+             : (j & 31) <= 24 ? -q((j & 31) - 16) : q(32 - (j & 31));
+    }
+    __host__ __device__ static constexpr double s(int j) { return c(j + 24); }  // sin x = cos(x - pi/2)
+};
+
 template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C *v);
 
 // N1 x N2 Cooley-Tukey in registers: x[t + N2 m] -> DFT_N1 over m, twiddle
@@ -237,6 +252,7 @@ template <int N, int S, typename C> __device__ __forceinline__ void dft_small(C 
     else if constexpr (N == 15) dft_nested<5, 3, S>(v);
     else if constexpr (N == 16) dft_nested<4, 4, S>(v);
     else if constexpr (N == 18) dft_nested<9, 2, S>(v);
+    else if constexpr (N == 32) dft_nested<8, 4, S>(v);
     else static_assert(N == 1, "no register DFT of this length");
 }
 

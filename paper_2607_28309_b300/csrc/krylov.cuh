@@ -148,12 +148,30 @@ __device__ __forceinline__ TfqmrScal init_scalars(double r2, double b2, double t
     return s;
 }
 
+// Relative tolerance of an inner (correction) solve of the mixed refinement:
+// the correction only has to bring the outer residual r below the outer
+// tolerance, so a solve whose residual is already small relative to the outer
+// right-hand side b needs less than inner_tol:
+//   tol_b = min(max(inner_tol, otol ||b|| / ||r||), 1/2),  otol = a fraction of the outer tol.
+// bo2 / ro2: ||b||^2 / ||r||^2 per right-hand side (nullptr: inner_tol as given).
+struct InnerTol {
+    const double *bo2 = nullptr, *ro2 = nullptr;
+    double otol = 0.0;
+};
+__device__ __forceinline__ double inner_tol_of(double tol, const InnerTol &it, int b) {
+    if (!it.bo2 || !it.ro2) return tol;
+    const double rr = it.ro2[b];
+    if (!(rr > 0.0)) return tol;
+    return fmin(fmax(tol, it.otol * sqrt(it.bo2[b] / rr)), 0.5);
+}
+
 // grid B, block 32
-__global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol, int stag) {
+__global__ void k_tfqmr_init(TfqmrScal *sc, const double *part_r2, const double *part_b2, double tol, int stag,
+                             InnerTol itol) {
     const int b = blockIdx.x;
     double r2 = reduce_parts(part_r2, b);
     double b2 = reduce_parts(part_b2, b);
-    if (threadIdx.x == 0) sc[b] = init_scalars(r2, b2, tol, stag);
+    if (threadIdx.x == 0) sc[b] = init_scalars(r2, b2, inner_tol_of(tol, itol, b), stag);
 }
 
 // x = 0 for right-hand sides with b = 0 (conv == 3), then mark them done
@@ -922,7 +940,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_start_zero(const S *__res
                                                                   V *__restrict__ rs, V *__restrict__ d, long L,
                                                                   double *__restrict__ part,
                                                                   TfqmrScal *__restrict__ sc, double tol, int stag,
-                                                                  unsigned *ctr) {
+                                                                  unsigned *ctr, InnerTol itol) {
     __shared__ double sh[32];
     const int b = blockIdx.y;
     const long o = (long)b * L;
@@ -945,7 +963,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_start_zero(const S *__res
     for (int bb = threadIdx.x >> 5; bb < B; bb += blockDim.x >> 5) {
         const double r2 = reduce_parts_lane(part, bb, lane);
         if (lane == 0) {
-            TfqmrScal u = init_scalars(r2, r2, tol, stag);
+            TfqmrScal u = init_scalars(r2, r2, inner_tol_of(tol, itol, bb), stag);
             if (u.conv == 3) u.conv = 1;
             sc[bb] = u;
         }

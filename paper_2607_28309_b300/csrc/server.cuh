@@ -92,8 +92,8 @@ size_t serve_estimate(const ServeJob &j) {
     b += (size_t)(ell + 1) * 6 * (Mh[2] / 2 + 1) * (Mh[1] / 2 + 1) * Hh * (mixed ? 4 : 8);  // history spectra
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + M0[1]) * H0 * 16;                        // product workspace
     b += 5 * n3 * 8 + 10 * n3 * (mixed ? 4 : 8) + (mixed ? 2 * n3 * 4 : 0);               // J, b, r, Krylov
-    const long tb = mixed ? 8 : 4;  // time block of the history: tb + 1 partial sums
-    b += (size_t)(ell + 1 + tb + 1) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum, partial sums
+    const long tb = mixed ? 8 : 4;  // time block of the history: 2 tb partial sums
+    b += (size_t)(ell + 1 + 2 * tb) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum, partial sums
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + Mh[1]) * Hh * cs;                       // history workspace
     return b + b / 10 + ((size_t)64 << 20);
 }

@@ -674,12 +674,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // slab     the tile's Lambda0 values, [6][Kz][TC] in shared memory, fetched
 //          with asynchronous copies issued first (they overlap stages A, B1);
 // stage A  thread (q, t, c): x_q[t + R2 m], m < R1, straight from HBM, R1-point
-//          DFT in registers, twiddle W_M^(t k1), to shared memory;
+//          DFT in registers, twiddle W_M^(t k1), to shared memory at (q, k1, t, c);
 // stage B  (task = (q, k1, c)): R2-point DFT over t -> X[k1 + R1 k2]; 3x3 Green
 //          multiply from the slab per (kz, c); inverse R2-point DFT, twiddle
 //          W_M^(-t k1);
 // stage A' thread (q, t, c): inverse R1-point DFT over k1, rows z < Nz to HBM.
-// grid = (ceil(My*H/TC), B); smem = (M + 3*TC*(M+1)) complex + 6*(M/2+1)*TC real
+// Staging in shared memory: [q][k1][t][c] with each (q, k1) block of R2*TC values
+// padded (z_stage_pad) so that the strided stages meet few bank conflicts.
+// grid = (ceil(My*H/TC), B); smem = (M + 3*R1*KS) complex + 6*(M/2+1)*TC real
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // TMA (cp.async.bulk.tensor) staging: a 2-D tensor map over the planes buffer
@@ -712,9 +714,38 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
+// padding of the z pass's staging blocks: the block of one (component, k1) holds
+// R2 x TC complex values ([t][c], c fastest) plus `pad`, chosen at compile time
+// so that the R2-point stages' accesses (a warp = 32/TC values of k1 x TC
+// columns, each thread walking its own t) spread over the fewest shared-memory
+// wavefronts (each bank serves one 4-byte word per wavefront)
+template <int R2, int TC, int ES> __host__ __device__ constexpr int z_stage_pad() {
+    int best = 0, bestw = 1 << 30;
+    for (int pad = 0; pad < 16; ++pad) {
+        const int KS = R2 * TC + pad;
+        int cnt[32] = {};
+        for (int i = 0; i < 32; ++i) {
+            const int k1 = i / TC, cc = i % TC;
+            const int w0 = (k1 * KS + cc) * (ES / 4);
+            for (int j = 0; j < ES / 4; ++j) cnt[(w0 + j) % 32] += 1;
+        }
+        int w = 0;
+        for (int b = 0; b < 32; ++b) w = w > cnt[b] ? w : cnt[b];
+        if (w < bestw) {
+            bestw = w;
+            best = pad;
+        }
+    }
+    return best;
+}
+template <typename T, int R2, int TC> __host__ __device__ constexpr int z_stage_ks() {
+    return R2 * TC + z_stage_pad<R2, TC, (int)sizeof(cplx<T>)>();
+}
+
 template <typename T, int R1, int R2, int TC>
 __host__ __device__ constexpr size_t z_green_r_smem() {
-    return (size_t)(R1 * R2 + 3 * TC * (R1 * R2 + 1)) * sizeof(cplx<T>) + (size_t)6 * (R1 * R2 / 2 + 1) * TC * sizeof(T);
+    return (size_t)(R1 * R2 + 3 * R1 * z_stage_ks<T, R2, TC>()) * sizeof(cplx<T>) +
+           (size_t)6 * (R1 * R2 / 2 + 1) * TC * sizeof(T);
 }
 // with TMA staging: plus the [3][Nz <= M][TC] landing tile (each component on a
 // 128-byte boundary) and the mbarrier
@@ -728,12 +759,13 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
                                                            const cplx<T> *__restrict__ tw_g, int Nz, int My, int H,
                                                            Octant oc, const __grid_constant__ CUtensorMap tmap) {
     using C = cplx<T>;
-    constexpr int M = R1 * R2, RS = M + 1, KZ = M / 2 + 1;  // RS: padded row stride in shared memory
+    constexpr int M = R1 * R2, KZ = M / 2 + 1;
+    constexpr int KS = z_stage_ks<T, R2, TC>(), QS = R1 * KS;  // staging: [q][k1][t][c], k1 blocks padded to KS
     constexpr int NT = 3 * TC * R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *S = tw + M;                                   // [q][c][RS]
-    T *sL = reinterpret_cast<T *>(S + 3 * TC * RS);  // [6][KZ][TC]
+    C *S = tw + M;                                  // element (q, k1, t, c) at q QS + k1 KS + t TC + c
+    T *sL = reinterpret_cast<T *>(S + 3 * QS);      // [6][KZ][TC]
     // TMA landing tile [q][z][c] (component stride tstride elements, 128-byte aligned) and its mbarrier
     unsigned char *tp = smem_raw + z_green_r_smem<T, R1, R2, TC>();
     tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 127) & ~(uintptr_t)127);
@@ -789,29 +821,29 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
             else v[m] = (live && z < Nz) ? base[q * comp + (long)z * plane + col0 + c] : cmake<C>(T(0), T(0));
         }
         dft_small<R1, -1>(v);
-        C *row = S + (q * TC + c) * RS;
+        C *row = S + q * QS + t * TC + c;
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) {
             C x = v[k1];
             if (k1 > 0 && t > 0) x = cmul(x, tw[t * k1]);
-            row[k1 * R2 + t] = x;
+            row[k1 * KS] = x;
         }
     }
     __syncthreads();
     // ---- stage B1: R2-point DFT of every (q, c, k1) row segment, in place
     for (int task = threadIdx.x; task < 3 * R1 * TC; task += NT) {
         const int qq = task / (R1 * TC), rem = task - qq * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
-        C *seg = S + (qq * TC + cc) * RS + k1 * R2;
+        C *seg = S + qq * QS + k1 * KS + cc;
         C u[R2];
 #pragma unroll
-        for (int tt = 0; tt < R2; ++tt) u[tt] = seg[tt];
+        for (int tt = 0; tt < R2; ++tt) u[tt] = seg[tt * TC];
         dft_small<R2, -1>(u);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) seg[k2] = u[k2];
+        for (int k2 = 0; k2 < R2; ++k2) seg[k2 * TC] = u[k2];
     }
     cp_async_wait_all();
     __syncthreads();
-    // ---- stage B2: 3x3 Green multiply at every (kz, c); kz = k1 + R1 k2 sits at k1*R2 + k2
+    // ---- stage B2: 3x3 Green multiply at every (kz, c); kz = k1 + R1 k2 sits at (k1, t = k2)
     const FastDiv fH = make_fastdiv((unsigned)H);
     for (int task = threadIdx.x; task < M * TC; task += NT) {
         const int pos = task / TC, cc = task - pos * TC;  // pos = k1*R2 + k2
@@ -824,26 +856,27 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
         float sz;
         if (2 * kz > M) { fz = M - kz; sz = -1.f; } else { fz = kz; sz = 1.f; }
         C in[3], out[3];
+        C *at = S + k1 * KS + k2 * TC + cc;
 #pragma unroll
-        for (int qq = 0; qq < 3; ++qq) in[qq] = S[(qq * TC + cc) * RS + pos];
+        for (int qq = 0; qq < 3; ++qq) in[qq] = at[qq * QS];
         green_mul<T>(sL, (long)KZ * TC, (long)fz * TC + cc, sz, sy, in, out);
 #pragma unroll
-        for (int qq = 0; qq < 3; ++qq) S[(qq * TC + cc) * RS + pos] = out[qq];
+        for (int qq = 0; qq < 3; ++qq) at[qq * QS] = out[qq];
     }
     __syncthreads();
     // ---- stage B3: inverse R2-point DFT over k2, twiddle W_M^(-t k1)
     for (int task = threadIdx.x; task < 3 * R1 * TC; task += NT) {
         const int qq = task / (R1 * TC), rem = task - qq * (R1 * TC), k1 = rem / TC, cc = rem - k1 * TC;
-        C *seg = S + (qq * TC + cc) * RS + k1 * R2;
+        C *seg = S + qq * QS + k1 * KS + cc;
         C u[R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) u[k2] = seg[k2];
+        for (int k2 = 0; k2 < R2; ++k2) u[k2] = seg[k2 * TC];
         dft_small<R2, +1>(u);
 #pragma unroll
         for (int tt = 0; tt < R2; ++tt) {
             C x = u[tt];
             if (k1 > 0 && tt > 0) x = cmul(x, cconj(tw[tt * k1]));
-            seg[tt] = x;
+            seg[tt * TC] = x;
         }
     }
     __syncthreads();
@@ -851,9 +884,9 @@ __global__ void __launch_bounds__(3 * TC * R2) k_z_green_r(cplx<T> *__restrict__
     // ---- stage A': inverse R1-point DFT over k1, rows z = t + R2 m < Nz
     {
         C v[R1];
-        const C *row = S + (q * TC + c) * RS;
+        const C *row = S + q * QS + t * TC + c;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) v[k1] = row[k1 * R2 + t];
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = row[k1 * KS];
         dft_small<R1, +1>(v);
         if (live) {
 #pragma unroll
@@ -887,10 +920,10 @@ template <int Mode, typename V> __device__ __forceinline__ V hist_ld(const V *p)
 }
 
 // Time-blocked history (see k_hist_block): the lags 2.. partial sums of the
-// steps of one time block live in TB + 1 rotating slots, slot m mod (TB + 1) for
-// step m.  QSlots tells the accumulation which of its operands is such a slot.
+// steps of two consecutive time blocks live in 2TB rotating slots, slot m mod 2TB
+// for step m.  QSlots tells the accumulation which of its operands is such a slot.
 template <typename T> struct QSlots {
-    cplx<T> *buf;   // TB + 1 slots of the full half spectrum (nullptr: not used)
+    cplx<T> *buf;   // 2 TB slots of the full half spectrum (nullptr: not used)
     long slot;      // elements per slot
     int TB;         // steps per time block
     int flags;      // kQBase: base = slot of step m; kQAcc: acc = that slot; kQNear: lags 2..(m mod TB)+1
@@ -905,7 +938,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
                                                   QSlots<T> qs = QSlots<T>{nullptr, 0, 0, 0}) {
     if (nptr) m = (long)*nptr + dm;  // graph mode: step index from device memory
     if (qs.buf) {
-        cplx<T> *q = qs.buf + (m % (qs.TB + 1)) * qs.slot;
+        cplx<T> *q = qs.buf + (m % (2 * qs.TB)) * qs.slot;
         if (qs.flags & kQBase) base = q;
         if (qs.flags & kQAcc) acc = q;
         if (qs.flags & kQNear) {
@@ -990,25 +1023,37 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 
 // ---------------------------------------------------------------------------
 // time-blocked history (Eq. 3): the lags >= 2 part of the history sums of the
-// TB steps m0 .. m0 + TB - 1 of one time block, computed in one pass.  Output t
-// (step m0 + t) gets the lags k >= t + 2, whose currents J_{m0+t-k} are all
-// older than m0 - 1; the lags 2 .. t + 1 are added before step m0 + t (kQNear
-// accumulation) and lag 1 in the step itself, so each step's sum is the same
-// lags 2.. partial sum in a different order of terms:
-//   Q[(m0 + t) mod (TB+1)] = sum_{k = t+2 .. min(ell, m0 + t)} Lambda_k Jhat_{m0+t-k},  t in [tlo, TB).
-// The pass walks the ring once from the newest slot (m0 - 2) back, each slot
-// read once for all TB outputs; the TB Lambda_k a slot needs (k = u + 2 + t,
-// u its age) slide one lag per slot, kept in a register window rotated by
-// unrolling.  One thread per octant point and group, holding the point's four
-// mirrored rows (they share the octant's Lambda values, sign-flipped); the
-// block's TB outputs are split over four thread groups of TH outputs (block
-// (32, 4)).  The ring values of the block's 32 points stream through a shared-
-// memory pipeline of kHistBlockDepth slots (cp.async, thread group y loading
-// mirror row y), so many slots are in flight without registers and the four
-// groups read each value once from HBM.  With nptr: m0 = *nptr + dm, and the
-// pass runs only when m0 is the first step of a block (m0 mod TB == 0).
+// TB steps m0 .. m0 + TB - 1 of one time block.  Output t (step m0 + t) gets
+// the lags k >= t + 2, whose currents J_{m0+t-k} are all older than m0 - 1;
+// the lags 2 .. t + 1 are added before step m0 + t (kQNear accumulation) and
+// lag 1 in the step itself, so each step's sum is the same lags 2.. partial
+// sum in a different order of terms:
+//   Q[(m0 + t) mod 2TB] = sum_{k = t+2 .. min(ell, m0 + t)} Lambda_k Jhat_{m0+t-k},  t in [tlo, TB).
+// With u = k - t - 2 the age of the input J_{m0-2-u} (the same for all TB
+// outputs), the sum splits in two parts of one kernel:
+//   old part    (u >= TB): its inputs exist TB steps before the block starts,
+//               so it runs in TB chunks of the octant points, one chunk beside
+//               each step of the previous block, and stores Q;
+//   recent part (u < TB): at the block start (beside step m0 - 1), adding onto
+//               the stored Q.
+// Blocks alternate between two halves of the 2TB partial-sum slots, so the old
+// part of the next block never writes a slot the current block reads.  Each
+// part walks its slots once from the newest back, each slot read once for all
+// TB outputs; the TB Lambda_k a slot needs (k = u + 2 + t) slide one lag per
+// slot, kept in a register window rotated by unrolling.  One thread per octant
+// point and group, holding the point's four mirrored rows (they share the
+// octant's Lambda values, sign-flipped); the TB outputs are split over four
+// thread groups of TH outputs (block (32, 4)).  The ring values of the block's
+// 32 points stream through a shared-memory pipeline of kHistBlockDepth slots
+// (cp.async, thread group y loading mirror row y), so many slots are in flight
+// without registers and the four groups read each value once from HBM.
+// Host-driven: m0 is the block start, [c_lo, c_hi) the chunks of TB.  With
+// nptr (graph mode, beside step *nptr): m = *nptr + dm is the next step, t =
+// m mod TB; the recent part runs only when t == 0 (block m0 = m), the old part
+// takes chunk t of the block after m's (m0 = m - t + TB).
 // ---------------------------------------------------------------------------
 constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
+constexpr int kHistOld = 0, kHistRecent = 1;
 
 template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
     return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
@@ -1017,20 +1062,32 @@ template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
 template <typename T, int TB, int TH>
 __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
                                                     cplx<T> *__restrict__ qbuf, long qslot, int Mz, int My, int H,
-                                                    Octant oc, int nrhs, int ell, long m0, int tlo,
-                                                    const long long *__restrict__ nptr, int dm) {
+                                                    Octant oc, int nrhs, int ell, long m0, int tlo, int part,
+                                                    int c_lo, int c_hi, const long long *__restrict__ nptr, int dm) {
     static_assert(TB / TH == 4, "four thread groups: group y also loads mirror row y");
     constexpr int D = kHistBlockDepth;
     if (nptr) {
-        m0 = (long)*nptr + dm;
-        if (m0 % TB != 0) return;
+        const long m = (long)*nptr + dm;
+        const int t = (int)(m % TB);
         tlo = 0;
+        if (part == kHistRecent) {
+            if (t != 0) return;
+            m0 = m;
+            c_lo = 0;
+            c_hi = TB;
+        } else {
+            m0 = m - t + TB;
+            c_lo = t;
+            c_hi = t + 1;
+        }
     }
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);  // [D][row 4][component 3][point 32]
     const int hz = Mz / 2 + 1, hy = My / 2 + 1;
     const unsigned total = (unsigned)nrhs * hz * hy * H;
+    const unsigned p_lo = (unsigned)((unsigned long long)total * c_lo / TB);
+    const unsigned p_hi = (unsigned)((unsigned long long)total * c_hi / TB);
     const long plane = (long)My * H;
     const long slot_comp = (long)Mz * plane;
     const long slot_size = (long)nrhs * 3 * slot_comp;
@@ -1038,11 +1095,15 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
     const FastDiv fH = make_fastdiv((unsigned)H), fy = make_fastdiv((unsigned)hy), fz_ = make_fastdiv((unsigned)hz);
     const int x = threadIdx.x, y = threadIdx.y;
     const int t0 = y * TH;  // this thread's outputs t0 .. t0 + TH - 1
-    // inputs J_j for j = m0 - 2 - u, u in [0, U): every j >= 0 and within ell of step m0
+    // inputs J_j for j = m0 - 2 - u: every j >= 0 and within ell of step m0, u < U;
+    // the old part takes u in [TB, U), the recent part u in [0, min(TB, U))
     const long U = (m0 - 1 < (long)ell - 1) ? m0 - 1 : (long)ell - 1;
-    for (unsigned base = blockIdx.x * 32; base < total; base += gridDim.x * 32) {
+    const long u_lo = part == kHistOld ? TB : 0;
+    const long u_hi = part == kHistOld ? U : (U < TB ? U : (long)TB);
+    const long nu = u_hi > u_lo ? u_hi - u_lo : 0;
+    for (unsigned base = p_lo + blockIdx.x * 32; base < p_hi; base += gridDim.x * 32) {
         const unsigned idx = base + x;
-        const bool valid = idx < total;
+        const bool valid = idx < p_hi;
         long off[4] = {0, 0, 0, 0};
         bool twoy = false, twoz = false;
         const T *Lp = Lh;
@@ -1065,7 +1126,7 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
         }
         // loader: thread (x, y) copies mirror row y of point x, three components, per slot
         const long my_off = y == 0 ? off[0] : y == 1 ? off[1] : y == 2 ? off[2] : off[3];
-        long s_issue = (m0 - 2) % ell;  // ring slot of the next slot to load (decremented, wrapping)
+        long s_issue = ((m0 - 2 - u_lo) % ell + ell) % ell;  // ring slot of the next slot to load (wrapping)
         auto issue = [&](int bslot) {
             if (valid) {
                 const C *R = ring + s_issue * slot_size + my_off;
@@ -1077,7 +1138,7 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
         };
 #pragma unroll 1
         for (int i = 0; i < D - 1; ++i) {
-            if (i < U) issue(i);
+            if (i < nu) issue(i);
             else asm volatile("cp.async.commit_group;\n" ::);
         }
         C a[TH][4][3];
@@ -1087,37 +1148,38 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) a[i][r][q] = cmake<C>(T(0), T(0));
-        // window: at walk position u, output t0 + i needs lag k = u + 2 + t0 + i, held in
-        // lw[(u + i) mod TH]; before the walk lw[i] holds lag 2 + t0 + i
+        // window: at walk position w (u = u_lo + w), output t0 + i needs lag
+        // k = u + 2 + t0 + i, held in lw[(w + i) mod TH]; before the walk lw[i]
+        // holds lag u_lo + 2 + t0 + i
         T lw[TH][6];
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
-            const long k = 2 + t0 + i;
+            const long k = u_lo + 2 + t0 + i;
 #pragma unroll
             for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = (valid && k <= ell) ? Lp[k * 6 * cs + c6 * cs] : T(0);
         }
-        for (long u0 = 0; u0 < U; u0 += TH) {
+        for (long w0 = 0; w0 < nu; w0 += TH) {
             // fully unrolled with a guard (uniform over the block) rather than a break: the
-            // window index (uu + i) % TH stays a compile-time constant, lw and a in registers
+            // window index (ww + i) % TH stays a compile-time constant, lw and a in registers
 #pragma unroll
-            for (int uu = 0; uu < TH; ++uu) {
-                const long u = u0 + uu;
-                if (u < U) {
-                    asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot u landed
-                    __syncthreads();  // ... for every thread; and slot u - 1's buffer is free again
-                    const int bs = (int)(u % D);
+            for (int ww = 0; ww < TH; ++ww) {
+                const long w = w0 + ww, u = u_lo + w;
+                if (w < nu) {
+                    asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot w landed
+                    __syncthreads();  // ... for every thread; and slot w - 1's buffer is free again
+                    const int bs = (int)(w % D);
                     C uv[4][3];
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) uv[r][q] = buf[((bs * 4 + r) * 3 + q) * 32 + x];
-                    if (u + D - 1 < U) issue((int)((u + D - 1) % D));
+                    if (w + D - 1 < nu) issue((int)((w + D - 1) % D));
                     else asm volatile("cp.async.commit_group;\n" ::);
 #pragma unroll
                     for (int i = 0; i < TH; ++i) {
                         const long k = u + 2 + t0 + i;
                         if (t0 + i >= tlo && k <= ell) {
-                            const T *g = lw[(uu + i) % TH];
+                            const T *g = lw[(ww + i) % TH];
                             const T gxx = g[0], gyy = g[1], gzz = g[2];
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
@@ -1133,11 +1195,11 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
                             }
                         }
                     }
-                    // lw[uu] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
+                    // lw[ww] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
                     const long kn = u + 2 + t0 + TH;
 #pragma unroll
                     for (int c6 = 0; c6 < 6; ++c6)
-                        lw[uu][c6] = (valid && kn <= ell) ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+                        lw[ww][c6] = (valid && kn <= ell) ? Lp[kn * 6 * cs + c6 * cs] : T(0);
                 }
             }
         }
@@ -1147,13 +1209,20 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
             if (t0 + i < tlo) continue;
-            C *Q = qbuf + ((m0 + t0 + i) % (TB + 1)) * qslot;
+            C *Q = qbuf + ((m0 + t0 + i) % (2 * TB)) * qslot;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const bool on = (r == 0) || (r == 1 && twoy) || (r == 2 && twoz) || (r == 3 && twoy && twoz);
                 if (!on) continue;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) Q[off[r] + q * slot_comp] = a[i][r][q];
+                for (int q = 0; q < 3; ++q) {
+                    C *dst = Q + off[r] + q * slot_comp;
+                    if (part == kHistRecent) {
+                        const C o = *dst;
+                        *dst = cmake<C>(o.x + a[i][r][q].x, o.y + a[i][r][q].y);
+                    } else
+                        *dst = a[i][r][q];
+                }
             }
         }
     }
@@ -1628,6 +1697,51 @@ struct EpiZ0 {
         return Plane{x + off, y + off, eps + zoff, dl};
     }
     __device__ __forceinline__ void finish(const Plane &, long) const {}  // end-of-block hook
+};
+
+// Z0 product with the FFT in double-float (FFT scalar dfl): x, y and eps in
+// FP64, G rounded to FP64 and the contrast terms formed in FP64
+struct EpiZ0DF {
+    static constexpr bool kPlaneOnly = false;
+    const double *x;
+    double *y;
+    const double *eps;
+    long plane_rows;
+    int Nx;
+    double dl = 0.0;
+    __device__ __forceinline__ void operator()(long row, int e, double g) const {
+        const long idx = row * Nx + e;
+        const double ep = eps[(row % plane_rows) * Nx + e];
+        y[idx] = (ep * 0.5 + dl) * x[idx] - (ep - 1.0) * g;
+    }
+    struct Plane {
+        const double *x;
+        double *y;
+        const double *eps;
+        double dl;
+        __device__ __forceinline__ void operator()(int i, dfl g) const {
+            const double ep = eps[i];
+            y[i] = (ep * 0.5 + dl) * x[i] - (ep - 1.0) * to_double(g);
+        }
+        __device__ __forceinline__ void prefetch(int i) const {
+            prefetch_l2(eps + i);
+            prefetch_l2(x + i);
+        }
+        template <int W> __device__ __forceinline__ void pack(int i, const dfl (&g)[W]) const {
+            double e[W], xv[W], r[W];
+            ldv<W>(e, eps + i);
+            ldv<W>(xv, x + i);
+#pragma unroll
+            for (int k = 0; k < W; ++k) r[k] = (e[k] * 0.5 + dl) * xv[k] - (e[k] - 1.0) * to_double(g[k]);
+            stv<W>(y + i, r);
+        }
+    };
+    __device__ __forceinline__ Plane bind(long plane, int Nz, int NyNx) const {
+        const long off = plane * (long)NyNx;
+        const long zoff = (plane % Nz) * (long)NyNx;
+        return Plane{x + off, y + off, eps + zoff, dl};
+    }
+    __device__ __forceinline__ void finish(const Plane &, long) const {}
 };
 
 // refinement residual: r = b - (eps T(0) x - (eps - 1) G), all FP64

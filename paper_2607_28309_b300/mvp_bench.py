@@ -59,7 +59,8 @@ def run(workload="cube64_a8", nrhs=None, dtype="f32", warmup=3, reps=20, kernels
     B = int(nrhs or len(w["exc"]))
     N = w["N"]
     nv = int(np.prod(N))
-    dt, tdt, es = (mot.MOT_F32, torch.float32, 4) if dtype == "f32" else (mot.MOT_F64, torch.float64, 8)
+    dt, tdt, es = {"f32": (mot.MOT_F32, torch.float32, 4), "f64": (mot.MOT_F64, torch.float64, 8),
+                   "f64df": (mot.MOT_F64DF, torch.float64, 8)}[dtype]
     ctx = mot.mot_ctx_create(device, stream.cuda_stream)
     prob = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"])
     try:
@@ -98,6 +99,11 @@ def run(workload="cube64_a8", nrhs=None, dtype="f32", warmup=3, reps=20, kernels
         if peak:
             out["alg_frac"] = out["alg_GBps"] / peak
             out["pass_frac"] = out["pass_GBps"] / peak
+        if dtype == "f64df":  # the double-float product against the FP64 one
+            y64 = torch.empty_like(x)
+            mot.mot_apply_Z0(prob, x, y64, B, mot.MOT_F64)
+            torch.cuda.synchronize()
+            out["rel_l2_vs_f64"] = float(torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64))
         if kernels:
             from torch.profiler import ProfilerActivity, profile
 
@@ -122,7 +128,7 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--workload", default="cube64_a8")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's plane waves)")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "f64df"])
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--kernels", action="store_true")

@@ -3,6 +3,8 @@
 Tolerances (relative L2 unless stated):
 - FP64 Z0 FFT product vs the oracle's direct product:            1e-10
 - FP32 Z0 FFT product vs the oracle:                             1e-5 (measured value reported)
+- double-float (FP32-pair) Z0 product vs the oracle with the oracle's
+  table loaded, and vs the FP64 product at full size:              1e-13
 - library lag tables vs the oracle's tables:                      1e-12 absolute
 - FP64 march vs the oracle march (exact solve), per step, scaled
   by max_n ||J_n||:                                                1e-9
@@ -39,7 +41,7 @@ def _rel(a, b):
 
 
 def _apply(prob, x_np, nrhs, dtype):
-    tdt = torch.float64 if dtype == mot.MOT_F64 else torch.float32
+    tdt = torch.float32 if dtype == mot.MOT_F32 else torch.float64
     x = torch.from_numpy(np.ascontiguousarray(x_np)).to("cuda", tdt)
     y = torch.empty_like(x)
     mot.mot_apply_Z0(prob, x, y, nrhs, dtype)
@@ -71,10 +73,17 @@ def test_z0_fft_product_matches_direct(ctx, orc, N, alpha):
             assert _rel(y64, ref) <= 1e-10
             y32 = _apply(prob, x, nrhs, mot.MOT_F32)
             assert _rel(y32, ref) <= 1e-5
-        # the same product with the oracle's table loaded into the FFT path
+        # the same product with the oracle's table loaded into the FFT path: what is
+        # left is the FFT's rounding, FP64 and double-float (FP32 pairs, the
+        # FP64-accuracy product of a GPU with a slow FP64 pipe; target 1e-13)
         mot.mot_set_kernel_table(prob, 0, g, R)
-        x = rng.standard_normal((1, 3) + N[::-1])
-        assert _rel(_apply(prob, x, 1, mot.MOT_F64), orc.Zk_apply(0, N, eps, R, g, x[0])[None]) <= 1e-10
+        x = rng.standard_normal((2, 3) + N[::-1])
+        ref = np.stack([orc.Zk_apply(0, N, eps, R, g, x[b]) for b in range(2)])
+        e64 = _rel(_apply(prob, x, 2, mot.MOT_F64), ref)
+        edf = _rel(_apply(prob, x, 2, mot.MOT_F64DF), ref)
+        print(f"{N} alpha {alpha}: FP64 {e64:.2e}, double-float {edf:.2e}")
+        assert e64 <= 1e-10
+        assert edf <= 1e-13
     finally:
         mot.mot_problem_destroy(prob)
 
@@ -218,8 +227,13 @@ def test_full_size_product_sampled_rows(ctx, orc, which):
         g = orc.lag_table(0, rho, R)
         y64 = _apply(prob, x, nrhs, mot.MOT_F64)
         y32 = _apply(prob, x, nrhs, mot.MOT_F32)
+        ydf = _apply(prob, x, nrhs, mot.MOT_F64DF)
     finally:
         mot.mot_problem_destroy(prob)
+    # double-float against FP64 on every element (the same tables): 1e-13
+    edf = _rel(ydf, y64)
+    print(f"{which}: double-float vs FP64 product {edf:.2e}")
+    assert edf <= 1e-13
     bsel = rng.integers(0, nrhs, 1024)
     psel = rng.integers(0, 3, 1024)
     msel = rng.integers(0, nv, 1024)

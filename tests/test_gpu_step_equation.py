@@ -71,19 +71,20 @@ def _march(ctx, w, precision, nsteps, keep):
     return out, int(info.ell)
 
 
-def _step_residuals(orc, w, tables, J, keep, steps, rng):
-    """Relative L2 of res_n over ROWS_PER_STEP sampled rows, per step in `steps`."""
+def _step_residuals(orc, w, tables, J, keep, steps, rng, rows=ROWS_PER_STEP, pool=None):
+    """Relative L2 of res_n over `rows` sampled rows (voxels drawn from `pool`, all
+    voxels if None), per step in `steps`."""
     N, eps, h = w["N"], w["eps"], w["h"]
     nv = int(np.prod(N))
     dt = w["alpha"] * synthetic.dt_cfl(h)
     out = []
     for n in steps:
-        b_sel = rng.integers(0, len(keep), ROWS_PER_STEP)
-        p_sel = rng.integers(0, 3, ROWS_PER_STEP)
-        m_sel = rng.integers(0, nv, ROWS_PER_STEP)
-        lhs = np.zeros(ROWS_PER_STEP)
-        rhs = np.zeros(ROWS_PER_STEP)
-        lhs0 = np.zeros(ROWS_PER_STEP)
+        b_sel = rng.integers(0, len(keep), rows)
+        p_sel = rng.integers(0, 3, rows)
+        m_sel = rng.integers(0, nv, rows) if pool is None else rng.choice(pool, rows)
+        lhs = np.zeros(rows)
+        rhs = np.zeros(rows)
+        lhs0 = np.zeros(rows)
         for bi in np.unique(b_sel):
             sel = b_sel == bi
             pw = w["exc"][keep[bi]]
@@ -134,4 +135,37 @@ def test_step_equation_at_full_size(ctx, orc, which):
     scale = np.linalg.norm(J64.reshape(nsteps, -1), axis=1).max()
     rel = np.linalg.norm(d, axis=1) / scale
     print(f"{which} mixed vs FP64 relative L2 per step: max {rel.max():.3e}, last {rel[-1]:.3e}")
+    assert rel.max() <= 1e-5, rel.max()
+
+
+def test_step_equation_on_the_pillar_array(ctx, orc):
+    """The same check on the 256 x 256 x 80 pillar array at alpha 8 (15.7 M
+    unknowns; 270-point present-time FFTs, 512 x 512 x 160 history grid, the
+    bench's compiled shapes), over the first 14 steps: the time-blocked history's
+    block pass (step 8 opens the second block) and its near-lag accumulations
+    (steps 10, 13).  A pulse of a 40-step window puts its peak inside those steps;
+    the oracle needs the lag tables 0..13 only.  Rows are sampled in the pillars
+    (eps_r > 1): outside them the contrast, the current and the row vanish."""
+    w = dict(synthetic.workload("pillars8x8"))
+    w["exc"] = [synthetic.pulse(40, w["alpha"], w["h"], khat=(0.0, 0.0, -1.0))]
+    N = w["N"]
+    rho = w["alpha"] / math.sqrt(3)
+    nsteps = 14
+    tables = [(orc.table_extent(k, rho, N), None) for k in range(nsteps)]
+    tables = [(R, orc.lag_table(k, rho, R)) for k, (R, _) in enumerate(tables)]
+    steps = [8, 10, 13]
+    pool = np.flatnonzero(np.asarray(w["eps"]).reshape(-1) > 1.0)
+    J64, ell = _march(ctx, w, mot.MOT_FP64, nsteps, [0])
+    assert ell > nsteps
+    assert np.abs(J64[-1]).max() > 0
+    r64 = _step_residuals(orc, w, tables, J64, [0], steps, np.random.default_rng(77), rows=96, pool=pool)
+    print("pillars8x8 FP64 step-equation residuals", r64)
+    assert max(r64) <= 1e-9, r64
+    J32, _ = _march(ctx, w, mot.MOT_MIXED, nsteps, [0])
+    r32 = _step_residuals(orc, w, tables, J32, [0], steps, np.random.default_rng(77), rows=96, pool=pool)
+    print("pillars8x8 mixed step-equation residuals", r32)
+    assert max(r32) <= 1e-5, r32
+    d = J32.reshape(nsteps, -1) - J64.reshape(nsteps, -1)
+    rel = np.linalg.norm(d, axis=1) / np.linalg.norm(J64.reshape(nsteps, -1), axis=1).max()
+    print(f"pillars8x8 mixed vs FP64 relative L2 per step: max {rel.max():.3e}")
     assert rel.max() <= 1e-5, rel.max()
