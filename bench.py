@@ -211,7 +211,7 @@ def oracle_sample(w, mvps_per_step: float, rows: int = 2048, seed: int = 0):
 KERNEL_NAMES = {
     "z_green": "k_z_green_r (present-time z pass)",
     "z_history": "k_hist_acc + k_col_r (lag 1 onto the step's partial history sum, inverse z pass)",
-    "hist_side": "k_hist_block + k_hist_acc (time-blocked history: recent part at a block start, a chunk of the next block's old part every step, near lags 2..)",
+    "hist_side": "k_hist_block + k_hist_acc (time-blocked history: block pass at a block start, near lags 2..)",
     "fwd_half": "k_xy_forward_r<SrcHalfA> (forward xy pass of Z0 y2 + first TFQMR half step)",
     "fwd_y1": "k_xy_forward_r<SrcY1> (forward xy pass of Z0 y1)",
     "fwd_plain": "k_xy_forward_r<SrcPlain> (forward xy pass, stored input)",
@@ -227,13 +227,15 @@ KERNEL_NAMES = {
 }
 
 
-def kernel_bytes(info, N, B, prec, steps, TB=None):
+def kernel_bytes(info, N, B, prec, steps, TB=None, spread=None):
     """Algorithmic bytes of one launch of each timed kernel class: every array
     the kernel must read or write once, nothing for re-reads.  steps: the
     indices of the timed steps (the history classes depend on them); TB: the
     time block of the history (8 in the mixed path, 4 in FP64)."""
     if TB is None:
         TB = 8 if prec == 1 else 4
+    if spread is None:  # the library's schedule of the time-blocked pass
+        spread = os.environ.get("MOTJVIE_HIST_SPREAD", "0") not in ("", "0")
     ell = info.ell
     nv = N[0] * N[1] * N[2]
     cs = 8 if prec == 1 else 16          # complex element of the FFT precision (MOT_MIXED = 1)
@@ -256,16 +258,26 @@ def kernel_bytes(info, N, B, prec, steps, TB=None):
         return max(0, min(ell, u_hi + TB) - (u_lo + 2) + 1) if u_hi > u_lo else 0
 
     def side(m):
-        """the time-blocked history work that prepares step m (t = m mod TB): at a
-        block start the recent part of the block (inputs of age u < TB read once
-        for the block's TB steps, its Lambda_k, the TB partial sums read and
-        written), every step one chunk of TB of the next block's old part (inputs
-        u >= TB read once for its TB steps, their Lambda_k, the partial sums
-        written), and the near accumulation of lags 2..t+1 onto the step's partial
-        sum (read and written)"""
+        """the time-blocked history work that prepares step m (t = m mod TB).
+        Whole-pass schedule (default): at a block start one pass over the inputs
+        within ell (read once for the block's TB steps), Lambda_2.. read once, TB
+        partial sums written.  Spread schedule: at a block start the recent part
+        of the block (inputs of age u < TB, its Lambda_k, the TB partial sums
+        read and written), every step one chunk of TB of the next block's old
+        part (inputs u >= TB, their Lambda_k, the partial sums written).  Both:
+        the near accumulation of lags 2..t+1 onto the step's partial sum (read
+        and written)."""
         t = m % TB
         m0 = m - t
         b = 0
+        if not spread:
+            if t == 0:
+                U = max(0, min(ell - 1, m - 1))
+                b += U * slot + min(ell - 1, U + TB) * lam_h + TB * slot
+            near = max(0, min(t + 1, m, ell) - 1)
+            if near:
+                b += near * (slot + lam_h) + 2 * slot
+            return b
         if t == 0:
             U = max(0, min(ell - 1, m0 - 1))
             R = min(TB, U)
@@ -564,16 +576,43 @@ def native(args, ws, rank, local):
             n64 = mot.mot_run_step_index(rb)
             if n64 < n_cmp:
                 mot.mot_run_step(rb, n_cmp - n64, None, None, allow_notconv=True)
-            if mot.mot_run_step_index(rb) == n_cmp and J_mixed is not None:
+            J64 = None
+            if mot.mot_run_step_index(rb) == n_cmp:
                 src = mot.mot_run_current_device(rb)
                 torch.cuda.synchronize()
-                J64 = _dev_view(src, B * 3 * nv, dev)
-                compare["mixed_rel_l2_vs_fp64"] = {
-                    "step": n_cmp, "value": float(torch.linalg.vector_norm(J_mixed - J64) / torch.linalg.vector_norm(J64))}
+                J64 = _dev_view(src, B * 3 * nv, dev).clone()
+                if J_mixed is not None:
+                    compare["mixed_rel_l2_vs_fp64"] = {
+                        "step": n_cmp,
+                        "value": float(torch.linalg.vector_norm(J_mixed - J64) / torch.linalg.vector_norm(J64))}
             mot.mot_run_destroy(rb)
             mot.mot_problem_destroy(pb)
+            # the FP64-accuracy march built on double-float products (FP32 inner
+            # solves refined to 1e-11 against double-float residuals, history in
+            # double-float), its error against the FP64 march at the same step
+            pb = mot.mot_problem_create(ctx, N, w["h"], w["eps"], w["alpha"], gopt)
+            rb = mot.mot_run_create(pb, w["exc"], mot.MOT_FP64DF)
+            mot.mot_run_step(rb, ell + 1, None, None, allow_notconv=True)
+            msdf = _events_ms(stream, lambda: mot.mot_run_step(rb, S64, None, None, allow_notconv=True))
+            compare["fp64_double_float"] = {
+                "steps_per_s": S64 / (msdf / 1e3), "steps": S64, "after_steps": mot.mot_run_step_index(rb) - S64,
+                "speedup_over_fp64": ms64 / msdf,
+                "what": "MOT_FP64DF: FP32 inner TFQMR refined to 1e-11 against double-float (FP32-pair) residual "
+                        "products; history ring, spectra and sum in double-float; J in FP64"}
+            ndf = mot.mot_run_step_index(rb)
+            if ndf < n_cmp:
+                mot.mot_run_step(rb, n_cmp - ndf, None, None, allow_notconv=True)
+            if mot.mot_run_step_index(rb) == n_cmp and J64 is not None:
+                src = mot.mot_run_current_device(rb)
+                torch.cuda.synchronize()
+                Jdf = _dev_view(src, B * 3 * nv, dev)
+                compare["fp64_double_float"]["rel_l2_vs_fp64"] = {
+                    "step": n_cmp, "value": float(torch.linalg.vector_norm(Jdf - J64) / torch.linalg.vector_norm(J64))}
+            mot.mot_run_destroy(rb)
+            mot.mot_problem_destroy(pb)
+            del J64
         except Exception as e:  # reported, not fatal
-            compare["fp64"] = {"error": str(e)[:200]}
+            compare.setdefault("fp64", {})["error"] = str(e)[:200]
 
     # ---- other workloads on the same GPU, mixed, steady state
     extra = {}

@@ -52,11 +52,16 @@ typedef enum {
 } mot_status;
 
 /* arithmetic of a marching run (a5/a6 of the solver):
- * MOT_FP64  -- every product, FFT, history sum and Krylov vector in FP64;
- * MOT_MIXED -- FFTs, spectral multiplies, the history sum and the inner TFQMR
- *              vectors in FP32; FP64 for Krylov inner products, the residual,
- *              the refinement correction and the marched solution J_n.         */
-typedef enum { MOT_FP64 = 0, MOT_MIXED = 1 } mot_precision;
+ * MOT_FP64   -- every product, FFT, history sum and Krylov vector in FP64;
+ * MOT_MIXED  -- FFTs, spectral multiplies, the history sum and the inner TFQMR
+ *               vectors in FP32; FP64 for Krylov inner products, the residual,
+ *               the refinement correction and the marched solution J_n.
+ * MOT_FP64DF -- the FP64 path's accuracy (tolerance 1e-11 by default) from the
+ *               mixed path's structure: FP32 inner TFQMR solves refined against
+ *               residuals whose Z0 product runs in double-float (FP32 pairs,
+ *               about 48 bits), the history ring, its spectra and the history
+ *               sum in double-float too; J_n and the residual in FP64.        */
+typedef enum { MOT_FP64 = 0, MOT_MIXED = 1, MOT_FP64DF = 2 } mot_precision;
 
 /* element type of device vectors handed to mot_apply_Z0, and the arithmetic
  * of its FFTs: MOT_F64 and MOT_F32 vectors computed in that precision;
@@ -80,14 +85,15 @@ typedef struct {
 /* Solver options; pass NULL for the defaults shown.                           */
 typedef struct {
     double tol;       /* TFQMR relative residual target (paper: 1e-6, Sec. V-A).
-                         Default 1e-11 for MOT_FP64, 1e-6 (outer) for MOT_MIXED   */
+                         Default 1e-11 for MOT_FP64 and MOT_FP64DF (outer), 1e-6
+                         (outer) for MOT_MIXED                                      */
     int maxit;        /* TFQMR iteration cap per solve (default 500)             */
-    double inner_tol; /* MOT_MIXED inner FP32 TFQMR tolerance (default 1e-6),
+    double inner_tol; /* inner FP32 TFQMR tolerance of MOT_MIXED and MOT_FP64DF (default 1e-6),
                          relative to the refinement residual r; a sweep whose r
                          is already small against the outer right-hand side b
                          solves only to max(inner_tol, 0.3 tol ||b|| / ||r||)
                          (at most 1/2): the outer test is what it must pass     */
-    int max_refine;   /* MOT_MIXED refinement sweeps cap (default 6)              */
+    int max_refine;   /* refinement sweeps cap of MOT_MIXED and MOT_FP64DF (default 6) */
     double delta;     /* diagonal shift of the delta-regularised MOT (Sec. II,
                          Z^delta_n = Z_n + delta_n I): here delta_0 = delta for the
                          present-time matrix (every Z0 product and the solve) and
@@ -330,7 +336,7 @@ typedef struct {
     double h;                  /* voxel size [m]                                   */
     const double *eps_r;       /* host [Nz][Ny][Nx], copied at submit               */
     double alpha;              /* dt = alpha dt_CFL                                */
-    int32_t precision;         /* MOT_FP64 or MOT_MIXED                            */
+    int32_t precision;         /* MOT_FP64, MOT_MIXED or MOT_FP64DF                */
     int32_t nrhs;              /* plane waves                                      */
     const mot_planewave *exc;  /* host [nrhs], copied at submit                    */
     int32_t nsteps;            /* steps to march                                  */

@@ -25,6 +25,7 @@ MOT_EBUSY = -7
 MOT_ECANCELLED = -8
 MOT_FP64 = 0
 MOT_MIXED = 1
+MOT_FP64DF = 2
 MOT_F64 = 0
 MOT_F32 = 1
 MOT_F64DF = 2
@@ -36,7 +37,7 @@ __all__ = [
     "mot_problem_destroy", "mot_apply_Z0", "mot_kernel_table", "mot_set_kernel_table", "mot_table_host",
     "mot_run_create", "mot_run_step", "mot_run_current_device", "mot_run_step_index", "mot_run_destroy",
     "MOT_OK", "MOT_EINVAL", "MOT_ENOMEM", "MOT_ENOTCONV", "MOT_EUNSUPPORTED", "MOT_ECUDA", "MOT_ETIMEOUT",
-    "MOT_FP64", "MOT_MIXED", "MOT_F64", "MOT_F32", "MOT_F64DF", "EXPORTED", "mot_kernel_launches", "default_options",
+    "MOT_FP64", "MOT_MIXED", "MOT_FP64DF", "MOT_F64", "MOT_F32", "MOT_F64DF", "EXPORTED", "mot_kernel_launches", "default_options",
     "mot_apply_Z0_static", "MOT_STATIC_SCRATCH_BYTES", "mot_run_kernel_times", "KERNEL_CLASSES",
     "mot_run_save", "mot_run_load", "MOT_EBUSY", "MOT_ECANCELLED", "mot_request", "mot_result",
     "mot_server_create", "mot_server_submit", "mot_server_wait", "mot_server_destroy", "mot_fma_peak",

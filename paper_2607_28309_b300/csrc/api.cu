@@ -427,9 +427,9 @@ struct mot_problem {
     std::vector<AxisTw *> tws;
     std::vector<LagTable> lags;
     DBuf L0_64, L0_32, L0_df;  // [6][K0z][K0y][H0] in FP64, FP32, double-float
-    DBuf Lh_64, Lh_32;  // [ell+1][6][Khz][Khy][Hh]
-    std::shared_ptr<SharedDev> lh_hold[2];  // set when Lh_64 / Lh_32 is shared (not owned)
-    bool hist64 = false, hist32 = false;
+    DBuf Lh_64, Lh_32, Lh_df;  // [ell+1][6][Khz][Khy][Hh] in FP64, FP32, double-float
+    std::shared_ptr<SharedDev> lh_hold[3];  // set when Lh_64 / Lh_32 / Lh_df is shared (not owned)
+    bool hist64 = false, hist32 = false, histdf = false;
     DBuf glx, glw;
     // Z0 product workspace
     DBuf wsA, wsB;
@@ -1000,6 +1000,7 @@ template <> const dfl *L0_of<dfl>(mot_problem *p) { return (const dfl *)p->L0_df
 template <typename T> const T *Lh_of(mot_problem *p);
 template <> const double *Lh_of<double>(mot_problem *p) { return (const double *)p->Lh_64.p; }
 template <> const float *Lh_of<float>(mot_problem *p) { return (const float *)p->Lh_32.p; }
+template <> const dfl *Lh_of<dfl>(mot_problem *p) { return (const dfl *)p->Lh_df.p; }
 
 // timing-option class of a forward source / inverse epilogue
 template <class S> struct FwdClass { static constexpr int v = MOT_K_FWD_PLAIN; };
@@ -1497,16 +1498,16 @@ mot_status build_Z0_spectrum(mot_problem *p) {
 struct SpecKey {
     int device;
     double rho;
-    int N[3], Mh[3], ell, fp32;
+    int N[3], Mh[3], ell, kind;
     bool operator==(const SpecKey &o) const {
         return device == o.device && rho == o.rho && !memcmp(N, o.N, sizeof N) && !memcmp(Mh, o.Mh, sizeof Mh) &&
-               ell == o.ell && fp32 == o.fp32;
+               ell == o.ell && kind == o.kind;
     }
 };
 std::mutex g_spec_mu;
 std::vector<std::pair<SpecKey, std::weak_ptr<SharedDev>>> g_spec;
 
-SpecKey spec_key(const mot_problem *p, bool fp32) {
+SpecKey spec_key(const mot_problem *p, int kind) {
     SpecKey k;
     k.device = p->ctx->device;
     k.rho = p->rho;
@@ -1515,7 +1516,7 @@ SpecKey spec_key(const mot_problem *p, bool fp32) {
         k.Mh[i] = p->Mh[i];
     }
     k.ell = p->ell;
-    k.fp32 = fp32;
+    k.kind = kind;
     return k;
 }
 
@@ -1533,72 +1534,67 @@ std::shared_ptr<SharedDev> spec_lookup(const SpecKey &k) {
 }
 
 // hand the problem's own spectra buffer over to a shared holder and register it
-void spec_share(mot_problem *p, DBuf &buf, int slot, bool fp32) {
+void spec_share(mot_problem *p, DBuf &buf, int kind) {
     auto h = std::make_shared<SharedDev>();
     h->p = buf.p;
     h->bytes = buf.bytes;
     h->device = p->ctx->device;
-    p->lh_hold[slot] = h;
+    p->lh_hold[kind] = h;
     std::lock_guard<std::mutex> lk(g_spec_mu);
-    g_spec.emplace_back(spec_key(p, fp32), h);
+    g_spec.emplace_back(spec_key(p, kind), h);
 }
 
-mot_status build_history_spectra(mot_problem *p, bool want64, bool want32) {
-    if ((!want64 || p->hist64) && (!want32 || p->hist32)) return MOT_OK;
+// history spectra of one arithmetic: FP64, FP32 or double-float (kinds below),
+// computed in FP64 per lag and stored in that arithmetic
+enum { kSpec64 = 0, kSpec32 = 1, kSpecDF = 2 };
+DBuf &spec_buf(mot_problem *p, int kind) { return kind == kSpec64 ? p->Lh_64 : kind == kSpec32 ? p->Lh_32 : p->Lh_df; }
+bool &spec_have(mot_problem *p, int kind) { return kind == kSpec64 ? p->hist64 : kind == kSpec32 ? p->hist32 : p->histdf; }
+
+mot_status build_history_spectra(mot_problem *p, int kind) {
+    bool &have = spec_have(p, kind);
+    if (have) return MOT_OK;
+    DBuf &buf = spec_buf(p, kind);
     bool shareable = true;  // no caller-supplied table among the history lags
     for (int k = 1; k <= p->ell; ++k)
         if (p->lags[k].override_) shareable = false;
     if (shareable) {
-        for (int f = 0; f < 2; ++f) {
-            const bool want = f ? want32 : want64;
-            bool &have = f ? p->hist32 : p->hist64;
-            if (!want || have) continue;
-            if (auto h = spec_lookup(spec_key(p, f == 1))) {
-                DBuf &b = f ? p->Lh_32 : p->Lh_64;
-                dfree(b);
-                b.p = h->p;
-                b.bytes = h->bytes;
-                p->lh_hold[f] = h;
-                have = true;
-            }
+        if (auto h = spec_lookup(spec_key(p, kind))) {
+            dfree(buf);
+            buf.p = h->p;
+            buf.bytes = h->bytes;
+            p->lh_hold[kind] = h;
+            have = true;
+            return MOT_OK;
         }
-        if ((!want64 || p->hist64) && (!want32 || p->hist32)) return MOT_OK;
     }
-    const bool new64 = want64 && !p->hist64, new32 = want32 && !p->hist32;
     bool need_oct = false;
     for (int k = 1; k <= p->ell; ++k)
         if (!p->lags[k].ready) need_oct = true;
     if (need_oct) MOT_TRY(compute_lag_octants(p, 1, p->ell));
     long kn = (long)p->Kh[0] * p->Kh[1] * p->Kh[2];
     size_t per = 6 * (size_t)kn;
+    const size_t es = kind == kSpec32 ? sizeof(float) : sizeof(double);  // a dfl is 8 bytes too
     DBuf tmp;
-    MOT_TRY(dalloc(tmp, sizeof(double) * per));
-    if (want64 && !p->hist64) {
-        MOT_TRY(dalloc(p->Lh_64, sizeof(double) * per * (p->ell + 1)));
-        MOT_CUDA_TRY(cudaMemsetAsync(p->Lh_64.p, 0, sizeof(double) * per, p->ctx->stream));
-    }
-    if (want32 && !p->hist32) {
-        MOT_TRY(dalloc(p->Lh_32, sizeof(float) * per * (p->ell + 1)));
-        MOT_CUDA_TRY(cudaMemsetAsync(p->Lh_32.p, 0, sizeof(float) * per, p->ctx->stream));
-    }
+    if (kind != kSpec64) MOT_TRY(dalloc(tmp, sizeof(double) * per));
+    MOT_TRY(dalloc(buf, es * per * (p->ell + 1)));
+    MOT_CUDA_TRY(cudaMemsetAsync(buf.p, 0, es * per, p->ctx->stream));
     for (int k = 1; k <= p->ell; ++k) {
-        double *dst = (want64 && !p->hist64) ? (double *)p->Lh_64.p + per * k : (double *)tmp.p;
+        double *dst = kind == kSpec64 ? (double *)buf.p + per * k : (double *)tmp.p;
         MOT_TRY(lag_spectrum(p, p->lags[k], p->Mh, dst));
-        if (want32 && !p->hist32) {
+        if (kind == kSpec32) {
             count_launch();
-            k_scale_store<float><<<grid_for(per), 256, 0, p->ctx->stream>>>(dst, (float *)p->Lh_32.p + per * k, per,
-                                                                            1.0);
+            k_scale_store<float><<<grid_for(per), 256, 0, p->ctx->stream>>>(dst, (float *)buf.p + per * k, per, 1.0);
+            MOT_CHECK_LAUNCH();
+        } else if (kind == kSpecDF) {
+            count_launch();
+            k_scale_store<dfl><<<grid_for(per), 256, 0, p->ctx->stream>>>(dst, (dfl *)buf.p + per * k, per, 1.0);
             MOT_CHECK_LAUNCH();
         }
     }
     MOT_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
     dfree(tmp);
-    if (want64) p->hist64 = true;
-    if (want32) p->hist32 = true;
-    if (shareable) {
-        if (new64) spec_share(p, p->Lh_64, 0, false);
-        if (new32) spec_share(p, p->Lh_32, 1, true);
-    }
+    have = true;
+    if (shareable) spec_share(p, buf, kind);
     return MOT_OK;
 }
 
@@ -1906,10 +1902,11 @@ void mot_problem_destroy(mot_problem *p) {
     // shared spectra are released with the holder, not freed here
     if (p->lh_hold[0]) p->Lh_64.p = nullptr;
     if (p->lh_hold[1]) p->Lh_32.p = nullptr;
-    p->lh_hold[0].reset();
-    p->lh_hold[1].reset();
+    if (p->lh_hold[2]) p->Lh_df.p = nullptr;
+    for (auto &h : p->lh_hold) h.reset();
     dfree(p->Lh_64);
     dfree(p->Lh_32);
+    dfree(p->Lh_df);
     dfree(p->glx);
     dfree(p->glw);
     dfree(p->wsA);
@@ -1993,7 +1990,7 @@ mot_status mot_kernel_table(mot_problem *p, int lag, double *g_out, int32_t R_ou
 mot_status mot_set_kernel_table(mot_problem *p, int lag, const double *g, const int32_t R[3]) {
     if (!p || !g || !R) MOT_FAIL(MOT_EINVAL, "NULL argument");
     if (lag < 0 || lag > p->ell) MOT_FAIL(MOT_EINVAL, "lag out of range [0, ell]");
-    if (lag >= 1 && (p->hist64 || p->hist32)) MOT_FAIL(MOT_EINVAL, "history tables already in use; set them before mot_run_create");
+    if (lag >= 1 && (p->hist64 || p->hist32 || p->histdf)) MOT_FAIL(MOT_EINVAL, "history tables already in use; set them before mot_run_create");
     for (int i = 0; i < 3; ++i)
         if (R[i] < 0 || R[i] > 4096) MOT_FAIL(MOT_EINVAL, "table extent out of range");
     MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
@@ -2193,6 +2190,25 @@ template <typename V> bool fused_start(const mot_problem *p) { return z0_planes_
 // correction solve is given 0.3 of the outer tolerance, the rest left to its
 // rounding; MOTJVIE_INNER_ADAPT=0 keeps inner_tol fixed (timing comparisons)
 mot_status dev_norms2(mot_run *r, const double *v, double *out, cudaStream_t st);
+
+// outer tolerance of the refined precisions: the mixed path's 1e-6, the
+// double-float path's FP64-level 1e-11 (options.tol overrides)
+inline double outer_tol(const mot_run *r) {
+    const double t = r->p->opt.tol;
+    return t > 0 ? t : (r->prec == MOT_FP64DF ? 1e-11 : 1e-6);
+}
+
+// the outer residual r = b - Z0 J of the refinement: the product's FFT in FP32
+// (MOT_MIXED) or in double-float (MOT_FP64DF), its epilogue in FP64
+mot_status residual_product(mot_run *r, cudaStream_t st) {
+    mot_problem *p = r->p;
+    const long pr = (long)p->N[2] * p->N[1];
+    EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p, (const double *)p->eps.p, pr,
+                     p->N[0], p->opt.delta};
+    if (r->prec == MOT_FP64DF)
+        return z0_product<double, dfl>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st);
+    return z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st);
+}
 
 inline InnerTol inner_tol_for(mot_run *r, const double *ro2, double tol) {
     static const bool off = getenv("MOTJVIE_INNER_ADAPT") && atoi(getenv("MOTJVIE_INNER_ADAPT")) == 0;
@@ -2405,6 +2421,15 @@ template <typename T> QSlots<T> qslots(mot_run *r, int flags) {
     return QSlots<T>{(cplx<T> *)r->hpart.p, slot, r->hTB, flags};
 }
 
+// schedule of the time-blocked pass: 1 = the old part spread over the previous
+// block's steps and the recent part at the block start (the block-start step is
+// not held up by a whole pass: lower p99 step latency); 0 = one whole pass at the
+// block start (fewer bytes).  MOTJVIE_HIST_SPREAD = 0 | 1 overrides the default.
+inline bool hist_spread() {
+    static const int f = getenv("MOTJVIE_HIST_SPREAD") ? atoi(getenv("MOTJVIE_HIST_SPREAD")) : 0;
+    return f != 0;
+}
+
 // one part of the time-blocked pass (k_hist_block) for the block starting at
 // m0, outputs t >= tlo, octant-point chunks [c_lo, c_hi) of hTB; with nptr the
 // kernel takes its block and chunk from m = *nptr + dm (see k_hist_block)
@@ -2468,6 +2493,11 @@ template <typename T> mot_status hist_side_host(mot_run *r, cudaStream_t st, uns
     const long m = r->n;
     const int TB = r->hTB, t = (int)(m % TB);
     const long m0 = m - t;
+    if (!hist_spread()) {  // one whole pass at the block start
+        if (t == 0 || r->q_stale) MOT_TRY(hist_block_pass<T>(r, st, m0, t, kHistAll, 0, TB, nullptr, 0));
+        r->q_stale = false;
+        return hist_near<T>(r, st, m, nullptr, 0, blocks, bt, mode);
+    }
     if (r->q_stale) {
         MOT_TRY(hist_block_pass<T>(r, st, m0, t, kHistOld, 0, TB, nullptr, 0));
         MOT_TRY(hist_block_pass<T>(r, st, m0, t, kHistRecent, 0, TB, nullptr, 0));
@@ -2484,6 +2514,7 @@ template <typename T> mot_status hist_side_host(mot_run *r, cudaStream_t st, uns
 mot_status hist_prime(mot_run *r, cudaStream_t st) {
     if (!hist_streaming(r) || r->hpart_ok) return MOT_OK;
     if (r->prec == MOT_MIXED) MOT_TRY(hist_side_host<float>(r, st, hist_blocks(r, 32), 256, 0));
+    else if (r->prec == MOT_FP64DF) MOT_TRY(hist_side_host<dfl>(r, st, hist_blocks(r, 32), 256, 0));
     else MOT_TRY(hist_side_host<double>(r, st, hist_blocks(r, 32), 256, 0));
     r->hpart_ok = true;
     return MOT_OK;
@@ -2540,8 +2571,11 @@ template <typename T> mot_status history_rhs(mot_run *r, cudaStream_t st, const 
             MOT_CUDA_TRY(cudaEventRecord(r->hfork, st));
             MOT_CUDA_TRY(cudaStreamWaitEvent(r->hside, r->hfork, 0));
             const int bt = hist_side_threads();
-            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistRecent, 0, 0, nptr, 1));
-            MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistOld, 0, 0, nptr, 1));
+            if (hist_spread()) {
+                MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistRecent, 0, 0, nptr, 1));
+                MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistOld, 0, 0, nptr, 1));
+            } else
+                MOT_TRY(hist_block_pass<T>(r, r->hside, 0, 0, kHistAll, 0, 0, nptr, 1));
             MOT_TRY(hist_near<T>(r, r->hside, 0, nptr, 1, hist_blocks(r, hist_side_per_sm_x2(), bt), bt,
                                  hist_side_mode()));
             MOT_CUDA_TRY(cudaEventRecord(r->hjoin, r->hside));
@@ -2612,12 +2646,13 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     const long n = L * r->B;
     const long pr = (long)p->N[2] * p->N[1];
-    const bool mixed = r->prec == MOT_MIXED;
+    const bool mixed = r->prec == MOT_MIXED, dfm = r->prec == MOT_FP64DF;
     p->kt.on = p->opt.timing != 0;
     p->kt.reset();
     int mvps = 0;
     cudaEventRecord(r->ev[0], st);
     if (mixed) MOT_TRY(history_rhs<float>(r, st));
+    else if (dfm) MOT_TRY(history_rhs<dfl>(r, st));
     else MOT_TRY(history_rhs<double>(r, st));
     cudaEventRecord(r->ev[1], st);
     if (p->opt.guess == 1) {
@@ -2630,7 +2665,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     std::vector<double> bn(r->B), rn(r->B);
     MOT_TRY(norms(r, (const double *)r->b.p, bn.data()));
     double relres = 0.0;
-    if (!mixed) {
+    if (!mixed && !dfm) {
         const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
         int it;
         bool c;
@@ -2646,15 +2681,13 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
         ++mvps;
         MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
     } else {
-        const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
+        const double tol = outer_tol(r);
         float *r32 = (float *)r->r32.p;
         float *c32 = r32 + n;
         MOT_TRY(dev_norms2(r, (const double *)r->b.p, (double *)r->b2.p, st));
         const InnerTol itol = inner_tol_for(r, (const double *)r->dots.p, tol);
         for (sweeps = 0; sweeps <= p->opt.max_refine; ++sweeps) {
-            EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
-                             (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
-            MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            MOT_TRY(residual_product(r, st));
             ++mvps;
             MOT_TRY(norms(r, (const double *)r->r.p, rn.data()));
             bool done = true;
@@ -2689,6 +2722,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     for (int b = 0; b < r->B; ++b) relres = std::max(relres, bn[b] > 0 ? rn[b] / bn[b] : 0.0);
     cudaEventRecord(r->ev[2], st);
     if (mixed) MOT_TRY(ring_push<float>(r, st));
+    else if (dfm) MOT_TRY(ring_push<dfl>(r, st));
     else MOT_TRY(ring_push<double>(r, st));
     cudaEventRecord(r->ev[3], st);
     if (stats) {
@@ -2917,7 +2951,7 @@ mot_status tfqmr_capture(mot_run *r, V *x, const V *rhs, bool zero_x0, double to
 // capture one whole MOT step (Eq. 3) into r->step_graph
 mot_status build_step_graph(mot_run *r) {
     mot_problem *p = r->p;
-    const bool mixed = r->prec == MOT_MIXED;
+    const bool mixed = r->prec == MOT_MIXED, dfm = r->prec == MOT_FP64DF;
     const long L = 3L * p->N[0] * p->N[1] * p->N[2];
     const long n = L * r->B;
     const long pr = (long)p->N[2] * p->N[1];
@@ -2933,6 +2967,7 @@ mot_status build_step_graph(mot_run *r) {
         k_step_begin<<<1, 32, 0, st>>>(sd);
         MOT_CHECK_LAUNCH();
         if (mixed) MOT_TRY(history_rhs<float>(r, st, nptr));
+        else if (dfm) MOT_TRY(history_rhs<dfl>(r, st, nptr));
         else MOT_TRY(history_rhs<double>(r, st, nptr));
         if (p->opt.guess == 1) {
             count_launch();
@@ -2940,7 +2975,7 @@ mot_status build_step_graph(mot_run *r) {
             MOT_CHECK_LAUNCH();
         }
         MOT_TRY(dev_norms2(r, (const double *)r->b.p, (double *)r->b2.p, st));
-        if (!mixed) {
+        if (!mixed && !dfm) {
             const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
             MOT_TRY(tfqmr_capture<double>(r, (double *)r->J.p, (const double *)r->b.p, false, tol, p->opt.maxit, st,
                                           r->cap2, 1));
@@ -2953,13 +2988,11 @@ mot_status build_step_graph(mot_run *r) {
             MOT_CHECK_LAUNCH();
             MOT_TRY(ring_push<double>(r, st, nptr));
         } else {
-            const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-6;
+            const double tol = outer_tol(r);
             float *r32 = (float *)r->r32.p;
             float *c32 = r32 + n;
-            EpiResidual e = {(const double *)r->J.p, (const double *)r->b.p, (double *)r->r.p,
-                             (const double *)p->eps.p, pr, p->N[0], p->opt.delta};
             // residual of the initial guess, then sweeps while it misses tol
-            MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, st)));
+            MOT_TRY(residual_product(r, st));
             MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, st));
             WhileNode wo;
             MOT_TRY(while_handle(st, wo, 0));
@@ -2984,7 +3017,7 @@ mot_status build_step_graph(mot_run *r) {
                 count_launch();
                 k_add_scaled<<<gs, 256, 0, cs>>>((double *)r->J.p, c32, (const double *)r->r2.p, L);
                 MOT_CHECK_LAUNCH();
-                MOT_TRY((z0_product<double, float>(p, (const double *)r->J.p, r->B, p->wsA.p, p->wsB.p, e, cs)));
+                MOT_TRY(residual_product(r, cs));
                 MOT_TRY(dev_norms2(r, (const double *)r->r.p, (double *)r->r2.p, cs));
                 count_launch();
                 k_refine_cond<<<1, 32, 0, cs>>>(wo.h, (const double *)r->b2.p, (const double *)r->r2.p, r->B, tol,
@@ -2993,7 +3026,8 @@ mot_status build_step_graph(mot_run *r) {
                 return MOT_OK;
             }, &r->k_outer));
             r->k_outer -= r->k_inner;  // the nested loop body is counted per iteration
-            MOT_TRY(ring_push<float>(r, st, nptr));
+            if (dfm) MOT_TRY(ring_push<dfl>(r, st, nptr));
+            else MOT_TRY(ring_push<float>(r, st, nptr));
         }
         if (r->hjoin_open) {  // the next step's partial history sum is part of this step
             MOT_CUDA_TRY(cudaStreamWaitEvent(st, r->hjoin, 0));
@@ -3034,7 +3068,8 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if (!p || !exc || !out) MOT_FAIL(MOT_EINVAL, "NULL argument");
     *out = nullptr;
     if (nrhs < 1 || nrhs > 1024) MOT_FAIL(MOT_EINVAL, "nrhs out of range [1, 1024]");
-    if (precision != MOT_FP64 && precision != MOT_MIXED) MOT_FAIL(MOT_EINVAL, "precision must be MOT_FP64 or MOT_MIXED");
+    if (precision != MOT_FP64 && precision != MOT_MIXED && precision != MOT_FP64DF)
+        MOT_FAIL(MOT_EINVAL, "precision must be MOT_FP64, MOT_MIXED or MOT_FP64DF");
     for (int b = 0; b < nrhs; ++b) {
         const mot_planewave &w = exc[b];
         double kk = 0, pp = 0, kp = 0;
@@ -3051,7 +3086,8 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     }
     MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
     const bool mixed = precision == MOT_MIXED;
-    MOT_TRY(build_history_spectra(p, !mixed, mixed));
+    const bool inner32 = precision != MOT_FP64;  // FP32 inner solves refined against an outer residual
+    MOT_TRY(build_history_spectra(p, mixed ? kSpec32 : precision == MOT_FP64DF ? kSpecDF : kSpec64));
     mot_run *r = new mot_run();
     r->p = p;
     r->B = nrhs;
@@ -3104,8 +3140,8 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     cudaMemcpy(r->pw.p, r->pw_host.data(), sizeof(PlaneWaveDev) * nrhs, cudaMemcpyHostToDevice);
     cudaMemcpy((char *)r->pw.p + sizeof(PlaneWaveDev) * nrhs, pol.data(), sizeof(double) * 3 * nrhs,
                cudaMemcpyHostToDevice);
-    const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
-    const size_t vs = mixed ? sizeof(float) : sizeof(double);
+    const size_t cs = mixed ? sizeof(float2) : sizeof(double2);  // history element (dfl2: 16 bytes too)
+    const size_t vs = inner32 ? sizeof(float) : sizeof(double);   // Krylov vectors
     if ((s = dalloc(r->inc, sizeof(double) * nv * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->J, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->J2, sizeof(double) * n)) != MOT_OK) return fail(s);
@@ -3114,14 +3150,14 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
     if ((s = dalloc(r->ring, ring_bytes)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->hacc, ring_bytes / p->ell)) != MOT_OK) return fail(s);
-    // time block: 8 steps in FP32, 4 in FP64 (the block pass holds that many outputs in registers)
+    // time block: 8 steps in FP32, 4 in FP64 and double-float (the block pass holds that many outputs in registers)
     r->hTB = mixed ? 8 : 4;
     if ((s = dalloc(r->hpart, ring_bytes / p->ell * (2 * r->hTB))) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsAh, (size_t)nrhs * 3 * p->N[2] * p->N[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->wsBh, (size_t)nrhs * 3 * p->N[2] * p->Mh[1] * p->Hh * cs)) != MOT_OK) return fail(s);
     for (int i = 0; i < 10; ++i)
         if ((s = dalloc(r->kv[i], vs * n)) != MOT_OK) return fail(s);
-    if (mixed && (s = dalloc(r->r32, sizeof(float) * 2 * n)) != MOT_OK) return fail(s);
+    if (inner32 && (s = dalloc(r->r32, sizeof(float) * 2 * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->scal, sizeof(TfqmrScal) * nrhs)) != MOT_OK) return fail(s);
     // partial sums per right-hand side: kRedBlocks blocks or one per (component, z) plane
     const long nparts = std::max<long>(kRedBlocks, 3L * p->N[2]);
@@ -3162,7 +3198,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MOT_ECUDA);
     {   // launch schedule of the batch's products (tuned once per problem and precision)
         const Sched *sc = nullptr;
-        s = mixed ? schedule_for<float>(p, nrhs, &sc) : schedule_for<double>(p, nrhs, &sc);
+        s = inner32 ? schedule_for<float>(p, nrhs, &sc) : schedule_for<double>(p, nrhs, &sc);
         if (s != MOT_OK) return fail(s);
     }
     *out = r;
@@ -3173,7 +3209,7 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
     if (!r) MOT_FAIL(MOT_EINVAL, "run is NULL");
     if (nsteps < 0) MOT_FAIL(MOT_EINVAL, "nsteps < 0");
     MOT_CUDA_TRY(cudaSetDevice(r->p->ctx->device));
-    SchedScope scope(r->p->sched_for(r->B, r->prec == MOT_MIXED));
+    SchedScope scope(r->p->sched_for(r->B, r->prec != MOT_FP64));
     const long n = 3L * r->p->N[0] * r->p->N[1] * r->p->N[2] * r->B;
     mot_status result = MOT_OK;
     // graph mode (default): after one eager step (which sets every kernel's

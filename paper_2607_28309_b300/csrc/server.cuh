@@ -91,7 +91,8 @@ size_t serve_estimate(const ServeJob &j) {
     b += 12 * 6 * (size_t)(M0[2] / 2 + 1) * (M0[1] / 2 + 1) * H0;                        // Lambda0 FP64 + FP32
     b += (size_t)(ell + 1) * 6 * (Mh[2] / 2 + 1) * (Mh[1] / 2 + 1) * Hh * (mixed ? 4 : 8);  // history spectra
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + M0[1]) * H0 * 16;                        // product workspace
-    b += 5 * n3 * 8 + 10 * n3 * (mixed ? 4 : 8) + (mixed ? 2 * n3 * 4 : 0);               // J, b, r, Krylov
+    const bool inner32 = j.precision != MOT_FP64;  // FP32 Krylov vectors (mixed, double-float refined)
+    b += 5 * n3 * 8 + 10 * n3 * (inner32 ? 4 : 8) + (inner32 ? 2 * n3 * 4 : 0);          // J, b, r, Krylov
     const long tb = mixed ? 8 : 4;  // time block of the history: 2 tb partial sums
     b += (size_t)(ell + 1 + 2 * tb) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum, partial sums
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + Mh[1]) * Hh * cs;                       // history workspace

@@ -916,7 +916,14 @@ constexpr int kHistPrefetch = 2;  // lags ahead
 // with prefetch; 2: evict-first loads, no prefetch (a branch beside other work)
 template <int Mode, typename V> __device__ __forceinline__ V hist_ld(const V *p) {
     if constexpr (Mode == 0) return *p;
-    else return __ldcs(p);
+    else if constexpr (std::is_same<V, dfl>::value) {
+        const float2 u = __ldcs(reinterpret_cast<const float2 *>(p));
+        return dfl(u.x, u.y);
+    } else if constexpr (std::is_same<V, dfl2>::value) {
+        const float4 u = __ldcs(reinterpret_cast<const float4 *>(p));
+        return dfl2{dfl(u.x, u.y), dfl(u.z, u.w)};
+    } else
+        return __ldcs(p);
 }
 
 // Time-blocked history (see k_hist_block): the lags 2.. partial sums of the
@@ -1047,13 +1054,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // 32 points stream through a shared-memory pipeline of kHistBlockDepth slots
 // (cp.async, thread group y loading mirror row y), so many slots are in flight
 // without registers and the four groups read each value once from HBM.
+// The two parts can also run as one pass at the block start (kHistAll, fewer
+// bytes: the partial sums are written once and no Lambda_k is read twice).
 // Host-driven: m0 is the block start, [c_lo, c_hi) the chunks of TB.  With
 // nptr (graph mode, beside step *nptr): m = *nptr + dm is the next step, t =
-// m mod TB; the recent part runs only when t == 0 (block m0 = m), the old part
-// takes chunk t of the block after m's (m0 = m - t + TB).
+// m mod TB; the recent part and the whole pass run only when t == 0 (block
+// m0 = m), the old part takes chunk t of the block after m's (m0 = m - t + TB).
 // ---------------------------------------------------------------------------
 constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
-constexpr int kHistOld = 0, kHistRecent = 1;
+constexpr int kHistOld = 0, kHistRecent = 1, kHistAll = 2;  // kHistAll: both parts in one pass at the block start
 
 template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
     return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
@@ -1070,7 +1079,7 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
         const long m = (long)*nptr + dm;
         const int t = (int)(m % TB);
         tlo = 0;
-        if (part == kHistRecent) {
+        if (part != kHistOld) {
             if (t != 0) return;
             m0 = m;
             c_lo = 0;
@@ -1096,10 +1105,11 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
     const int x = threadIdx.x, y = threadIdx.y;
     const int t0 = y * TH;  // this thread's outputs t0 .. t0 + TH - 1
     // inputs J_j for j = m0 - 2 - u: every j >= 0 and within ell of step m0, u < U;
-    // the old part takes u in [TB, U), the recent part u in [0, min(TB, U))
+    // the old part takes u in [TB, U), the recent part u in [0, min(TB, U)), a
+    // whole pass u in [0, U)
     const long U = (m0 - 1 < (long)ell - 1) ? m0 - 1 : (long)ell - 1;
     const long u_lo = part == kHistOld ? TB : 0;
-    const long u_hi = part == kHistOld ? U : (U < TB ? U : (long)TB);
+    const long u_hi = part == kHistRecent ? (U < TB ? U : (long)TB) : U;
     const long nu = u_hi > u_lo ? u_hi - u_lo : 0;
     for (unsigned base = p_lo + blockIdx.x * 32; base < p_hi; base += gridDim.x * 32) {
         const unsigned idx = base + x;
@@ -1764,9 +1774,9 @@ struct EpiResidual {
         double *r;
         const double *eps;
         double dl = 0.0;
-        __device__ __forceinline__ void operator()(int i, double g) const {
+        template <typename G> __device__ __forceinline__ void operator()(int i, G g) const {
             double ep = eps[i];
-            r[i] = b[i] - ((ep * 0.5 + dl) * x[i] - (ep - 1.0) * g);
+            r[i] = b[i] - ((ep * 0.5 + dl) * x[i] - (ep - 1.0) * (double)g);
         }
         __device__ __forceinline__ void prefetch(int i) const {
             prefetch_l2(eps + i);
@@ -1820,9 +1830,9 @@ struct EpiHistory {
         const double *inc, *Jprev, *eps;
         double *out;
         double pol;
-        __device__ __forceinline__ void operator()(int i, double g) const {
+        template <typename G> __device__ __forceinline__ void operator()(int i, G g) const {
             double ep = eps[i];
-            double v = inc[i] * pol + (ep - 1.0) * g;
+            double v = inc[i] * pol + (ep - 1.0) * (double)g;
             if (Jprev) v -= ep * 0.5 * Jprev[i];
             out[i] = v;
         }

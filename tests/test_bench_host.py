@@ -24,6 +24,24 @@ def test_z_pass_and_history_bytes_cube64_a8():
     out = 3 * 64 * 128 * 65 * 8            # the Nz kept planes of the inverse z pass
     # critical path: the step's partial sum + the lag-1 slot + Lambda_1 in, the kept planes out
     assert kb["z_history"] == 2 * slot + lam_h + out
+    # step 40 is the first of a time block (40 mod 8 = 0): the block pass reads the
+    # 25 ring slots within ell of it and Lambda_2..Lambda_26 once, writes 8 partial sums
+    assert kb["hist_side"] == 25 * slot + 25 * lam_h + 8 * slot
+    # step 43 (t = 3): near lags 2..4 onto its partial sum
+    assert bench.kernel_bytes(INFO, N, 1, 1, [43])["hist_side"] == 3 * (slot + lam_h) + 2 * slot
+    # averaged over a whole block (steps 40..47): one block pass, near lags 1+2+...+7 = 28,
+    # seven near read-modify-writes of a partial sum; less than half the direct sum's
+    # 26 (slot + Lambda) per step
+    kb8 = bench.kernel_bytes(INFO, N, 1, 1, list(range(40, 48)))
+    assert kb8["hist_side"] * 8 == 25 * slot + 25 * lam_h + 8 * slot + 28 * (slot + lam_h) + 7 * 2 * slot
+    assert kb8["hist_side"] + kb8["z_history"] - out < 26 * (slot + lam_h) / 2
+
+
+def test_spread_history_schedule_bytes_cube64_a8():
+    slot = 3 * 128 * 128 * 65 * 8
+    lam_h = 6 * 65 ** 3 * 4
+    out = 3 * 64 * 128 * 65 * 8
+    kb = bench.kernel_bytes(INFO, N, 1, 1, [40], spread=True)
     # step 40 is the first of a time block (40 mod 8 = 0): the recent part of the block
     # reads the 8 newest of the 25 ring slots within ell of it (ages 0..7) and
     # Lambda_2..Lambda_16, and reads and writes the block's 8 partial sums; and one
@@ -32,11 +50,11 @@ def test_z_pass_and_history_bytes_cube64_a8():
     old48 = (17 * slot + 17 * lam_h + 8 * slot) / 8
     assert kb["hist_side"] == 8 * slot + 15 * lam_h + 16 * slot + old48
     # step 43 (t = 3): near lags 2..4 onto its partial sum, and its chunk of block 48's old part
-    assert bench.kernel_bytes(INFO, N, 1, 1, [43])["hist_side"] == 3 * (slot + lam_h) + 2 * slot + old48
+    assert bench.kernel_bytes(INFO, N, 1, 1, [43], spread=True)["hist_side"] == 3 * (slot + lam_h) + 2 * slot + old48
     # averaged over a whole block (steps 40..47): the recent part once, the next block's
     # old part once, near lags 1+2+...+7 = 28, seven near read-modify-writes of a
     # partial sum; less than half the direct sum's 26 (slot + Lambda) per step
-    kb8 = bench.kernel_bytes(INFO, N, 1, 1, list(range(40, 48)))
+    kb8 = bench.kernel_bytes(INFO, N, 1, 1, list(range(40, 48)), spread=True)
     assert abs(kb8["hist_side"] * 8 - (8 * slot + 15 * lam_h + 16 * slot + 8 * old48 + 28 * (slot + lam_h)
                                        + 7 * 2 * slot)) < 1e-6 * kb8["hist_side"]
     assert kb8["hist_side"] + kb8["z_history"] - out < 26 * (slot + lam_h) / 2

@@ -37,7 +37,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b, axis=1).max() / max(np.linalg.norm(b, axis=1).max(), 1e-300))
 
 
-@pytest.mark.parametrize("precision", [mot.MOT_FP64, mot.MOT_MIXED])
+@pytest.mark.parametrize("precision", [mot.MOT_FP64, mot.MOT_MIXED, mot.MOT_FP64DF])
 def test_resume_matches_uninterrupted(ctx, tmp_path, precision):
     N = (10, 9, 8)
     eps = synthetic.block_eps(N, 3, 2.0, 5.0, 3)

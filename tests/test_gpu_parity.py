@@ -9,6 +9,8 @@ Tolerances (relative L2 unless stated):
 - FP64 march vs the oracle march (exact solve), per step, scaled
   by max_n ||J_n||:                                                1e-9
 - mixed FP32/FP64 march vs the oracle, same scaling:               1e-5
+- double-float refined march (FP32 inner solves, double-float
+  residual and history) vs the oracle, same scaling:              1e-9
 """
 import math
 
@@ -122,6 +124,9 @@ def test_mot_small_fp64_and_mixed(ctx, orc):
     assert e64.max() <= 1e-9, e64.max()
     e32 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_MIXED), Jo)
     assert e32.max() <= 1e-5, e32.max()
+    edf = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64DF), Jo)
+    print("FP64 / mixed / double-float march errors", e64.max(), e32.max(), edf.max())
+    assert edf.max() <= 1e-9, edf.max()
 
 
 def test_mot_oblique_batch(ctx, orc):
@@ -132,6 +137,8 @@ def test_mot_oblique_batch(ctx, orc):
     Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
     e64 = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64), Jo)
     assert e64.max() <= 1e-9, e64.max()
+    edf = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, mot.MOT_FP64DF), Jo)
+    assert edf.max() <= 1e-9, edf.max()
 
 
 def test_step_drivers_agree(ctx, orc):
@@ -143,7 +150,7 @@ def test_step_drivers_agree(ctx, orc):
     alpha, steps = 8.0, 14
     exc = [synthetic.pulse(steps, alpha)]
     Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
-    for precision, tol in ((mot.MOT_FP64, 1e-9), (mot.MOT_MIXED, 1e-5)):
+    for precision, tol in ((mot.MOT_FP64, 1e-9), (mot.MOT_MIXED, 1e-5), (mot.MOT_FP64DF, 1e-9)):
         J = {g: _march_pair(ctx, orc, N, eps, alpha, exc, steps, precision, mot.default_options(graph=g))
              for g in (0, 1, 2)}
         for g in (0, 1, 2):
@@ -162,7 +169,7 @@ def test_steps_in_several_calls_match_one_call(ctx):
     alpha, steps = 8.0, 16
     exc = [synthetic.pulse(steps, alpha)]
     nv = int(np.prod(N))
-    for precision in (mot.MOT_FP64, mot.MOT_MIXED):
+    for precision in (mot.MOT_FP64, mot.MOT_MIXED, mot.MOT_FP64DF):
         prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
         try:
             J = {}

@@ -130,6 +130,16 @@ def test_step_equation_at_full_size(ctx, orc, which):
     print(f"{which} mixed step-equation residuals", r32)
     assert max(r32) <= 1e-5, r32
 
+    if which == "cube64_a8":
+        # the double-float refined march holds the FP64 path's residual
+        Jdf, _ = _march(ctx, w, mot.MOT_FP64DF, nsteps, keep)
+        rdf = _step_residuals(orc, w, tables, Jdf, keep, steps, rng)
+        print(f"{which} double-float step-equation residuals", rdf)
+        assert max(rdf) <= 1e-9, rdf
+        ddf = np.linalg.norm((Jdf - J64).reshape(nsteps, -1), axis=1).max()
+        print(f"{which} double-float vs FP64 march: max relative L2 per step",
+              ddf / np.linalg.norm(J64.reshape(nsteps, -1), axis=1).max())
+
     # the mixed path's relative L2 error against the FP64 path, per step
     d = J32.reshape(nsteps, -1) - J64.reshape(nsteps, -1)
     scale = np.linalg.norm(J64.reshape(nsteps, -1), axis=1).max()
