@@ -317,7 +317,7 @@ def kernel_bytes(info, N, B, prec, steps, TB=None, spread=None):
 
 # the headers that hold the kernels (host-only sources such as the server are left out)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2607_28309_b300", "csrc", f)
-                  for f in ("common.cuh", "fft.cuh", "krylov.cuh", "spectral.cuh")]
+                  for f in ("common.cuh", "dfloat.cuh", "fft.cuh", "krylov.cuh", "spectral.cuh")]
 
 
 def kernel_digest():
