@@ -747,7 +747,8 @@ bool x_forward_r_go(const TI *x, cplx<T> *out, long nrows, int Nx, AxisTw *tw, c
     constexpr size_t smem = x_r_smem<T, R1, R2, P>();
     if (smem > kSmemMax || allow_smem<k_x_forward_r<TI, T, R1, R2, P>>() != MOT_OK) return false;
     count_launch();
-    k_x_forward_r<TI, T, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(x, out, Nx, twp<T>(tw));
+    launch_chain(k_x_forward_r<TI, T, R1, R2, P>, dim3((unsigned)(nrows / (2 * P))), dim3(P * R2), smem, st, x, out,
+                 Nx, twp<T>(tw));
     return true;
 }
 
@@ -756,8 +757,8 @@ bool x_inverse_r_go(const cplx<T> *in, long nrows, int Nx, int Ny, int Nz, AxisT
     constexpr size_t smem = x_r_smem<T, R1, R2, P>();
     if (smem > kSmemMax || allow_smem<k_x_inverse_r<T, Epi, R1, R2, P>>() != MOT_OK) return false;
     count_launch();
-    k_x_inverse_r<T, Epi, R1, R2, P><<<(unsigned)(nrows / (2 * P)), P * R2, smem, st>>>(in, Nx, Ny, Nz, twp<T>(tw),
-                                                                                        epi);
+    launch_chain(k_x_inverse_r<T, Epi, R1, R2, P>, dim3((unsigned)(nrows / (2 * P))), dim3(P * R2), smem, st, in, Nx,
+                 Ny, Nz, twp<T>(tw), epi);
     return true;
 }
 
@@ -768,8 +769,8 @@ bool col_r_go(const cplx<T> *in, cplx<T> *out, AxisTw *tw, int H, int Lin, int L
     const size_t smem = (size_t)(M + TC * (M + 1)) * sizeof(cplx<T>);
     if (smem > kSmemMax || allow_smem<k_col_r<T, S, R1, R2, TC>>() != MOT_OK) return false;
     count_launch();
-    k_col_r<T, S, R1, R2, TC><<<dim3((H + TC - 1) / TC, planes), TC * R2, smem, st>>>(in, out, twp<T>(tw), H, Lin, Lout,
-                                                                                      ips, ops, nptr, ell, slot_stride);
+    launch_chain(k_col_r<T, S, R1, R2, TC>, dim3((H + TC - 1) / TC, planes), dim3(TC * R2), smem, st, in, out,
+                 twp<T>(tw), H, Lin, Lout, ips, ops, nptr, ell, slot_stride);
     return true;
 }
 
@@ -2451,7 +2452,7 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, int pa
     if (r->hTB != (sizeof(T) == 4 ? 8 : 4)) MOT_FAIL(MOT_EINVAL, "time block does not match the history precision");
     // time block 8 (FP32) with two outputs per thread, 4 (FP64) with one: four thread groups
     constexpr int TB = sizeof(T) == 4 ? 8 : 4, TH = TB / 4;
-    constexpr size_t smem = hist_block_smem<T>();
+    constexpr size_t smem = hist_block_smem<T, TB>();
     MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
     count_launch();
     k_hist_block<T, TB, TH><<<grid, dim3(32, 4), smem, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,
