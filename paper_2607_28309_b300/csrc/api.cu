@@ -2452,7 +2452,7 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, int pa
     if (r->hTB != (sizeof(T) == 4 ? 8 : 4)) MOT_FAIL(MOT_EINVAL, "time block does not match the history precision");
     // time block 8 (FP32) with two outputs per thread, 4 (FP64) with one: four thread groups
     constexpr int TB = sizeof(T) == 4 ? 8 : 4, TH = TB / 4;
-    constexpr size_t smem = hist_block_smem<T, TB>();
+    constexpr size_t smem = hist_block_smem<T>();
     MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
     count_launch();
     k_hist_block<T, TB, TH><<<grid, dim3(32, 4), smem, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B,

@@ -1053,10 +1053,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // thread groups of TH outputs (block (32, 4)).  The ring values of the block's
 // 32 points stream through a shared-memory pipeline of kHistBlockDepth slots
 // (cp.async, thread group y loading mirror row y), so many slots are in flight
-// without registers and the four groups read each value once from HBM; the
-// Lambda_k the pipelined slots need stream beside them into a ring of
-// TB + D - 1 lags in shared memory (one new lag per slot), read from there by
-// all four groups.
+// without registers and the four groups read each value once from HBM.
 // The two parts can also run as one pass at the block start (kHistAll, fewer
 // bytes: the partial sums are written once and no Lambda_k is read twice).
 // Host-driven: m0 is the block start, [c_lo, c_hi) the chunks of TB.  With
@@ -1067,11 +1064,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
 constexpr int kHistOld = 0, kHistRecent = 1, kHistAll = 2;  // kHistAll: both parts in one pass at the block start
 
-// lags staged per block: the TB + D - 1 Lambda_k from the oldest one a slot in
-// the pipeline still needs to the newest one issued
-template <int TB> __host__ __device__ constexpr int hist_block_lags() { return TB + kHistBlockDepth - 1; }
-template <typename T, int TB> __host__ __device__ constexpr size_t hist_block_smem() {
-    return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>) + (size_t)hist_block_lags<TB>() * 6 * 32 * sizeof(T);
+template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
+    return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
 }
 
 template <typename T, int TB, int TH>
@@ -1097,10 +1091,8 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
         }
     }
     using C = cplx<T>;
-    constexpr int LR = hist_block_lags<TB>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);          // [D][row 4][component 3][point 32]
-    T *lring = reinterpret_cast<T *>(buf + D * 4 * 3 * 32);  // [LR][component 6][point 32]
+    C *buf = reinterpret_cast<C *>(smem_raw);  // [D][row 4][component 3][point 32]
     const int hz = Mz / 2 + 1, hy = My / 2 + 1;
     const unsigned total = (unsigned)nrhs * hz * hy * H;
     const unsigned p_lo = (unsigned)((unsigned long long)total * c_lo / TB);
@@ -1142,41 +1134,22 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];
             Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
         }
-        // loader: thread (x, y) copies mirror row y of point x, three components, per slot,
-        // and components y and y + 4 (< 6) of point x's Lambda_k, per lag
+        // loader: thread (x, y) copies mirror row y of point x, three components, per slot
         const long my_off = y == 0 ? off[0] : y == 1 ? off[1] : y == 2 ? off[2] : off[3];
         long s_issue = ((m0 - 2 - u_lo) % ell + ell) % ell;  // ring slot of the next slot to load (wrapping)
-        // lag k sits at lring[(k - u_lo - 2) mod LR]
-        auto issue_lag = [&](long k) {
-            T *dst = lring + (int)((k - u_lo - 2) % LR) * 6 * 32 + x;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int c6 = y + 4 * c;
-                if (c6 < 6) {
-                    if (valid && k <= ell) cp_async_elem(dst + c6 * 32, Lp + k * 6 * cs + c6 * cs);
-                    else dst[c6 * 32] = T(0);  // made visible by the barrier before its first use
-                }
-            }
-        };
         auto issue = [&](int bslot) {
             if (valid) {
                 const C *R = ring + s_issue * slot_size + my_off;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) cp_async_elem(buf + ((bslot * 4 + y) * 3 + q) * 32 + x, R + q * slot_comp);
             }
+            asm volatile("cp.async.commit_group;\n" ::);
             s_issue = s_issue == 0 ? ell - 1 : s_issue - 1;
         };
-        // the lags of the first slot (u_lo + 2 .. u_lo + TB), then per pipelined slot w
-        // its newest lag u_lo + w + TB + 1, in the same commit group as the slot
-#pragma unroll 1
-        for (long k = u_lo + 2; k <= u_lo + TB; ++k) issue_lag(k);
 #pragma unroll 1
         for (int i = 0; i < D - 1; ++i) {
-            if (i < nu) {
-                issue(i);
-                issue_lag(u_lo + i + TB + 1);
-            }
-            asm volatile("cp.async.commit_group;\n" ::);
+            if (i < nu) issue(i);
+            else asm volatile("cp.async.commit_group;\n" ::);
         }
         C a[TH][4][3];
 #pragma unroll
@@ -1185,40 +1158,58 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) a[i][r][q] = cmake<C>(T(0), T(0));
-        for (long w = 0; w < nu; ++w) {
-            const long u = u_lo + w;
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot w and its lag landed
-            __syncthreads();  // ... for every thread; and slot w - 1's buffers are free again
-            const int bs = (int)(w % D);
-            C uv[4][3];
+        // window: at walk position w (u = u_lo + w), output t0 + i needs lag
+        // k = u + 2 + t0 + i, held in lw[(w + i) mod TH]; before the walk lw[i]
+        // holds lag u_lo + 2 + t0 + i
+        T lw[TH][6];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+        for (int i = 0; i < TH; ++i) {
+            const long k = u_lo + 2 + t0 + i;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) uv[r][q] = buf[((bs * 4 + r) * 3 + q) * 32 + x];
-            if (w + D - 1 < nu) {
-                issue((int)((w + D - 1) % D));
-                issue_lag(u + D - 1 + TB + 1);
-            }
-            asm volatile("cp.async.commit_group;\n" ::);
+            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = (valid && k <= ell) ? Lp[k * 6 * cs + c6 * cs] : T(0);
+        }
+        for (long w0 = 0; w0 < nu; w0 += TH) {
+            // fully unrolled with a guard (uniform over the block) rather than a break: the
+            // window index (ww + i) % TH stays a compile-time constant, lw and a in registers
 #pragma unroll
-            for (int i = 0; i < TH; ++i) {
-                const long k = u + 2 + t0 + i;
-                if (t0 + i >= tlo && k <= ell) {
-                    const T *gl = lring + (int)((k - u_lo - 2) % LR) * 6 * 32 + x;
-                    const T g[6] = {gl[0], gl[32], gl[64], gl[96], gl[128], gl[160]};
-                    const T gxx = g[0], gyy = g[1], gzz = g[2];
+            for (int ww = 0; ww < TH; ++ww) {
+                const long w = w0 + ww, u = u_lo + w;
+                if (w < nu) {
+                    asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot w landed
+                    __syncthreads();  // ... for every thread; and slot w - 1's buffer is free again
+                    const int bs = (int)(w % D);
+                    C uv[4][3];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
-                        const T exy = sy * g[3], exz = sz * g[4], eyz = sy * sz * g[5];
-                        const C u0v = uv[r][0], u1v = uv[r][1], u2v = uv[r][2];
-                        a[i][r][0] = cmake<C>(a[i][r][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
-                                              a[i][r][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
-                        a[i][r][1] = cmake<C>(a[i][r][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
-                                              a[i][r][1].y + exy * u0v.y + gyy * u1v.y + eyz * u2v.y);
-                        a[i][r][2] = cmake<C>(a[i][r][2].x + exz * u0v.x + eyz * u1v.x + gzz * u2v.x,
-                                              a[i][r][2].y + exz * u0v.y + eyz * u1v.y + gzz * u2v.y);
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) uv[r][q] = buf[((bs * 4 + r) * 3 + q) * 32 + x];
+                    if (w + D - 1 < nu) issue((int)((w + D - 1) % D));
+                    else asm volatile("cp.async.commit_group;\n" ::);
+#pragma unroll
+                    for (int i = 0; i < TH; ++i) {
+                        const long k = u + 2 + t0 + i;
+                        if (t0 + i >= tlo && k <= ell) {
+                            const T *g = lw[(ww + i) % TH];
+                            const T gxx = g[0], gyy = g[1], gzz = g[2];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
+                                const T exy = sy * g[3], exz = sz * g[4], eyz = sy * sz * g[5];
+                                const C u0v = uv[r][0], u1v = uv[r][1], u2v = uv[r][2];
+                                a[i][r][0] = cmake<C>(a[i][r][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
+                                                      a[i][r][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
+                                a[i][r][1] = cmake<C>(a[i][r][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
+                                                      a[i][r][1].y + exy * u0v.y + gyy * u1v.y + eyz * u2v.y);
+                                a[i][r][2] = cmake<C>(a[i][r][2].x + exz * u0v.x + eyz * u1v.x + gzz * u2v.x,
+                                                      a[i][r][2].y + exz * u0v.y + eyz * u1v.y + gzz * u2v.y);
+                            }
+                        }
                     }
+                    // lw[ww] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
+                    const long kn = u + 2 + t0 + TH;
+#pragma unroll
+                    for (int c6 = 0; c6 < 6; ++c6)
+                        lw[ww][c6] = (valid && kn <= ell) ? Lp[kn * 6 * cs + c6 * cs] : T(0);
                 }
             }
         }
