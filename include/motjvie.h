@@ -276,9 +276,13 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
                           mot_run **out);
 
 /* Advance nsteps time steps (Eq. 3): b_n = E^i_n - sum_{k=1..ell} Z_k J_{n-k},
- * then Z0 J_n = b_n by TFQMR (x0 = J_{n-1}).  J_out (host, nullable) receives
- * [nsteps][nrhs][3][Nz][Ny][Nx] doubles in A/m^2; stats (nullable) receives
- * nsteps entries.  Synchronous when J_out or stats is given.
+ * then Z0 J_n = b_n by TFQMR (x0 from options.guess).  J_out (host, nullable)
+ * receives [nsteps][nrhs][3][Nz][Ny][Nx] doubles in A/m^2 (in graph mode each
+ * J_n goes through a device staging buffer and reaches the host on its own
+ * stream while the next step runs: page-locked J_out memory lets the copies
+ * overlap the steps); stats (nullable) receives nsteps entries.  Synchronous
+ * when J_out or stats is given; the first J_out use in graph mode allocates
+ * two staging buffers of nrhs*3*n doubles.
  * Errors: MOT_EINVAL, MOT_ENOTCONV (state still advanced), MOT_ECUDA.         */
 mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *stats);
 

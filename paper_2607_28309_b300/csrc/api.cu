@@ -24,6 +24,7 @@
 
 #include <atomic>
 #include <memory>
+#include <chrono>
 #include <mutex>
 
 namespace mot {
@@ -279,6 +280,23 @@ void lag_map(const ItemSet &is, int k, std::vector<int> &map) {
 
 int lag_reach(int k, double rho) { return gk::reach(k, rho); }
 
+// set-up phase timings on stderr when MOTJVIE_TRACE=1 (profiling the set-up)
+struct PhaseTrace {
+    const char *what;
+    std::chrono::steady_clock::time_point t0;
+    static bool on() {
+        static const bool f = getenv("MOTJVIE_TRACE") && atoi(getenv("MOTJVIE_TRACE")) != 0;
+        return f;
+    }
+    explicit PhaseTrace(const char *w) : what(w), t0(std::chrono::steady_clock::now()) {}
+    ~PhaseTrace() {
+        if (!on()) return;
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        fprintf(stderr, "[motjvie] %s: %.1f ms\n", what, ms);
+    }
+};
+
 // cos / sin coefficient tables of one axis: [K][R+1]
 void axis_coef(int M, int R, bool odd, std::vector<double> &cf) {
     const double pi = 3.141592653589793238462643383279502884;
@@ -500,6 +518,11 @@ struct mot_run {
     DBuf r32;  // mixed: residual in FP32 / correction
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> sev;  // graph mode: start/end event of each step of a chunk
+    // graph mode with J_out: J_n is copied on the device into one of two staging
+    // buffers and from there to the host on its own stream, beside the next step
+    DBuf jstage[2];
+    cudaStream_t jcopy = nullptr;
+    cudaEvent_t jready[2] = {nullptr, nullptr}, jdone[2] = {nullptr, nullptr};
     // whole-step graph (graph mode)
     cudaStream_t cap2 = nullptr, cap3 = nullptr;
     cudaGraph_t step_graph = nullptr;
@@ -1351,8 +1374,13 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
     int rmax = lag_reach(k1, p->rho);
     for (int i = 0; i < 3; ++i) S[i] = std::min(S[i], rmax);
     ItemSet is;
-    if (!build_items(p->rho, S, k0, k1, is))
-        MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (alpha < 0.5)");
+    PhaseTrace tr_all("lag tables (items, quadrature or cache, octants)");
+    bool items_ok;
+    {
+        PhaseTrace tr_items("lag-table items (host)");
+        items_ok = build_items(p->rho, S, k0, k1, is);
+    }
+    if (!items_ok) MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (alpha < 0.5)");
     const int nit = (int)is.items.size();
     DBuf dA, dmap;
     MOT_TRY(dalloc(dA, sizeof(double) * 6 * std::max(1, nit)));
@@ -1397,7 +1425,14 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         dfree(dFM);
         dfree(dBM);
     }
-    std::vector<int> map;
+    // each lag's item map is formed on the device from the per-offset item ranges
+    const long n3 = (long)is.base.size();
+    DBuf drange;
+    MOT_TRY(dalloc(drange, sizeof(int) * 3 * n3));
+    int *dbase = (int *)drange.p, *dklo = dbase + n3, *dcnt = dklo + n3;
+    MOT_CUDA_TRY(cudaMemcpyAsync(dbase, is.base.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(dklo, is.klo.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(dcnt, is.cnt.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
     for (int k = k0; k <= k1; ++k) {
         LagTable &L = p->lags[k];
         if (L.override_) continue;
@@ -1405,24 +1440,30 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         for (int i = 0; i < 3; ++i) L.R[i] = std::min(rk, ext[i]);
         long n = (long)(L.R[0] + 1) * (L.R[1] + 1) * (L.R[2] + 1);
         MOT_TRY(dalloc(L.oct, sizeof(double) * 6 * n));
-        lag_map(is, k, map);
-        MOT_CUDA_TRY(cudaMemcpyAsync(dmap.p, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, st));
+        count_launch();
+        k_lag_map<<<grid_for(n3), 256, 0, st>>>(dbase, dklo, dcnt, n3, k, (int *)dmap.p);
         count_launch();
         k_expand_octant<<<grid_for(n), 256, 0, st>>>((const double *)dA.p, (const int *)dmap.p, is.Rm, L.R[0],
                                                      L.R[1], L.R[2], (double *)L.oct.p);
         MOT_CHECK_LAUNCH();
-        // map is reused by the next lag: wait for the copy before host reuse
-        MOT_CUDA_TRY(cudaStreamSynchronize(st));
         L.ready = true;
     }
     MOT_CUDA_TRY(cudaStreamSynchronize(st));
     dfree(dA);
     dfree(dmap);
+    dfree(drange);
     return MOT_OK;
 }
 
 // Lambda of one lag octant on grid M (K = M/2+1), FP64, into dst64 [6][Kz][Ky][Kx]
-mot_status lag_spectrum(mot_problem *p, const LagTable &L, const int M[3], double *dst64) {
+// Lambda of one lag table: three separable passes over the octant (section on
+// tables.cuh).  df: the passes as double-float matrix products (k_gemm_df,
+// relative error about 1e-14, several times the FP64 rate of this GPU); else
+// plain FP64 sums.  The history lags take df, Lambda0 (the product's own
+// spectrum) FP64; MOTJVIE_SPECTRA_FP64=1 keeps every lag in FP64.
+mot_status lag_spectrum(mot_problem *p, const LagTable &L, const int M[3], double *dst64, bool df = false) {
+    static const bool force64 = getenv("MOTJVIE_SPECTRA_FP64") && atoi(getenv("MOTJVIE_SPECTRA_FP64")) != 0;
+    if (force64) df = false;
     cudaStream_t st = p->ctx->stream;
     int K[3] = {M[0] / 2 + 1, M[1] / 2 + 1, M[2] / 2 + 1};
     int R1[3] = {L.R[0] + 1, L.R[1] + 1, L.R[2] + 1};
@@ -1450,6 +1491,24 @@ mot_status lag_spectrum(mot_problem *p, const LagTable &L, const int M[3], doubl
         const double *cx = (const double *)(par[c][0] ? dco[0].p : dce[0].p);
         const double *cy = (const double *)(par[c][1] ? dco[1].p : dce[1].p);
         const double *cz = (const double *)(par[c][2] ? dco[2].p : dce[2].p);
+        if (df) {
+            const double s = c >= 3 ? -scale : scale;
+            const int M1 = R1[2] * R1[1];
+            count_launch();
+            k_gemm_df<<<dim3((K[0] + 63) / 64, (M1 + 63) / 64, 1), 256, 0, st>>>(
+                GemmView{src, 0, R1[0], 1}, GemmView{cx, 0, 1, R1[0]}, (double *)t1.p, 0, K[0], 1, M1, K[0], R1[0], 1.0);
+            count_launch();
+            k_gemm_df<<<dim3((K[0] + 63) / 64, (K[1] + 63) / 64, R1[2]), 256, 0, st>>>(
+                GemmView{cy, 0, R1[1], 1}, GemmView{(const double *)t1.p, (long)R1[1] * K[0], K[0], 1}, (double *)t2.p,
+                (long)K[1] * K[0], K[0], 1, K[1], K[0], R1[1], 1.0);
+            const int NN = K[1] * K[0];
+            count_launch();
+            k_gemm_df<<<dim3((NN + 63) / 64, (K[2] + 63) / 64, 1), 256, 0, st>>>(
+                GemmView{cz, 0, R1[2], 1}, GemmView{(const double *)t2.p, 0, NN, 1}, dst64 + c * kn, 0, NN, 1, K[2], NN,
+                R1[2], s);
+            MOT_CHECK_LAUNCH();
+            continue;
+        }
         long n1 = (long)R1[2] * R1[1] * K[0];
         count_launch();
         k_axis_sum<<<grid_for(n1), 256, 0, st>>>(src, (double *)t1.p, cx, R1[2] * R1[1], R1[0], K[0], 1);
@@ -1572,6 +1631,7 @@ mot_status build_history_spectra(mot_problem *p, int kind) {
     for (int k = 1; k <= p->ell; ++k)
         if (!p->lags[k].ready) need_oct = true;
     if (need_oct) MOT_TRY(compute_lag_octants(p, 1, p->ell));
+    PhaseTrace tr_spec("history spectra");
     long kn = (long)p->Kh[0] * p->Kh[1] * p->Kh[2];
     size_t per = 6 * (size_t)kn;
     const size_t es = kind == kSpec32 ? sizeof(float) : sizeof(double);  // a dfl is 8 bytes too
@@ -1581,7 +1641,7 @@ mot_status build_history_spectra(mot_problem *p, int kind) {
     MOT_CUDA_TRY(cudaMemsetAsync(buf.p, 0, es * per, p->ctx->stream));
     for (int k = 1; k <= p->ell; ++k) {
         double *dst = kind == kSpec64 ? (double *)buf.p + per * k : (double *)tmp.p;
-        MOT_TRY(lag_spectrum(p, p->lags[k], p->Mh, dst));
+        MOT_TRY(lag_spectrum(p, p->lags[k], p->Mh, dst, true));
         if (kind == kSpec32) {
             count_launch();
             k_scale_store<float><<<grid_for(per), 256, 0, p->ctx->stream>>>(dst, (float *)buf.p + per * k, per, 1.0);
@@ -3086,6 +3146,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
             MOT_FAIL(MOT_EINVAL, "plane wave: sigma must be > 0 and all parameters finite");
     }
     MOT_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    PhaseTrace tr_run("run creation");
     const bool mixed = precision == MOT_MIXED;
     const bool inner32 = precision != MOT_FP64;  // FP32 inner solves refined against an outer residual
     MOT_TRY(build_history_spectra(p, mixed ? kSpec32 : precision == MOT_FP64DF ? kSpecDF : kSpec64));
@@ -3206,6 +3267,17 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     return MOT_OK;
 }
 
+// the staging buffers, copy stream and events of the overlapped J_n copies
+mot_status jcopy_setup(mot_run *r, long n) {
+    for (int b = 0; b < 2; ++b) {
+        if (!r->jstage[b].p) MOT_TRY(dalloc(r->jstage[b], sizeof(double) * n));
+        if (!r->jready[b]) MOT_CUDA_TRY(cudaEventCreateWithFlags(&r->jready[b], cudaEventDisableTiming));
+        if (!r->jdone[b]) MOT_CUDA_TRY(cudaEventCreateWithFlags(&r->jdone[b], cudaEventDisableTiming));
+    }
+    if (!r->jcopy) MOT_CUDA_TRY(cudaStreamCreateWithFlags(&r->jcopy, cudaStreamNonBlocking));
+    return MOT_OK;
+}
+
 mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *stats) {
     if (!r) MOT_FAIL(MOT_EINVAL, "run is NULL");
     if (nsteps < 0) MOT_FAIL(MOT_EINVAL, "nsteps < 0");
@@ -3234,19 +3306,30 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
                 MOT_CUDA_TRY(cudaEventCreate(&e));
                 r->sev.push_back(e);
             }
+            if (J_out) MOT_TRY(jcopy_setup(r, n));
             for (int i = 0; i < chunk; ++i) {
                 const int sidx = done + i;
                 if (stats) MOT_CUDA_TRY(cudaEventRecord(r->sev[2 * i], st));
                 MOT_CUDA_TRY(cudaGraphLaunch(r->step_exec, st));
                 r->n += 1;
                 if (stats) MOT_CUDA_TRY(cudaEventRecord(r->sev[2 * i + 1], st));
-                if (J_out)
-                    MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)sidx * n, r->J.p, sizeof(double) * n,
-                                                 cudaMemcpyDeviceToHost, st));
+                if (J_out) {
+                    // J_n to a staging buffer (free once its previous host copy is done), then
+                    // to the host on the copy stream while the next step runs
+                    const int b = sidx & 1;
+                    if (sidx >= 2) MOT_CUDA_TRY(cudaStreamWaitEvent(st, r->jdone[b], 0));
+                    MOT_CUDA_TRY(cudaMemcpyAsync(r->jstage[b].p, r->J.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+                    MOT_CUDA_TRY(cudaEventRecord(r->jready[b], st));
+                    MOT_CUDA_TRY(cudaStreamWaitEvent(r->jcopy, r->jready[b], 0));
+                    MOT_CUDA_TRY(cudaMemcpyAsync(J_out + (size_t)sidx * n, r->jstage[b].p, sizeof(double) * n,
+                                                 cudaMemcpyDeviceToHost, r->jcopy));
+                    MOT_CUDA_TRY(cudaEventRecord(r->jdone[b], r->jcopy));
+                }
             }
             std::vector<StepStatDev> hs(chunk);
             MOT_CUDA_TRY(cudaMemcpyAsync(hs.data(), r->sstats.p, sizeof(StepStatDev) * chunk, cudaMemcpyDeviceToHost, st));
             MOT_CUDA_TRY(cudaStreamSynchronize(st));
+            if (J_out) MOT_CUDA_TRY(cudaStreamSynchronize(r->jcopy));
             for (int i = 0; stats && i < chunk; ++i) {
                 mot_step_stats &S = stats[done + i];
                 memset(&S, 0, sizeof(S));
@@ -3541,6 +3624,15 @@ void mot_run_destroy(mot_run *r) {
     for (int i = 0; i < 4; ++i)
         if (r->ev[i]) cudaEventDestroy(r->ev[i]);
     for (cudaEvent_t e : r->sev) cudaEventDestroy(e);
+    if (r->jcopy) {
+        cudaStreamSynchronize(r->jcopy);
+        cudaStreamDestroy(r->jcopy);
+    }
+    for (int b = 0; b < 2; ++b) {
+        dfree(r->jstage[b]);
+        if (r->jready[b]) cudaEventDestroy(r->jready[b]);
+        if (r->jdone[b]) cudaEventDestroy(r->jdone[b]);
+    }
     for (LoopGraph *G : {&r->loop64, &r->loop32}) {
         if (G->exec) cudaGraphExecDestroy(G->exec);
         if (G->graph) cudaGraphDestroy(G->graph);

@@ -68,6 +68,17 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
     dfop::fast_two_sum(p, e, h, l);
     return dfl(h, l);
 }
+// the accurate double-word sum (their Algorithm 6: both pairs through TwoSum,
+// two renormalisations): relative error below about 2^-46 even under
+// cancellation, for long accumulations whose terms differ in sign
+__device__ __forceinline__ dfl add_accurate(dfl a, dfl b) {
+    float sh, sl, th, tl, vh, vl, zh, zl;
+    dfop::two_sum(a.hi, b.hi, sh, sl);
+    dfop::two_sum(a.lo, b.lo, th, tl);
+    dfop::fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
+    dfop::fast_two_sum(vh, __fadd_rn(tl, vl), zh, zl);
+    return dfl(zh, zl);
+}
 __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
 __device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = a * b; }

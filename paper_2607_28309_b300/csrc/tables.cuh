@@ -131,6 +131,16 @@ __host__ __device__ inline void expand_one(const double *A6, const int *map, int
     }
 }
 
+// the item index of lag k for every sorted offset (dense key), -1 where lag k
+// has no item: map = base + (k - klo) for klo <= k < klo + cnt
+__global__ void k_lag_map(const int *__restrict__ base, const int *__restrict__ klo, const int *__restrict__ cnt,
+                          long n, int k, int *__restrict__ map) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int b = base[i], lo = klo[i];
+        map[i] = (b >= 0 && k >= lo && k < lo + cnt[i]) ? b + (k - lo) : -1;
+    }
+}
+
 __global__ void k_expand_octant(const double *__restrict__ A6, const int *__restrict__ map, int Rm, int Rx, int Ry,
                                 int Rz, double *__restrict__ oct) {
     long n = (long)(Rx + 1) * (Ry + 1) * (Rz + 1);
@@ -156,6 +166,62 @@ __global__ void k_axis_sum(const double *__restrict__ in, double *__restrict__ o
         for (int d = 0; d < Rin; ++d) acc += cf[d] * src[(long)d * ninner];
         out[t] = acc;
     }
+}
+
+// batched C = s A B in double-float arithmetic on FP64 data, for the separable
+// transforms of the history spectra (each pass a product of a coefficient
+// matrix and a stack of table lines).  Element (m, k) of batch z of A is at
+// A + z sAz + m sAm + k sAk (B and C alike).  64 x 64 outputs per block of 256
+// threads, 4 x 4 per thread, K in chunks of 16 staged in shared memory as
+// (hi, lo) pairs; products by the double-word product, sums by the accurate
+// double-word sum.  grid (ceil(N/64), ceil(M/64), batches)
+struct GemmView {
+    const double *p;
+    long sz, sr, sc;  // batch, row, column strides (elements)
+};
+__global__ void __launch_bounds__(256) k_gemm_df(GemmView A, GemmView B, double *__restrict__ C, long sCz, long sCm,
+                                                 long sCn, int M, int N, int K, double s) {
+    __shared__ dfl As[16][64 + 1];
+    __shared__ dfl Bs[16][64 + 1];
+    const int z = blockIdx.z, m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const double *Ab = A.p + z * A.sz, *Bb = B.p + z * B.sz;
+    dfl acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = dfl(0.0f, 0.0f);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int kk = e / 64, mm = e % 64;
+            const int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? to_dfl(Ab[m * A.sr + k * A.sc]) : dfl(0.0f, 0.0f);
+            const int n = n0 + mm;
+            Bs[kk][mm] = (n < N && k < K) ? to_dfl(Bb[k * B.sr + n * B.sc]) : dfl(0.0f, 0.0f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            dfl a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = add_accurate(acc[i][j], a[i] * b[j]);
+        }
+        __syncthreads();
+    }
+    double *Cb = C + z * sCz;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < M && n < N) Cb[m * sCm + n * sCn] = s * to_double(acc[i][j]);
+        }
 }
 
 template <typename T>
