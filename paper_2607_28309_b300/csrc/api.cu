@@ -244,30 +244,35 @@ struct TableCacheEntry {
     double rho;
     int S[3], k0, k1;
     std::vector<double> A6;
+    // the per-offset item ranges of the item set (what a cached set-up needs of it)
+    int Rm = 0;
+    std::vector<int> base, klo, cnt;
 };
 std::mutex g_tcache_mu;
-std::vector<TableCacheEntry> g_tcache;
+std::vector<std::shared_ptr<const TableCacheEntry>> g_tcache;
 constexpr size_t kTableCacheEntries = 8;
 
-bool tcache_get(double rho, const int S[3], int k0, int k1, std::vector<double> &A6) {
+std::shared_ptr<const TableCacheEntry> tcache_find(double rho, const int S[3], int k0, int k1) {
     std::lock_guard<std::mutex> lk(g_tcache_mu);
     for (auto &e : g_tcache)
-        if (e.rho == rho && e.S[0] == S[0] && e.S[1] == S[1] && e.S[2] == S[2] && e.k0 == k0 && e.k1 == k1) {
-            A6 = e.A6;
-            return true;
-        }
-    return false;
+        if (e->rho == rho && e->S[0] == S[0] && e->S[1] == S[1] && e->S[2] == S[2] && e->k0 == k0 && e->k1 == k1)
+            return e;
+    return nullptr;
 }
 
-void tcache_put(double rho, const int S[3], int k0, int k1, std::vector<double> &&A6) {
+void tcache_put(double rho, const int S[3], int k0, int k1, std::vector<double> &&A6, const ItemSet &is) {
+    auto e = std::make_shared<TableCacheEntry>();
+    e->rho = rho;
+    for (int i = 0; i < 3; ++i) e->S[i] = S[i];
+    e->k0 = k0;
+    e->k1 = k1;
+    e->A6 = std::move(A6);
+    e->Rm = is.Rm;
+    e->base = is.base;
+    e->klo = is.klo;
+    e->cnt = is.cnt;
     std::lock_guard<std::mutex> lk(g_tcache_mu);
     if (g_tcache.size() >= kTableCacheEntries) g_tcache.erase(g_tcache.begin());
-    TableCacheEntry e;
-    e.rho = rho;
-    for (int i = 0; i < 3; ++i) e.S[i] = S[i];
-    e.k0 = k0;
-    e.k1 = k1;
-    e.A6 = std::move(A6);
     g_tcache.push_back(std::move(e));
 }
 
@@ -1375,19 +1380,22 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
     for (int i = 0; i < 3; ++i) S[i] = std::min(S[i], rmax);
     ItemSet is;
     PhaseTrace tr_all("lag tables (items, quadrature or cache, octants)");
-    bool items_ok;
-    {
+    // a cached quadrature brings the item ranges with it: the host item set is built on a miss only
+    auto hit = tcache_find(p->rho, S, k0, k1);
+    if (!hit) {
         PhaseTrace tr_items("lag-table items (host)");
-        items_ok = build_items(p->rho, S, k0, k1, is);
+        if (!build_items(p->rho, S, k0, k1, is))
+            MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (alpha < 0.5)");
     }
-    if (!items_ok) MOT_FAIL(MOT_EUNSUPPORTED, "time step too small for the lag-table quadrature (alpha < 0.5)");
-    const int nit = (int)is.items.size();
+    const int nit = hit ? (int)(hit->A6.size() / 6) : (int)is.items.size();
+    const int Rm = hit ? hit->Rm : is.Rm;
+    const std::vector<int> &rbase = hit ? hit->base : is.base, &rklo = hit ? hit->klo : is.klo,
+                           &rcnt = hit ? hit->cnt : is.cnt;
     DBuf dA, dmap;
     MOT_TRY(dalloc(dA, sizeof(double) * 6 * std::max(1, nit)));
-    MOT_TRY(dalloc(dmap, sizeof(int) * is.base.size()));
-    std::vector<double> cached;
-    if (nit > 0 && tcache_get(p->rho, S, k0, k1, cached) && cached.size() == 6 * (size_t)nit) {
-        MOT_CUDA_TRY(cudaMemcpyAsync(dA.p, cached.data(), sizeof(double) * 6 * nit, cudaMemcpyHostToDevice, st));
+    MOT_TRY(dalloc(dmap, sizeof(int) * rbase.size()));
+    if (hit && nit > 0) {
+        MOT_CUDA_TRY(cudaMemcpyAsync(dA.p, hit->A6.data(), sizeof(double) * 6 * nit, cudaMemcpyHostToDevice, st));
         MOT_CUDA_TRY(cudaStreamSynchronize(st));
     } else if (nit > 0) {
         const int nf = (int)is.faces.size(), nt = (int)is.tri.size();
@@ -1418,7 +1426,7 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         std::vector<double> A6(6 * (size_t)nit);
         MOT_CUDA_TRY(cudaMemcpyAsync(A6.data(), dA.p, sizeof(double) * 6 * nit, cudaMemcpyDeviceToHost, st));
         MOT_CUDA_TRY(cudaStreamSynchronize(st));
-        tcache_put(p->rho, S, k0, k1, std::move(A6));
+        tcache_put(p->rho, S, k0, k1, std::move(A6), is);
         dfree(ditems);
         dfree(dfaces);
         dfree(dtri);
@@ -1426,13 +1434,13 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         dfree(dBM);
     }
     // each lag's item map is formed on the device from the per-offset item ranges
-    const long n3 = (long)is.base.size();
+    const long n3 = (long)rbase.size();
     DBuf drange;
     MOT_TRY(dalloc(drange, sizeof(int) * 3 * n3));
     int *dbase = (int *)drange.p, *dklo = dbase + n3, *dcnt = dklo + n3;
-    MOT_CUDA_TRY(cudaMemcpyAsync(dbase, is.base.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
-    MOT_CUDA_TRY(cudaMemcpyAsync(dklo, is.klo.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
-    MOT_CUDA_TRY(cudaMemcpyAsync(dcnt, is.cnt.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(dbase, rbase.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(dklo, rklo.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
+    MOT_CUDA_TRY(cudaMemcpyAsync(dcnt, rcnt.data(), sizeof(int) * n3, cudaMemcpyHostToDevice, st));
     for (int k = k0; k <= k1; ++k) {
         LagTable &L = p->lags[k];
         if (L.override_) continue;
@@ -1443,7 +1451,7 @@ mot_status compute_lag_octants(mot_problem *p, int k0, int k1) {
         count_launch();
         k_lag_map<<<grid_for(n3), 256, 0, st>>>(dbase, dklo, dcnt, n3, k, (int *)dmap.p);
         count_launch();
-        k_expand_octant<<<grid_for(n), 256, 0, st>>>((const double *)dA.p, (const int *)dmap.p, is.Rm, L.R[0],
+        k_expand_octant<<<grid_for(n), 256, 0, st>>>((const double *)dA.p, (const int *)dmap.p, Rm, L.R[0],
                                                      L.R[1], L.R[2], (double *)L.oct.p);
         MOT_CHECK_LAUNCH();
         L.ready = true;
