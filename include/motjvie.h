@@ -227,7 +227,8 @@ mot_status mot_apply_Z0(mot_problem *p, const void *x_dev, void *y_dev, int nrhs
  *   start at zero.  Calls whose kernels overlap on the GPU (other streams or
  *   threads) race on the array; order them on one stream.
  * - x_dev, y_dev, nrhs, dtype as mot_apply_Z0.  With c = the byte size of one
- *   complex element of dtype and H0 = M0x/2 + 1, the scratch needed is
+ *   complex element of the FFT (16 for MOT_F64 and MOT_F64DF, 8 for MOT_F32)
+ *   and H0 = M0x/2 + 1, the scratch needed is
  *   round_up(nrhs * 3 * Nz * Ny * H0 * c, 256) + nrhs * 3 * Nz * M0y * H0 * c
  *   bytes; a request above MOT_STATIC_SCRATCH_BYTES fails with MOT_EINVAL
  *   (message gives both sizes) before any device work.

@@ -3682,14 +3682,15 @@ std::atomic<void *> g_static_ptr[kMaxDevices];
 extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, void *y_dev, int nrhs, int dtype) {
     if (!p || !x_dev || !y_dev) MOT_FAIL(MOT_EINVAL, "NULL argument");
     if (nrhs < 1) MOT_FAIL(MOT_EINVAL, "nrhs < 1");
-    if (dtype != MOT_F64 && dtype != MOT_F32) MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64 or MOT_F32");
+    if (dtype != MOT_F64 && dtype != MOT_F32 && dtype != MOT_F64DF)
+        MOT_FAIL(MOT_EINVAL, "dtype must be MOT_F64, MOT_F32 or MOT_F64DF");
     if (x_dev == y_dev) MOT_FAIL(MOT_EINVAL, "x and y must not overlap");
     if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15u)
         MOT_FAIL(MOT_EINVAL, "x and y must be 16-byte aligned");
     const int dev = p->ctx->device;
     if (dev < 0 || dev >= kMaxDevices) MOT_FAIL(MOT_EINVAL, "device index beyond the static-scratch table");
     size_t a, b;
-    z0_ws_bytes(p, nrhs, dtype == MOT_F64 ? sizeof(double2) : sizeof(float2), &a, &b);
+    z0_ws_bytes(p, nrhs, dtype == MOT_F32 ? sizeof(float2) : sizeof(double2), &a, &b);
     a = (a + 255) / 256 * 256;
     if (a + b > (size_t)MOT_STATIC_SCRATCH_BYTES)
         MOT_FAIL(MOT_EINVAL, "mot_apply_Z0_static needs " + std::to_string(a + b) + " bytes of scratch; the static array holds " +
@@ -3713,6 +3714,9 @@ extern "C" mot_status mot_apply_Z0_static(mot_problem *p, const void *x_dev, voi
         EpiZ0<double, double> e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0],
                                    p->opt.delta};
         st = z0_product<double, double>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
+    } else if (dtype == MOT_F64DF) {
+        EpiZ0DF e = {(const double *)x_dev, (double *)y_dev, eps_of<double>(p), pr, p->N[0], p->opt.delta};
+        st = z0_product<double, dfl>(p, (const double *)x_dev, nrhs, ws, ws + a, e, p->ctx->stream);
     } else {
         EpiZ0<float, float> e = {(const float *)x_dev, (float *)y_dev, eps_of<float>(p), pr, p->N[0],
                              (float)p->opt.delta};

@@ -318,3 +318,54 @@ def test_delta_regularised_product_and_march(ctx, orc):
     # the shift is not dropped: the unshifted march differs
     J0 = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
     assert _mot_errors(J0, Jo).max() > 1e-3
+
+
+_SPREAD_SCRIPT = r'''
+import sys, numpy as np, torch
+import paper_2607_28309_b300 as mot
+from paper_2607_28309_b300 import synthetic
+N = (9, 7, 8)
+eps = synthetic.block_eps(N, 3, 2.0, 5.0, 8)
+alpha, steps = 8.0, 30
+ctx = mot.mot_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+prob = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha)
+out = {}
+for prec in (mot.MOT_FP64, mot.MOT_MIXED):
+    run = mot.mot_run_create(prob, [synthetic.pulse(steps, alpha)], prec)
+    J = np.zeros((steps, 1, 3, int(np.prod(N))))
+    mot.mot_run_step(run, 11, J[:11])
+    mot.mot_run_step(run, steps - 11, J[11:])
+    mot.mot_run_destroy(run)
+    out[str(prec)] = J
+mot.mot_problem_destroy(prob)
+mot.mot_ctx_destroy(ctx)
+np.savez(sys.argv[1], **out)
+'''
+
+
+def test_spread_history_schedule_matches_whole_pass(tmp_path):
+    """The spread schedule of the time-blocked history (the old part in chunks
+    beside the previous block's steps, the recent part at the block start;
+    MOTJVIE_HIST_SPREAD=1, read once per process) sums the same terms in another
+    order: its march equals the whole-pass march to rounding, FP64 and mixed,
+    past two time blocks and across a split of the march into calls."""
+    import os
+    import subprocess
+    import sys
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    script = tmp_path / "march.py"
+    script.write_text(_SPREAD_SCRIPT)
+    res = {}
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for spread in ("0", "1"):
+        env = dict(os.environ, MOTJVIE_HIST_SPREAD=spread,
+                   PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+        outp = tmp_path / f"J{spread}.npz"
+        subprocess.run([sys.executable, str(script), str(outp)], check=True, env=env, timeout=600, cwd=root)
+        res[spread] = np.load(outp)
+    for prec, tol in ((str(mot.MOT_FP64), 1e-12), (str(mot.MOT_MIXED), 1e-6)):
+        a, b = res["0"][prec], res["1"][prec]
+        assert np.abs(a[-1]).max() > 0
+        assert _mot_errors(b, a).max() <= tol, (prec, _mot_errors(b, a).max())

@@ -40,7 +40,8 @@ def test_static_scratch_product_matches_allocating_product():
         try:
             nv = int(np.prod(N))
             gen = torch.Generator(device="cuda").manual_seed(5)
-            for dtype, tdt, tol in ((mot.MOT_F64, torch.float64, 1e-10), (mot.MOT_F32, torch.float32, 1e-5)):
+            for dtype, tdt, tol in ((mot.MOT_F64, torch.float64, 1e-10), (mot.MOT_F32, torch.float32, 1e-5),
+                                    (mot.MOT_F64DF, torch.float64, 1e-10)):
                 for nrhs in (1, 3):
                     x = torch.randn(nrhs, 3, nv, device="cuda", dtype=tdt, generator=gen)
                     ref = torch.empty_like(x)
