@@ -59,6 +59,20 @@ def test_problem_rejects_non_finite_delta(ctx, delta):
     assert "delta" in mot.mot_last_error()
 
 
+def test_bad_precision_and_dtype_are_refused(ctx):
+    N = (4, 3, 5)
+    prob = mot.mot_problem_create(ctx, N, 10e-9, np.full(N[::-1], 2.0), 4.0)
+    try:
+        for bad in (-1, 3):
+            assert _status(mot.mot_run_create, prob, [synthetic.pulse(8, 4.0)], bad) == mot.MOT_EINVAL
+            x = torch.zeros(3 * int(np.prod(N)), dtype=torch.float64, device="cuda")
+            y = torch.zeros_like(x)
+            assert _status(mot.mot_apply_Z0, prob, x, y, 1, bad) == mot.MOT_EINVAL
+            assert _status(mot.mot_apply_Z0_static, prob, x, y, 1, bad) == mot.MOT_EINVAL
+    finally:
+        mot.mot_problem_destroy(prob)
+
+
 def test_run_rejects_bad_plane_waves(ctx):
     N = (5, 4, 3)
     prob = mot.mot_problem_create(ctx, N, 10e-9, np.full(N[::-1], 3.0), 4.0)
@@ -83,7 +97,7 @@ def test_run_rejects_bad_plane_waves(ctx):
         mot.mot_problem_destroy(prob)
 
 
-@pytest.mark.parametrize("precision", [mot.MOT_FP64, mot.MOT_MIXED])
+@pytest.mark.parametrize("precision", [mot.MOT_FP64, mot.MOT_MIXED, mot.MOT_FP64DF])
 @pytest.mark.parametrize("graph", [0, 1, 2])
 def test_iteration_cap_gives_notconv(ctx, precision, graph):
     N = (8, 7, 6)
