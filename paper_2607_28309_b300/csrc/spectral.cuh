@@ -661,6 +661,12 @@ template <typename T> __device__ __forceinline__ void cp_async_elem(T *dst_smem,
     else if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
     else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
 }
+// the same with the shared-memory destination given as a shared-window address
+template <typename T> __device__ __forceinline__ void cp_async_elem_s(unsigned d, const T *src) {
+    static_assert(sizeof(T) == 8 || sizeof(T) == 16, "8- or 16-byte elements");
+    if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -1061,6 +1067,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_hist_acc(const 
 // m mod TB; the recent part and the whole pass run only when t == 0 (block
 // m0 = m), the old part takes chunk t of the block after m's (m0 = m - t + TB).
 // ---------------------------------------------------------------------------
+// two FP32 fused multiply-adds in one instruction (round to nearest, each lane
+// exactly the scalar fmaf): d = a * b + c lane-wise
+__device__ __forceinline__ float2 fma_f32x2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&c)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+
 constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
 constexpr int kHistOld = 0, kHistRecent = 1, kHistAll = 2;  // kHistAll: both parts in one pass at the block start
 
@@ -1068,12 +1085,15 @@ template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
     return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
 }
 
-template <typename T, int TB, int TH>
+template <typename T, int TB, int TH, bool Pair = std::is_same<T, float>::value>
 __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
                                                     cplx<T> *__restrict__ qbuf, long qslot, int Mz, int My, int H,
                                                     Octant oc, int nrhs, int ell, long m0, int tlo, int part,
-                                                    int c_lo, int c_hi, const long long *__restrict__ nptr, int dm) {
+                                                    int c_lo, int c_hi, const long long *__restrict__ nptr, int dm,
+                                                    int lpf) {
     static_assert(TB / TH == 4, "four thread groups: group y also loads mirror row y");
+    static_assert(kHistBlockDepth % 2 == 0 && kHistBlockDepth >= 4 && kHistBlockDepth % TH == 0,
+                  "pairs of slots per barrier, whole windows per pipeline round");
     constexpr int D = kHistBlockDepth;
     if (nptr) {
         const long m = (long)*nptr + dm;
@@ -1091,6 +1111,16 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
         }
     }
     using C = cplx<T>;
+    // FP32: the mirror rows' sign flips move from Lambda onto the inputs and
+    // accumulators (row r holds a_0, sy a_1, sz a_2 and multiplies u_0, sy u_1,
+    // sz u_2), so every multiplier is a plain Lambda entry and each complex
+    // multiply-add is one packed FMA; negation is exact, the sums are the same
+    constexpr bool kPair = Pair && std::is_same<T, float>::value;
+    using LwT = typename std::conditional<kPair, float2, T>::type;
+    auto lw_of = [](T v) -> LwT {
+        if constexpr (kPair) return make_float2(v, v);
+        else return v;
+    };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);  // [D][row 4][component 3][point 32]
     const int hz = Mz / 2 + 1, hy = My / 2 + 1;
@@ -1134,21 +1164,35 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             off[3] = (twoy && twoz) ? off[2] + (long)(My - 2 * j) * H : off[0];
             Lp = Lh + ((long)fz * oc.Ky + j) * oc.H + kx;
         }
-        // loader: thread (x, y) copies mirror row y of point x, three components, per slot
+        // loader: thread (x, y) copies mirror row y of point x, three components, per
+        // slot.  Rn is the ring address of its next copy: slot s_i, one slot back per
+        // copy, from slot 0 on to slot ell - 1
         const long my_off = y == 0 ? off[0] : y == 1 ? off[1] : y == 2 ? off[2] : off[3];
-        long s_issue = ((m0 - 2 - u_lo) % ell + ell) % ell;  // ring slot of the next slot to load (wrapping)
+        int s_i = (int)(((m0 - 2 - u_lo) % ell + ell) % ell);
+        const C *Rn = ring + (long)s_i * slot_size + my_off;
+        const long wrap = (long)(ell - 1) * slot_size;
+        // shared address of this thread's element in buffer 0, component 0
+        const unsigned sdst = (unsigned)__cvta_generic_to_shared(buf + y * 3 * 32 + x);
+        constexpr unsigned kBufBytes = 4 * 3 * 32 * sizeof(C), kCompBytes = 32 * sizeof(C);
         auto issue = [&](int bslot) {
             if (valid) {
-                const C *R = ring + s_issue * slot_size + my_off;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) cp_async_elem(buf + ((bslot * 4 + y) * 3 + q) * 32 + x, R + q * slot_comp);
+                for (int q = 0; q < 3; ++q) cp_async_elem_s(sdst + bslot * kBufBytes + q * kCompBytes, Rn + q * slot_comp);
             }
             asm volatile("cp.async.commit_group;\n" ::);
-            s_issue = s_issue == 0 ? ell - 1 : s_issue - 1;
+            if (s_i == 0) {
+                s_i = ell - 1;
+                Rn += wrap;
+            } else {
+                --s_i;
+                Rn -= slot_size;
+            }
         };
-#pragma unroll 1
-        for (int i = 0; i < D - 1; ++i) {
-            if (i < nu) issue(i);
+        const int nui = (int)nu, ulo = (int)u_lo;
+        // D - 2 slots in flight ahead of the pair being read (one barrier per two slots)
+#pragma unroll
+        for (int i = 0; i < D - 2; ++i) {
+            if (i < nui) issue(i);
             else asm volatile("cp.async.commit_group;\n" ::);
         }
         C a[TH][4][3];
@@ -1160,42 +1204,73 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
                 for (int q = 0; q < 3; ++q) a[i][r][q] = cmake<C>(T(0), T(0));
         // window: at walk position w (u = u_lo + w), output t0 + i needs lag
         // k = u + 2 + t0 + i, held in lw[(w + i) mod TH]; before the walk lw[i]
-        // holds lag u_lo + 2 + t0 + i
-        T lw[TH][6];
+        // holds lag u_lo + 2 + t0 + i.  FP32: each value twice (a lane pair), the
+        // multiplier of a complex value in one packed FMA
+        LwT lw[TH][6];
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
-            const long k = u_lo + 2 + t0 + i;
+            const int k = ulo + 2 + t0 + i;
+            const T *Lk = Lp + (long)k * 6 * cs;
 #pragma unroll
-            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = (valid && k <= ell) ? Lp[k * 6 * cs + c6 * cs] : T(0);
+            for (int c6 = 0; c6 < 6; ++c6) lw[i][c6] = lw_of((valid && k <= ell) ? Lk[c6 * cs] : T(0));
         }
-        for (long w0 = 0; w0 < nu; w0 += TH) {
-            // fully unrolled with a guard (uniform over the block) rather than a break: the
-            // window index (ww + i) % TH stays a compile-time constant, lw and a in registers
+        // the window's next lag kn (at Ln) and the lag kp (at Lpf) whose lines are
+        // prefetched to L2: the lag entering the newest window lpf slots later, group y
+        // taking arrays y and y + 4 so that each line is asked for once per block;
+        // both advance one lag per slot
+        const long lstep = 6 * cs;
+        int kn = ulo + 2 + t0 + TH;
+        const T *Ln = Lp + (long)kn * lstep;
+        int kp = ulo + TB + 2 + lpf;
+        const T *Lpf = Lp + (long)kp * lstep + y * cs;
+        for (int w0 = 0; w0 < nui; w0 += D) {
+            // fully unrolled over the D buffers with a guard (uniform over the block)
+            // rather than a break: the buffer (w mod D) and the window index
+            // ((w + i) mod TH) are compile-time constants, lw and a stay in registers
 #pragma unroll
-            for (int ww = 0; ww < TH; ++ww) {
-                const long w = w0 + ww, u = u_lo + w;
-                if (w < nu) {
-                    asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");  // slot w landed
-                    __syncthreads();  // ... for every thread; and slot w - 1's buffer is free again
-                    const int bs = (int)(w % D);
-                    C uv[4][3];
+            for (int ww = 0; ww < D; ++ww) {
+                const int w = w0 + ww;
+                if (w < nui) {
+                    if ((ww & 1) == 0) {
+                        asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 4) : "memory");  // slots w, w + 1 landed
+                        __syncthreads();  // ... for every thread; slots w - 2, w - 1's buffers are free again
+                        // the next two copies go to those buffers; slots w, w + 1's are
+                        // rewritten only after the next barrier
+                        if (w + D - 2 < nui) issue((ww + D - 2) % D);
+                        else asm volatile("cp.async.commit_group;\n" ::);
+                        if (w + D - 1 < nui) issue((ww + D - 1) % D);
+                        else asm volatile("cp.async.commit_group;\n" ::);
+                    }
+                    // no test per output: the window holds zeros for lags above ell, and
+                    // outputs t < tlo are computed but not stored
+                    const C *sb = buf + ww * 4 * 3 * 32 + x;  // buffer ww, point x
+                    if constexpr (kPair) {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                        for (int r = 0; r < 4; ++r) {
+                            const C *ub = sb + r * 3 * 32;
+                            const C u0v = ub[0];
+                            C v1 = ub[32], v2 = ub[64];
+                            if (r & 1) v1 = cmake<C>(-v1.x, -v1.y);
+                            if (r & 2) v2 = cmake<C>(-v2.x, -v2.y);
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) uv[r][q] = buf[((bs * 4 + r) * 3 + q) * 32 + x];
-                    if (w + D - 1 < nu) issue((int)((w + D - 1) % D));
-                    else asm volatile("cp.async.commit_group;\n" ::);
+                            for (int i = 0; i < TH; ++i) {
+                                const LwT *g = lw[(ww + i) % TH];  // xx yy zz xy xz yz
+                                a[i][r][0] = fma_f32x2(g[4], v2, fma_f32x2(g[3], v1, fma_f32x2(g[0], u0v, a[i][r][0])));
+                                a[i][r][1] = fma_f32x2(g[5], v2, fma_f32x2(g[1], v1, fma_f32x2(g[3], u0v, a[i][r][1])));
+                                a[i][r][2] = fma_f32x2(g[2], v2, fma_f32x2(g[5], v1, fma_f32x2(g[4], u0v, a[i][r][2])));
+                            }
+                        }
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < TH; ++i) {
-                        const long k = u + 2 + t0 + i;
-                        if (t0 + i >= tlo && k <= ell) {
-                            const T *g = lw[(ww + i) % TH];
-                            const T gxx = g[0], gyy = g[1], gzz = g[2];
+                        for (int r = 0; r < 4; ++r) {
+                            const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
+                            const C *ub = sb + r * 3 * 32;
+                            const C u0v = ub[0], u1v = ub[32], u2v = ub[64];
 #pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const T sy = (r & 1) ? T(-1) : T(1), sz = (r & 2) ? T(-1) : T(1);
+                            for (int i = 0; i < TH; ++i) {
+                                const T *g = lw[(ww + i) % TH];
+                                const T gxx = g[0], gyy = g[1], gzz = g[2];
                                 const T exy = sy * g[3], exz = sz * g[4], eyz = sy * sz * g[5];
-                                const C u0v = uv[r][0], u1v = uv[r][1], u2v = uv[r][2];
                                 a[i][r][0] = cmake<C>(a[i][r][0].x + gxx * u0v.x + exy * u1v.x + exz * u2v.x,
                                                       a[i][r][0].y + gxx * u0v.y + exy * u1v.y + exz * u2v.y);
                                 a[i][r][1] = cmake<C>(a[i][r][1].x + exy * u0v.x + gyy * u1v.x + eyz * u2v.x,
@@ -1205,11 +1280,17 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
                             }
                         }
                     }
-                    // lw[ww] held lag u + 2 + t0 (done); it takes lag u + 2 + t0 + TH
-                    const long kn = u + 2 + t0 + TH;
+                    if (lpf > 0 && valid && kp <= ell) {
+                        prefetch_l2(Lpf);
+                        if (y < 2) prefetch_l2(Lpf + 4 * cs);
+                    }
+                    ++kp;
+                    Lpf += lstep;
+                    // lw[w mod TH] held lag u + 2 + t0 (done); it takes lag kn = u + 2 + t0 + TH
 #pragma unroll
-                    for (int c6 = 0; c6 < 6; ++c6)
-                        lw[ww][c6] = (valid && kn <= ell) ? Lp[kn * 6 * cs + c6 * cs] : T(0);
+                    for (int c6 = 0; c6 < 6; ++c6) lw[ww % TH][c6] = lw_of((valid && kn <= ell) ? Ln[c6 * cs] : T(0));
+                    ++kn;
+                    Ln += lstep;
                 }
             }
         }
@@ -1227,11 +1308,13 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     C *dst = Q + off[r] + q * slot_comp;
+                    C v = a[i][r][q];
+                    if (kPair && ((q == 1 && (r & 1)) || (q == 2 && (r & 2)))) v = cmake<C>(-v.x, -v.y);
                     if (part == kHistRecent) {
                         const C o = *dst;
-                        *dst = cmake<C>(o.x + a[i][r][q].x, o.y + a[i][r][q].y);
+                        *dst = cmake<C>(o.x + v.x, o.y + v.y);
                     } else
-                        *dst = a[i][r][q];
+                        *dst = v;
                 }
             }
         }

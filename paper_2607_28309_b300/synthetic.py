@@ -170,6 +170,15 @@ def pillars8x8():
             "exc": [pulse(200, 8.0, khat=(0.0, 0.0, -1.0))]}
 
 
+def pillars2x2():
+    """2x2 pillars on 64x64x80 (the pillar array's layers and pitch), normal incidence
+    along -z, x-pol, alpha 8, 200 steps: a history grid of 128x128x160 whose ring
+    and Lambda_k tables exceed L2 while the whole run holds a few GB."""
+    eps = pillar_eps(2, 2)
+    return {"name": "pillars2x2_a8", "N": (64, 64, 80), "h": H_DEFAULT, "eps": eps, "alpha": 8.0, "steps": 200,
+            "exc": [pulse(200, 8.0, khat=(0.0, 0.0, -1.0))]}
+
+
 def metasurface8x8(nsteps: int = 1250):
     """The paper's 8 x 8 bilayer metasurface (Sec. V-B): 240 x 240 x 90 voxels,
     dt = 16 dt_CFL, its own pulse (sigma 11.06 fs, t0 68.85 fs, f0 312 THz, -z, x-pol);
@@ -193,6 +202,7 @@ WORKLOADS = {
     "cube64_a8": lambda: cube64(8.0),
     "cube64_a16": lambda: cube64(16.0),
     "cube64_b16": lambda: cube64_batch16(),
+    "pillars2x2": lambda: pillars2x2(),
     "pillars8x8": lambda: pillars8x8(),
     "metasurface8x8": lambda: metasurface8x8(),
 }
