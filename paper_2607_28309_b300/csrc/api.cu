@@ -2520,27 +2520,12 @@ mot_status hist_block_pass(mot_run *r, cudaStream_t st, long m0, int tlo, int pa
     if (r->hTB != (sizeof(T) == 4 ? 8 : 4)) MOT_FAIL(MOT_EINVAL, "time block does not match the history precision");
     // time block 8 (FP32) with two outputs per thread, 4 (FP64) with one: four thread groups
     constexpr int TB = sizeof(T) == 4 ? 8 : 4, TH = TB / 4;
-    constexpr size_t smem = hist_block_smem<T>();
     // L2 prefetch distance of the Lambda_k window in slots (MOTJVIE_HIST_LAM_PF; 0: none)
     static const int lpf = getenv("MOTJVIE_HIST_LAM_PF") ? std::max(0, atoi(getenv("MOTJVIE_HIST_LAM_PF"))) : 4;
-    // FP32: MOTJVIE_HIST_SCALAR=1 takes scalar FMAs instead of the packed ones (timing comparisons)
-    static const bool scalar = getenv("MOTJVIE_HIST_SCALAR") && atoi(getenv("MOTJVIE_HIST_SCALAR")) != 0;
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {
-        if (scalar) {
-            MOT_TRY((allow_smem<k_hist_block<T, TB, TH, false>>()));
-            count_launch();
-            k_hist_block<T, TB, TH, false><<<grid, dim3(32, 4), smem, st>>>(
-                ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo, part, c_lo, c_hi, nptr, dm, lpf);
-            done = true;
-        }
-    }
-    if (!done) {
-        MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
-        count_launch();
-        k_hist_block<T, TB, TH><<<grid, dim3(32, 4), smem, st>>>(ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc,
-                                                                r->B, p->ell, m0, tlo, part, c_lo, c_hi, nptr, dm, lpf);
-    }
+    MOT_TRY(allow_smem<k_hist_block<T, TB, TH>>());
+    count_launch();
+    k_hist_block<T, TB, TH><<<grid, dim3(32, 4), hist_block_smem<T>(), st>>>(
+        ring, Lh_of<T>(p), q.buf, q.slot, Mz, My, H, oc, r->B, p->ell, m0, tlo, part, c_lo, c_hi, nptr, dm, lpf);
     MOT_CHECK_LAUNCH();
     return MOT_OK;
 }
