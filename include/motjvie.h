@@ -105,8 +105,10 @@ typedef struct {
                          overhead).  Default 0                                     */
     int guess;        /* initial guess of each step's solve (the paper does not
                          specify one): 0 = J_{n-1}; 1 = 2 J_{n-1} - J_{n-2}
-                         (linear extrapolation, default: 19.8 instead of 21
-                         products per step on the 256 x 256 x 80 pillar array)   */
+                         (linear extrapolation); 2 = 3 J_{n-1} - 3 J_{n-2} +
+                         J_{n-3} (quadratic, default; one more FP64 current
+                         vector held by the run).  Products per step on the
+                         256 x 256 x 80 pillar array: 21.0 / 19.8 / 19.0      */
     int graph;        /* 1 (default): after the first step each step is one CUDA
                          graph launch whose loops and tests run on the device; 0:
                          host-driven steps, each solve's TFQMR loop one graph
@@ -289,8 +291,9 @@ mot_status mot_run_step(mot_run *r, int nsteps, double *J_out, mot_step_stats *s
 
 /* Checkpoint: write run r's state to the file at path -- the problem's
  * fingerprint (grid, h, alpha, a hash of eps_r), precision, plane waves, the
- * next step index, J_{n-1}, J_{n-2} and the whole history ring of spectra
- * (ell slots; for large grids this is most of the file) -- so that marching
+ * next step index, J_{n-1}, J_{n-2} (and J_{n-3} when the run's options.guess
+ * is 2) and the whole history ring of spectra (ell slots; for large grids this
+ * is most of the file) -- so that marching
  * can resume in another process.  Synchronises the context stream.  The
  * format is this library's own (little-endian, version 1).
  * Errors: MOT_EINVAL (null, file cannot be written), MOT_ECUDA.              */
@@ -298,7 +301,8 @@ mot_status mot_run_save(mot_run *r, const char *path);
 
 /* Resume: create a run on problem p from a checkpoint written by
  * mot_run_save.  p must describe the same problem (grid, h, alpha and eps_r
- * are checked against the checkpoint; options may differ).  The first step
+ * are checked against the checkpoint; options may differ: a run whose guess
+ * needs J_{n-3} but whose checkpoint has none takes J_{n-2} for it).  The first step
  * after loading runs host-driven, then graph mode resumes.  *out is owned by
  * the caller (mot_run_destroy).
  * Errors: MOT_EINVAL (null, unreadable/corrupt file, another problem),

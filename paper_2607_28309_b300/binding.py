@@ -379,7 +379,7 @@ def mot_fma_peak(device: int = 0, dtype: int = MOT_F64):
 
 def default_options(**kw) -> mot_options:
     """mot_options with the library defaults (tol 0 = per-precision default)."""
-    o = mot_options(0.0, 500, 1e-6, 6, 0.0, 0, 1, 1, 1)
+    o = mot_options(0.0, 500, 1e-6, 6, 0.0, 0, 2, 1, 1)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

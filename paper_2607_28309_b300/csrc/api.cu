@@ -504,7 +504,7 @@ struct mot_run {
     std::vector<PlaneWaveDev> pw_host;
     std::vector<mot_planewave> exc_host;  // the plane waves as given (checkpoints)
     bool warmed = false;  // one host-driven step done in this process (graph mode needs it first)
-    DBuf pw, inc, J, J2, b, r;  // J2: J_{n-2} for the extrapolated guess
+    DBuf pw, inc, J, J2, J3, b, r;  // J2, J3: J_{n-2}, J_{n-3} for the extrapolated guesses (J3: guess 2 only)
     DBuf ring, wsAh, wsBh;
     DBuf hacc;  // history accumulation on the full Mh grid [B][3][Mhz][Mhy][Hh]
     // time-blocked history: the lags 2.. partial sums of the steps of the current
@@ -1874,11 +1874,11 @@ mot_status mot_problem_create(mot_ctx *ctx, const int32_t n[3], double h, const 
     long nv = (long)n[0] * n[1] * n[2];
     for (long i = 0; i < nv; ++i)
         if (!std::isfinite(eps_r[i]) || eps_r[i] < 1.0) MOT_FAIL(MOT_EINVAL, "eps_r must be finite and >= 1");
-    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 1, 1, 1};
+    mot_options o = {0.0, 500, 1e-6, 6, 0.0, 0, 2, 1, 1};
     if (opt) o = *opt;
     if (!std::isfinite(o.delta)) MOT_FAIL(MOT_EINVAL, "delta must be finite");
     if (o.maxit < 1) MOT_FAIL(MOT_EINVAL, "maxit < 1");
-    if (o.guess != 0 && o.guess != 1) MOT_FAIL(MOT_EINVAL, "guess must be 0 or 1");
+    if (o.guess < 0 || o.guess > 2) MOT_FAIL(MOT_EINVAL, "guess must be 0, 1 or 2");
     if (o.graph < 0 || o.graph > 2) MOT_FAIL(MOT_EINVAL, "graph must be 0, 1 or 2");
     if (o.autotune != 0 && o.autotune != 1) MOT_FAIL(MOT_EINVAL, "autotune must be 0 or 1");
     MOT_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -2129,6 +2129,28 @@ __global__ void k_extrapolate(double *__restrict__ J, double *__restrict__ J2, l
         J[i] = 2.0 * a - J2[i];
         J2[i] = a;
     }
+}
+
+// x0 = 3 J_{n-1} - 3 J_{n-2} + J_{n-3} in J (the quadratic through the last
+// three currents), J_{n-1} saved into J2 and J_{n-2} into J3
+__global__ void k_extrapolate2(double *__restrict__ J, double *__restrict__ J2, double *__restrict__ J3, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double a = J[i], b = J2[i];
+        J[i] = 3.0 * (a - b) + J3[i];
+        J3[i] = b;
+        J2[i] = a;
+    }
+}
+
+// the step's initial guess in J from the saved currents (options.guess)
+mot_status launch_guess(mot_run *r, long n, cudaStream_t st) {
+    const int g = r->p->opt.guess;
+    if (g == 0) return MOT_OK;
+    count_launch();
+    if (g == 1) k_extrapolate<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, n);
+    else k_extrapolate2<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, (double *)r->J3.p, n);
+    MOT_CHECK_LAUNCH();
+    return MOT_OK;
 }
 
 template <typename T> __global__ void k_sub(T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ a, long n) {
@@ -2725,11 +2747,7 @@ mot_status run_one_step(mot_run *r, mot_step_stats *stats) {
     else if (dfm) MOT_TRY(history_rhs<dfl>(r, st));
     else MOT_TRY(history_rhs<double>(r, st));
     cudaEventRecord(r->ev[1], st);
-    if (p->opt.guess == 1) {
-        count_launch();
-        k_extrapolate<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, n);
-        MOT_CHECK_LAUNCH();
-    }
+    MOT_TRY(launch_guess(r, n, st));
     int iters = 0, sweeps = 0;
     bool conv = true;
     std::vector<double> bn(r->B), rn(r->B);
@@ -3039,11 +3057,7 @@ mot_status build_step_graph(mot_run *r) {
         if (mixed) MOT_TRY(history_rhs<float>(r, st, nptr));
         else if (dfm) MOT_TRY(history_rhs<dfl>(r, st, nptr));
         else MOT_TRY(history_rhs<double>(r, st, nptr));
-        if (p->opt.guess == 1) {
-            count_launch();
-            k_extrapolate<<<grid_for(n), 256, 0, st>>>((double *)r->J.p, (double *)r->J2.p, n);
-            MOT_CHECK_LAUNCH();
-        }
+        MOT_TRY(launch_guess(r, n, st));
         MOT_TRY(dev_norms2(r, (const double *)r->b.p, (double *)r->b2.p, st));
         if (!mixed && !dfm) {
             const double tol = p->opt.tol > 0 ? p->opt.tol : 1e-11;
@@ -3216,6 +3230,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     if ((s = dalloc(r->inc, sizeof(double) * nv * nrhs)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->J, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->J2, sizeof(double) * n)) != MOT_OK) return fail(s);
+    if (p->opt.guess == 2 && (s = dalloc(r->J3, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->b, sizeof(double) * n)) != MOT_OK) return fail(s);
     if ((s = dalloc(r->r, sizeof(double) * n)) != MOT_OK) return fail(s);
     size_t ring_bytes = (size_t)p->ell * nrhs * 3 * p->Mh[2] * p->Mh[1] * p->Hh * cs;
@@ -3264,6 +3279,7 @@ mot_status mot_run_create(mot_problem *p, int nrhs, const mot_planewave *exc, in
     cudaMemsetAsync(r->hpart.p, 0, r->hpart.bytes, st);
     cudaMemsetAsync(r->J.p, 0, sizeof(double) * n, st);
     cudaMemsetAsync(r->J2.p, 0, sizeof(double) * n, st);
+    if (r->J3.p) cudaMemsetAsync(r->J3.p, 0, sizeof(double) * n, st);
     for (int i = 0; i < 4; ++i)
         if (cudaEventCreate(&r->ev[i]) != cudaSuccess) return fail(MOT_ECUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MOT_ECUDA);
@@ -3474,6 +3490,7 @@ mot_status mot_run_save(mot_run *r, const char *path) {
         MOT_FAIL(MOT_EINVAL, "checkpoint write failed");
     MOT_TRY(dev_to_file(fc.f, r->J.p, hd.vec_bytes));
     MOT_TRY(dev_to_file(fc.f, r->J2.p, hd.vec_bytes));
+    if (r->J3.p) MOT_TRY(dev_to_file(fc.f, r->J3.p, hd.vec_bytes));  // guess 2 (hd.opt.guess says so)
     MOT_TRY(dev_to_file(fc.f, r->ring.p, hd.ring_bytes));
     if (fflush(fc.f) != 0) MOT_FAIL(MOT_EINVAL, "checkpoint write failed");
     return MOT_OK;
@@ -3506,6 +3523,21 @@ mot_status mot_run_load(mot_problem *p, const char *path, mot_run **out) {
     }
     if (s == MOT_OK) s = file_to_dev(fc.f, r->J.p, vec);
     if (s == MOT_OK) s = file_to_dev(fc.f, r->J2.p, vec);
+    // J_{n-3}: stored when the saving run used guess 2; a run that needs it but finds
+    // none takes J_{n-2} in its place (one less accurate first guess), one that does
+    // not need it skips it
+    if (s == MOT_OK && hd.opt.guess == 2) {
+        if (r->J3.p) s = file_to_dev(fc.f, r->J3.p, vec);
+        else if (fseek(fc.f, (long)vec, SEEK_CUR) != 0) {
+            set_error("checkpoint truncated");
+            s = MOT_EINVAL;
+        }
+    } else if (s == MOT_OK && r->J3.p) {
+        if (cudaMemcpy(r->J3.p, r->J2.p, vec, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+            set_error("cudaMemcpy of J_{n-2} into J_{n-3} failed");
+            s = MOT_ECUDA;
+        }
+    }
     if (s == MOT_OK) s = file_to_dev(fc.f, r->ring.p, hd.ring_bytes);
     if (s != MOT_OK) {
         mot_run_destroy(r);
@@ -3616,6 +3648,7 @@ void mot_run_destroy(mot_run *r) {
     dfree(r->inc);
     dfree(r->J);
     dfree(r->J2);
+    dfree(r->J3);
     dfree(r->b);
     dfree(r->r);
     dfree(r->ring);

@@ -93,6 +93,7 @@ size_t serve_estimate(const ServeJob &j) {
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + M0[1]) * H0 * 16;                        // product workspace
     const bool inner32 = j.precision != MOT_FP64;  // FP32 Krylov vectors (mixed, double-float refined)
     b += 5 * n3 * 8 + 10 * n3 * (inner32 ? 4 : 8) + (inner32 ? 2 * n3 * 4 : 0);          // J, b, r, Krylov
+    if (j.has_opt && j.opt.guess == 2) b += n3 * 8;                                       // J_{n-3}
     const long tb = mixed ? 8 : 4;  // time block of the history: 2 tb partial sums
     b += (size_t)(ell + 1 + 2 * tb) * j.nrhs * 3 * Mh[2] * Mh[1] * Hh * cs;  // history ring, sum, partial sums
     b += (size_t)j.nrhs * 3 * j.n[2] * (j.n[1] + Mh[1]) * Hh * cs;                       // history workspace

@@ -1081,20 +1081,21 @@ __device__ __forceinline__ float2 fma_f32x2(float2 a, float2 b, float2 c) {
 constexpr int kHistBlockDepth = 8;  // ring slots in flight per block (shared-memory pipeline depth)
 constexpr int kHistOld = 0, kHistRecent = 1, kHistAll = 2;  // kHistAll: both parts in one pass at the block start
 
-template <typename T> __host__ __device__ constexpr size_t hist_block_smem() {
-    return (size_t)kHistBlockDepth * 4 * 3 * 32 * sizeof(cplx<T>);
+constexpr int kHistSyncSlots = 2;   // ring slots read per block barrier
+template <typename T, int D = kHistBlockDepth> __host__ __device__ constexpr size_t hist_block_smem() {
+    return (size_t)D * 4 * 3 * 32 * sizeof(cplx<T>);
 }
 
-template <typename T, int TB, int TH, bool Pair = std::is_same<T, float>::value>
+template <typename T, int TB, int TH, bool Pair = std::is_same<T, float>::value, int D = kHistBlockDepth,
+          int G = kHistSyncSlots>
 __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ ring, const T *__restrict__ Lh,
                                                     cplx<T> *__restrict__ qbuf, long qslot, int Mz, int My, int H,
                                                     Octant oc, int nrhs, int ell, long m0, int tlo, int part,
                                                     int c_lo, int c_hi, const long long *__restrict__ nptr, int dm,
                                                     int lpf) {
     static_assert(TB / TH == 4, "four thread groups: group y also loads mirror row y");
-    static_assert(kHistBlockDepth % 2 == 0 && kHistBlockDepth >= 4 && kHistBlockDepth % TH == 0,
-                  "pairs of slots per barrier, whole windows per pipeline round");
-    constexpr int D = kHistBlockDepth;
+    static_assert(D % G == 0 && D >= 2 * G && D % TH == 0,
+                  "whole groups of G slots per barrier, whole windows per pipeline round");
     if (nptr) {
         const long m = (long)*nptr + dm;
         const int t = (int)(m % TB);
@@ -1189,9 +1190,9 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             }
         };
         const int nui = (int)nu, ulo = (int)u_lo;
-        // D - 2 slots in flight ahead of the pair being read (one barrier per two slots)
+        // D - G slots in flight ahead of the G being read (one barrier per G slots)
 #pragma unroll
-        for (int i = 0; i < D - 2; ++i) {
+        for (int i = 0; i < D - G; ++i) {
             if (i < nui) issue(i);
             else asm volatile("cp.async.commit_group;\n" ::);
         }
@@ -1231,15 +1232,16 @@ __global__ void __launch_bounds__(128) k_hist_block(const cplx<T> *__restrict__ 
             for (int ww = 0; ww < D; ++ww) {
                 const int w = w0 + ww;
                 if (w < nui) {
-                    if ((ww & 1) == 0) {
-                        asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 4) : "memory");  // slots w, w + 1 landed
-                        __syncthreads();  // ... for every thread; slots w - 2, w - 1's buffers are free again
-                        // the next two copies go to those buffers; slots w, w + 1's are
+                    if (ww % G == 0) {
+                        asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2 * G) : "memory");  // slots w .. w + G - 1 landed
+                        __syncthreads();  // ... for every thread; slots w - G .. w - 1's buffers are free again
+                        // the next G copies go to those buffers; slots w .. w + G - 1's are
                         // rewritten only after the next barrier
-                        if (w + D - 2 < nui) issue((ww + D - 2) % D);
-                        else asm volatile("cp.async.commit_group;\n" ::);
-                        if (w + D - 1 < nui) issue((ww + D - 1) % D);
-                        else asm volatile("cp.async.commit_group;\n" ::);
+#pragma unroll
+                        for (int j = 0; j < G; ++j) {
+                            if (w + D - G + j < nui) issue((ww + D - G + j) % D);
+                            else asm volatile("cp.async.commit_group;\n" ::);
+                        }
                     }
                     // no test per output: the window holds zeros for lags above ell, and
                     // outputs t < tlo are computed but not stored

@@ -2,7 +2,8 @@
 
 A run marched n1 steps, saved, and resumed from the file in a fresh run must
 produce the same currents for the following steps as the uninterrupted run
-(the state that carries over is J_{n-1}, J_{n-2}, the history ring and the
+(the state that carries over is J_{n-1}, J_{n-2} (and J_{n-3} for the quadratic
+guess), the history ring and the
 step index; everything else is rebuilt).  The uninterrupted run continues in
 graph mode while the resumed one takes its first step host-driven, so the
 comparison allows the drivers' rounding difference (1e-12 relative).
@@ -93,3 +94,40 @@ def test_checkpoint_of_another_problem_is_refused(ctx, tmp_path):
     finally:
         mot.mot_problem_destroy(other)
         mot.mot_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("g_save,g_load", [(2, 1), (1, 2), (0, 2)])
+def test_resume_with_another_initial_guess(ctx, tmp_path, g_save, g_load):
+    """A checkpoint of a run with one initial-guess rule loads into a problem
+    with another: J_{n-3} (kept by guess 2) is skipped when not needed and
+    taken as J_{n-2} when missing.  Only the solver's starting points differ,
+    so the resumed FP64 march agrees with the uninterrupted one to the solver
+    tolerance."""
+    N = (8, 7, 6)
+    eps = synthetic.block_eps(N, 2, 2.0, 5.0, 8)
+    alpha, steps, n1 = 8.0, 10, 4
+    exc = [synthetic.pulse(steps, alpha)]
+    nv = int(np.prod(N))
+    path = tmp_path / "run.ckpt"
+    p1 = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha, mot.default_options(guess=g_save))
+    p2 = mot.mot_problem_create(ctx, N, 10e-9, eps, alpha, mot.default_options(guess=g_load))
+    try:
+        run = mot.mot_run_create(p1, exc, mot.MOT_FP64)
+        try:
+            J = np.zeros((steps, 1, 3, nv))
+            mot.mot_run_step(run, n1, J[:n1])
+            mot.mot_run_save(run, path)
+            mot.mot_run_step(run, steps - n1, J[n1:])
+        finally:
+            mot.mot_run_destroy(run)
+        run2 = mot.mot_run_load(p2, path)
+        try:
+            J2 = np.zeros((steps - n1, 1, 3, nv))
+            mot.mot_run_step(run2, steps - n1, J2)
+        finally:
+            mot.mot_run_destroy(run2)
+        assert np.abs(J[n1:]).max() > 0
+        assert _rel(J2, J[n1:]) <= 1e-9
+    finally:
+        mot.mot_problem_destroy(p2)
+        mot.mot_problem_destroy(p1)

@@ -129,6 +129,21 @@ def test_mot_small_fp64_and_mixed(ctx, orc):
     assert edf.max() <= 1e-9, edf.max()
 
 
+@pytest.mark.parametrize("guess", [0, 1, 2])
+def test_march_initial_guesses(ctx, orc, guess):
+    """Every initial guess of the step's solve (J_{n-1}; its linear and its
+    quadratic extrapolation) reaches the oracle's march: the guess moves the
+    solver's starting point only."""
+    N = (7, 6, 5)
+    eps = synthetic.block_eps(N, 2, 1.5, 5.0, 33)
+    alpha, steps = 4.0, 24
+    exc = [synthetic.pulse(steps, alpha)]
+    Jo = orc.Problem(N, 10e-9, eps, alpha).march(exc, steps)
+    for prec, tol in ((mot.MOT_FP64, 1e-9), (mot.MOT_MIXED, 1e-5)):
+        e = _mot_errors(_march_pair(ctx, orc, N, eps, alpha, exc, steps, prec, mot.default_options(guess=guess)), Jo)
+        assert e.max() <= tol, (guess, prec, e.max())
+
+
 def test_mot_oblique_batch(ctx, orc):
     N = (8, 8, 8)
     eps = synthetic.block_eps(N, 4, 2.0, 4.0, 4)

@@ -88,4 +88,4 @@ def test_ctypes_structs_match_header(tmp_path):
     # the binding's defaults follow the header's documented defaults
     o = mot.default_options()
     assert (o.maxit, o.inner_tol, o.max_refine, o.delta, o.timing, o.guess, o.graph, o.autotune) == \
-        (500, 1e-6, 6, 0.0, 0, 1, 1, 1)
+        (500, 1e-6, 6, 0.0, 0, 2, 1, 1)
