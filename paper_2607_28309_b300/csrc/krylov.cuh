@@ -909,22 +909,54 @@ __device__ __forceinline__ int pow2_exponent(double n2) {
     return ilogb(n2) / 2;
 }
 
+// 2^k as a double, built from its exponent field (|k| <= 1022; pow2_exponent's
+// range, |k| <= 537, lies well inside): x * pow2d(k) is ldexp(x, k), rounded
+// the same way where the result is subnormal
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// dst = 2^-e src in FP32 (e from ||src||^2 per right-hand side); 16-byte packs
+// when L allows (vectors of L elements per right-hand side start 16-byte aligned)
 __global__ void k_convert_scaled(float *__restrict__ dst, const double *__restrict__ src,
                                  const double *__restrict__ n2, long L) {
     const int b = blockIdx.y;
-    const int e = pow2_exponent(n2[b]);
+    const double sc = pow2d(-pow2_exponent(n2[b]));
     const long o = (long)b * L;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
-        dst[o + i] = (float)ldexp(src[o + i], -e);
+    const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+    if (L % 4 == 0) {
+        for (long j = t0; j < L / 4; j += ts) {
+            double v[4];
+            float f[4];
+            ldv<4>(v, src + o + 4 * j);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] = (float)(v[k] * sc);
+            stv<4>(dst + o + 4 * j, f);
+        }
+    } else {
+        for (long i = t0; i < L; i += ts) dst[o + i] = (float)(src[o + i] * sc);
+    }
 }
 
+// J += 2^e c (the correction of a refinement sweep; the product is exact, so the
+// sum rounds once as with ldexp)
 __global__ void k_add_scaled(double *__restrict__ J, const float *__restrict__ c, const double *__restrict__ n2,
                              long L) {
     const int b = blockIdx.y;
-    const int e = pow2_exponent(n2[b]);
+    const double sc = pow2d(pow2_exponent(n2[b]));
     const long o = (long)b * L;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
-        J[o + i] += ldexp((double)c[o + i], e);
+    const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+    if (L % 4 == 0) {
+        for (long j = t0; j < L / 4; j += ts) {
+            double v[4];
+            float f[4];
+            ldv<4>(v, J + o + 4 * j);
+            ldv<4>(f, c + o + 4 * j);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += (double)f[k] * sc;
+            stv<4>(J + o + 4 * j, v);
+        }
+    } else {
+        for (long i = t0; i < L; i += ts) J[o + i] += (double)c[o + i] * sc;
+    }
 }
 
 // start of a solve from x0 = 0 in one kernel: w = y1 = r* = rhs, x = d = 0, the
@@ -944,11 +976,11 @@ __global__ void __launch_bounds__(kRedThreads) k_tfqmr_start_zero(const S *__res
     __shared__ double sh[32];
     const int b = blockIdx.y;
     const long o = (long)b * L;
-    const int e = n2 ? pow2_exponent(n2[b]) : 0;
+    const double scl = n2 ? pow2d(-pow2_exponent(n2[b])) : 1.0;  // 2^-e: the product is k_convert_scaled's
     using A = typename AccOf<V>::type;
     A s = A(0);
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x) {
-        const V v = n2 ? (V)ldexp((double)src[o + i], -e) : (V)src[o + i];
+        const V v = n2 ? (V)((double)src[o + i] * scl) : (V)src[o + i];
         w[o + i] = v;
         y1[o + i] = v;
         rs[o + i] = v;
